@@ -1,0 +1,172 @@
+/*
+ * rpca.h -- C ABI of the GB300 robust-PCA solver (principal component pursuit
+ * by the augmented-Lagrangian iteration) for ultrasound frame windows.
+ *
+ * Method (arXiv 2506.10257, Sec. II-A): a window of T frames of m pixels forms
+ * the Casorati matrix X (m x T, Eq. 1 context).  PCP (Eq. 2) splits
+ * X = L + S into a low-rank L (bound bubbles, tissue) and a sparse S (free
+ * bubbles, noise).  Each iteration does
+ *     Eq. 4  L = D_{1/mu}(X - S + Y/mu)        singular value thresholding
+ *     Eq. 5  S = shrink_{lambda/mu}(X - L + Y/mu)
+ *     Eq. 6  Y = Y + mu (X - L - S)
+ * and stops when ||X - L - S||_F <= tol ||X||_F (Sec. II-A).
+ *
+ * Memory layout (all device buffers): frame-major, i.e. column-major X with
+ * element (pixel p, frame t) at X[t*m + p]; frame t is a contiguous run of m
+ * values.  Real data is float32; complex IQ data is interleaved complex64
+ * (re, im) pairs with the same indexing.  Buffers must be 16-byte aligned.
+ *
+ * Ownership: the caller owns X, L, S and mask; X is only read.  A plan owns
+ * its workspace (iterate state, Gram partials, eigenvectors) unless the
+ * caller passes one.  Every entry point returns a status; nothing is thrown
+ * across the ABI.  A plan is not thread-safe; a server is (submit/poll may be
+ * called from several host threads).
+ */
+#ifndef RPCA_H_
+#define RPCA_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RPCA_OK = 0,
+  RPCA_NOT_CONVERGED = 1,   /* max_iter reached; outputs hold the last iterate */
+  RPCA_PENDING = 2,         /* rpca_poll: request not finished yet */
+  RPCA_ERR_ARG = -1,        /* invalid argument (shape, pointer, tolerance ...) */
+  RPCA_ERR_CUDA = -2,       /* a CUDA runtime call failed */
+  RPCA_ERR_NOMEM = -3,      /* device allocation failed */
+  RPCA_ERR_BUDGET = -4,     /* request exceeds the server's HBM budget */
+  RPCA_ERR_TIMEOUT = -5,    /* a bounded device wait ran out */
+  RPCA_ERR_NONFINITE = -6,  /* residual became NaN/Inf (input not finite) */
+  RPCA_ERR_UNSUPPORTED = -7,/* shape/precision combination not built */
+  RPCA_ERR_NOTFOUND = -8    /* unknown request id */
+} rpca_status;
+
+typedef enum { RPCA_R32 = 0, RPCA_C64 = 1 } rpca_dtype;
+
+/* Arithmetic of the two dense contractions per iteration (Z*Wbar and the
+ * rotated Gram).  The eigensolve, the sigma-vs-tau decision, mu and the
+ * convergence test are FP64 in every mode. */
+typedef enum {
+  RPCA_PREC_FP32 = 0,       /* FP32 CUDA-core FMA */
+  RPCA_PREC_TF32X3 = 1,     /* tensor cores, TF32 hi/lo split, 3 products, FP32 accumulate */
+  RPCA_PREC_BF16X3 = 2,     /* tensor cores, BF16 hi/lo split, 3 products, FP32 accumulate */
+  RPCA_PREC_TF32 = 3        /* tensor cores, plain TF32 */
+} rpca_precision;
+
+/* Penalty schedule.  IALM: mu_1 = mu0_scale/||X||_2, mu_{k+1} = min(rho mu_k,
+ * mu_max_factor mu_1).  FIXED_L1: mu = m T / (4 ||X||_1) for every iteration
+ * (the choice of Sec. II-A / II-B). */
+typedef enum { RPCA_MU_IALM = 0, RPCA_MU_FIXED_L1 = 1 } rpca_mu_schedule;
+
+/* How the iterations are driven. */
+typedef enum {
+  RPCA_DRIVE_GRAPH = 0,     /* one CUDA graph per solve, device-side while loop, fused pass */
+  RPCA_DRIVE_HOST = 1       /* host loop, separate Gram / update passes, residual read back
+                               every iteration (the plain form) */
+} rpca_drive;
+
+typedef struct {
+  int64_t m;                /* pixels per frame (rows of X), >= 1 */
+  int32_t T;                /* frames (columns of X), 1 <= T <= RPCA_MAX_T */
+  int32_t dtype;            /* rpca_dtype */
+  int32_t precision;        /* rpca_precision */
+  int32_t mu_schedule;      /* rpca_mu_schedule */
+  int32_t drive;            /* rpca_drive */
+  int32_t max_iter;         /* >= 1 (default 500) */
+  double lambda;            /* <= 0 selects 1/sqrt(max(m, T)) */
+  double mu0_scale;         /* IALM: mu_1 = mu0_scale / ||X||_2 (default 1.25) */
+  double rho;               /* IALM growth factor (default 1.5), >= 1 */
+  double mu_max_factor;     /* IALM cap mu_max = factor * mu_1 (default 1e7) */
+  double tol;               /* relative Frobenius stopping tolerance (default 1e-7), > 0 */
+} rpca_params;
+
+#define RPCA_MAX_T 32
+
+typedef struct {
+  int32_t status;           /* rpca_status of this solve */
+  int32_t iters;            /* completed iterations (Y updates) */
+  int32_t rank;             /* singular values above 1/mu in the last iteration */
+  int32_t sweeps;           /* Jacobi sweeps summed over the solve */
+  double resid;             /* ||X - L - S||_F / ||X||_F of the last iteration */
+  double mu;                /* penalty used by the last iteration */
+  double normX;             /* ||X||_F */
+  double lambda;            /* lambda used */
+  double pass_us;           /* mean device time of the per-iteration passes after the
+                               first (device global timer, first CTA start to last
+                               CTA end), microseconds */
+  double eig_us;            /* mean device time of the eigen-steps, microseconds */
+  double init_us;           /* device time of the initial pass over X, microseconds */
+  int32_t passes_timed;     /* passes in pass_us */
+  int32_t eigs_timed;       /* eigen-steps in eig_us */
+} rpca_result;
+
+typedef struct rpca_plan_s* rpca_plan_t;
+
+/* Fill *p with the defaults above for an m x T real window. */
+rpca_status rpca_params_default(rpca_params* p, int64_t m, int32_t T);
+
+/* Bytes of device workspace a plan with these parameters needs. */
+rpca_status rpca_workspace_size(const rpca_params* p, size_t* bytes);
+
+/* Create a plan.  `workspace` is a device buffer of at least
+ * rpca_workspace_size() bytes owned by the caller (kept alive until
+ * rpca_plan_destroy), or NULL to let the plan allocate its own.  Builds the
+ * CUDA graph on first use.  Errors: RPCA_ERR_ARG, RPCA_ERR_UNSUPPORTED,
+ * RPCA_ERR_NOMEM, RPCA_ERR_CUDA. */
+rpca_status rpca_plan_create(const rpca_params* p, void* workspace, size_t workspace_bytes,
+                             rpca_plan_t* out);
+
+/* Solve PCP for one window on `stream` (a cudaStream_t, NULL = legacy default).
+ *   X     device, m x T frame-major, read only.
+ *   L, S  device outputs, m x T frame-major (may not alias X or each other).
+ *   mask  optional device output of m bytes: 1 where the per-pixel temporal
+ *         mean of |L| is >= theta (the binarised bound-bubble image of
+ *         Sec. II-F), else 0.  NULL skips it.
+ *   out   if non-NULL the call waits for the stream and fills *out; if NULL
+ *         the call returns right after enqueueing and the result can be read
+ *         with rpca_plan_result() after the stream has been synchronised.
+ * Returns the solve status when out != NULL, else RPCA_OK once enqueued. */
+rpca_status rpca_solve(rpca_plan_t plan, const void* X, void* L, void* S, uint8_t* mask,
+                       float theta, void* stream, rpca_result* out);
+
+/* Same as rpca_solve with HOST buffers: X_host (m*T values, frame-major) is
+ * copied to device staging buffers owned by the plan (allocated on the first
+ * call), the window is solved, and L, S (and the mask, if mask_host is not
+ * NULL) are copied back into the host buffers; the call returns when they are
+ * there.  Host buffers should be pinned (cudaHostAlloc) for full copy speed.
+ * `out` may be NULL. */
+rpca_status rpca_solve_host(rpca_plan_t plan, const void* X_host, void* L_host, void* S_host,
+                            uint8_t* mask_host, float theta, void* stream, rpca_result* out);
+
+/* Result of the last solve on this plan (call after synchronising its stream). */
+rpca_status rpca_plan_result(rpca_plan_t plan, rpca_result* out);
+
+void rpca_plan_destroy(rpca_plan_t plan);
+
+const char* rpca_status_str(int32_t status);
+
+/* ---- kernel-level entry points (each one step of the iteration) ---------- */
+
+/* Rotated Gram of a window: G = (Z V)^T (Z V) with Z = X (frame-major m x T,
+ * real float32) and V a T x T row-major float32 matrix (NULL = identity).
+ * G is written as T x T row-major float64 on the device.  This is the
+ * contraction that feeds the SVT step of Eq. 4 (SVD of Z through the
+ * eigen-decomposition of its Gram).  Synchronous on `stream`. */
+rpca_status rpca_gram(const float* X, int64_t m, int32_t T, const float* V, double* G,
+                      int32_t precision, void* stream);
+
+/* Symmetric eigen-decomposition of a T x T float64 matrix G (row-major,
+ * device) by cyclic Jacobi in FP64 on one CTA: on return evals[i] and the
+ * columns of evecs (T x T row-major, device) satisfy G evecs = evecs diag(evals),
+ * evals in descending order.  Synchronous on `stream`. */
+rpca_status rpca_eig(const double* G, int32_t T, double* evals, double* evecs, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RPCA_H_ */

@@ -1,0 +1,548 @@
+// rpca_capi.cu -- C ABI of the GB300 PCP solver: plans, CUDA-graph driver,
+// host-driven plain form, kernel-level entry points.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "../../include/rpca.h"
+#include "rpca_kernels.cuh"
+
+using namespace rpca;
+
+namespace {
+
+struct KernelSet {
+  void* pass[4];
+  void* eig32;
+  void* eig64;
+  int TB;
+  int eig_threads;
+};
+
+template <int TB>
+KernelSet make_set() {
+  KernelSet k;
+  k.pass[PM_INIT] = (void*)pass_kernel<TB, PM_INIT>;
+  k.pass[PM_FUSED] = (void*)pass_kernel<TB, PM_FUSED>;
+  k.pass[PM_UPDATE] = (void*)pass_kernel<TB, PM_UPDATE>;
+  k.pass[PM_GRAM] = (void*)pass_kernel<TB, PM_GRAM>;
+  k.eig32 = (void*)eig_kernel<TB, float>;
+  k.eig64 = (void*)eig_kernel<TB, double>;
+  k.TB = TB;
+  k.eig_threads = TB > 20 ? 512 : 256;
+  return k;
+}
+
+int bucket_of(int T) {
+  if (T <= 8) return 8;
+  if (T <= 12) return 12;
+  if (T <= 16) return 16;
+  if (T <= 20) return 20;
+  if (T <= 24) return 24;
+  if (T <= 32) return 32;
+  return 0;
+}
+
+bool get_set(int T, KernelSet* out) {
+  switch (bucket_of(T)) {
+    case 8: *out = make_set<8>(); return true;
+    case 12: *out = make_set<12>(); return true;
+    case 16: *out = make_set<16>(); return true;
+    case 20: *out = make_set<20>(); return true;
+    case 24: *out = make_set<24>(); return true;
+    case 32: *out = make_set<32>(); return true;
+    default: return false;
+  }
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Layout {
+  size_t ctrl, eig, red, job, gram_part, group_part, scal_part, gscal_part, ybuf, total;
+  int grid, ngroups;
+};
+
+int device_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return sms;
+}
+
+// Grid: two 256-thread CTAs per SM (register bound), never more than the tiles.
+Layout make_layout(int64_t m, int T, int sms) {
+  Layout L;
+  const int64_t ntiles = (m + kTile - 1) / kTile;
+  int64_t grid = std::min<int64_t>(ntiles, (int64_t)std::max(sms, 1) * 2);
+  grid = std::min<int64_t>(grid, (int64_t)kGroup * kMaxGroups);
+  L.grid = (int)std::max<int64_t>(grid, 1);
+  L.ngroups = (L.grid + kGroup - 1) / kGroup;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + bytes, 256);
+    return o;
+  };
+  L.ctrl = take(sizeof(Ctrl));
+  L.eig = take(sizeof(EigState));
+  L.red = take(sizeof(RedState));
+  L.job = take(sizeof(Job));
+  L.gram_part = take(sizeof(float) * (size_t)L.grid * T * T);
+  L.group_part = take(sizeof(float) * (size_t)L.ngroups * T * T);
+  L.scal_part = take(sizeof(double) * 2 * (size_t)L.grid);
+  L.gscal_part = take(sizeof(double) * 2 * (size_t)L.ngroups);
+  L.ybuf = take(sizeof(float) * (size_t)m * T);
+  L.total = off;
+  return L;
+}
+
+rpca_status validate(const rpca_params* p) {
+  if (!p) return RPCA_ERR_ARG;
+  if (p->m < 1 || p->T < 1) return RPCA_ERR_ARG;
+  if (p->T > RPCA_MAX_T) return RPCA_ERR_UNSUPPORTED;
+  if (!(p->tol > 0) || p->max_iter < 1) return RPCA_ERR_ARG;
+  if (p->mu_schedule != RPCA_MU_IALM && p->mu_schedule != RPCA_MU_FIXED_L1) return RPCA_ERR_ARG;
+  if (p->mu_schedule == RPCA_MU_IALM && (!(p->rho >= 1.0) || !(p->mu0_scale > 0) || !(p->mu_max_factor >= 1.0)))
+    return RPCA_ERR_ARG;
+  if (p->drive != RPCA_DRIVE_GRAPH && p->drive != RPCA_DRIVE_HOST) return RPCA_ERR_ARG;
+  if (p->dtype != RPCA_R32) return RPCA_ERR_UNSUPPORTED;
+  if (p->precision != RPCA_PREC_FP32) return RPCA_ERR_UNSUPPORTED;
+  if (p->m * (int64_t)p->T > (int64_t)1 << 40) return RPCA_ERR_ARG;
+  return RPCA_OK;
+}
+
+}  // namespace
+
+struct rpca_plan_s {
+  rpca_params p;
+  KernelSet ks;
+  Layout lay;
+  Bufs bufs;
+  char* ws;
+  bool own_ws;
+  double lambda;
+  int eig_fp64;
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  Ctrl* ctrl_host;  // pinned
+  // device staging of rpca_solve_host (allocated on first use)
+  float* stage_x;
+  float* stage_l;
+  float* stage_s;
+  uint8_t* stage_mask;
+};
+
+static rpca_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return RPCA_OK;
+  if (e == cudaErrorMemoryAllocation) return RPCA_ERR_NOMEM;
+  return RPCA_ERR_CUDA;
+}
+#define CK(x)                                 \
+  do {                                        \
+    cudaError_t _e = (x);                     \
+    if (_e != cudaSuccess) return cuda_status(_e); \
+  } while (0)
+
+static cudaError_t launch(void* fn, dim3 g, dim3 blk, void** args, cudaStream_t s) {
+  return cudaLaunchKernel(fn, g, blk, args, 0, s);
+}
+
+static void* eig_fn(const rpca_plan_s* pl) { return pl->eig_fp64 ? pl->ks.eig64 : pl->ks.eig32; }
+
+static cudaError_t add_kernel(cudaGraph_t g, cudaGraphNode_t* node, const cudaGraphNode_t* deps, size_t ndeps,
+                              void* fn, dim3 grid, dim3 blk, void** args) {
+  cudaKernelNodeParams kp;
+  memset(&kp, 0, sizeof(kp));
+  kp.func = fn;
+  kp.gridDim = grid;
+  kp.blockDim = blk;
+  kp.sharedMemBytes = 0;
+  kp.kernelParams = args;
+  kp.extra = nullptr;
+  return cudaGraphAddKernelNode(node, g, deps, ndeps, &kp);
+}
+
+// Graph: init pass -> eig(init) -> while(cond){ fused pass -> eig(check|eig) } -> final.
+static rpca_status build_graph(rpca_plan_s* pl) {
+  CK(cudaGraphCreate(&pl->graph, 0));
+  cudaGraphConditionalHandle h;
+  CK(cudaGraphConditionalHandleCreate(&h, pl->graph, 0, cudaGraphCondAssignDefault));
+  Bufs b = pl->bufs;
+  const dim3 pg(pl->lay.grid), pb(kPassThreads), eg(1), eb(pl->ks.eig_threads);
+  const double* nulld = nullptr;
+  double* nullo = nullptr;
+  int use_cond = 1;
+  int f_init = EF_INIT | EF_EIG, f_iter = EF_CHECK | EF_EIG;
+
+  void* a_pass[] = {&b};
+  void* a_eig0[] = {&b, &f_init, &h, &use_cond, &nulld, &nullo, &nullo};
+  void* a_eig1[] = {&b, &f_iter, &h, &use_cond, &nulld, &nullo, &nullo};
+  cudaGraphNode_t n_init, n_eig0, n_while, n_fin, n_pass, n_eig;
+  CK(add_kernel(pl->graph, &n_init, nullptr, 0, pl->ks.pass[PM_INIT], pg, pb, a_pass));
+  CK(add_kernel(pl->graph, &n_eig0, &n_init, 1, eig_fn(pl), eg, eb, a_eig0));
+
+  alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+  memset(cp_raw, 0, sizeof(cp_raw));
+  cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_raw);
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  CK(cudaGraphAddNode(&n_while, pl->graph, &n_eig0, nullptr, 1, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  CK(add_kernel(body, &n_pass, nullptr, 0, pl->ks.pass[PM_FUSED], pg, pb, a_pass));
+  CK(add_kernel(body, &n_eig, &n_pass, 1, eig_fn(pl), eg, eb, a_eig1));
+
+  const int fgrid = (int)std::min<int64_t>((pl->p.m + 255) / 256, 4096);
+  CK(add_kernel(pl->graph, &n_fin, &n_while, 1, (void*)final_kernel, dim3(fgrid), dim3(256), a_pass));
+  CK(cudaGraphInstantiate(&pl->exec, pl->graph, 0));
+  return RPCA_OK;
+}
+
+extern "C" {
+
+rpca_status rpca_params_default(rpca_params* p, int64_t m, int32_t T) {
+  if (!p) return RPCA_ERR_ARG;
+  memset(p, 0, sizeof(*p));
+  p->m = m;
+  p->T = T;
+  p->dtype = RPCA_R32;
+  p->precision = RPCA_PREC_FP32;
+  p->mu_schedule = RPCA_MU_IALM;
+  p->drive = RPCA_DRIVE_GRAPH;
+  p->max_iter = 500;
+  p->lambda = 0.0;
+  p->mu0_scale = 1.25;
+  p->rho = 1.5;
+  p->mu_max_factor = 1e7;
+  p->tol = 1e-7;
+  return RPCA_OK;
+}
+
+rpca_status rpca_workspace_size(const rpca_params* p, size_t* bytes) {
+  rpca_status st = validate(p);
+  if (st != RPCA_OK) return st;
+  if (!bytes) return RPCA_ERR_ARG;
+  const int sms = device_sms();
+  if (sms <= 0) return RPCA_ERR_CUDA;
+  *bytes = make_layout(p->m, p->T, sms).total;
+  return RPCA_OK;
+}
+
+rpca_status rpca_plan_create(const rpca_params* p, void* workspace, size_t workspace_bytes, rpca_plan_t* out) {
+  rpca_status st = validate(p);
+  if (st != RPCA_OK) return st;
+  if (!out) return RPCA_ERR_ARG;
+  *out = nullptr;
+  const int sms = device_sms();
+  if (sms <= 0) return RPCA_ERR_CUDA;
+  rpca_plan_s* pl = new rpca_plan_s();
+  pl->p = *p;
+  if (!get_set(p->T, &pl->ks)) {
+    delete pl;
+    return RPCA_ERR_UNSUPPORTED;
+  }
+  pl->lay = make_layout(p->m, p->T, sms);
+  pl->eig_fp64 = (getenv("RPCA_EIG_FP64") && atoi(getenv("RPCA_EIG_FP64")) != 0) ? 1 : 0;
+  if (workspace) {
+    if (workspace_bytes < pl->lay.total || ((uintptr_t)workspace & 255u)) {
+      delete pl;
+      return RPCA_ERR_ARG;
+    }
+    pl->ws = (char*)workspace;
+    pl->own_ws = false;
+  } else {
+    cudaError_t e = cudaMalloc((void**)&pl->ws, pl->lay.total);
+    if (e != cudaSuccess) {
+      delete pl;
+      return cuda_status(e);
+    }
+    pl->own_ws = true;
+  }
+  Bufs& b = pl->bufs;
+  b.ctrl = (Ctrl*)(pl->ws + pl->lay.ctrl);
+  b.eig = (EigState*)(pl->ws + pl->lay.eig);
+  b.red = (RedState*)(pl->ws + pl->lay.red);
+  b.job = (Job*)(pl->ws + pl->lay.job);
+  b.gram_part = (float*)(pl->ws + pl->lay.gram_part);
+  b.group_part = (float*)(pl->ws + pl->lay.group_part);
+  b.scal_part = (double*)(pl->ws + pl->lay.scal_part);
+  b.gscal_part = (double*)(pl->ws + pl->lay.gscal_part);
+  b.m = p->m;
+  b.T = p->T;
+  b.grid = pl->lay.grid;
+  b.ngroups = pl->lay.ngroups;
+
+  const int mT = (int)std::max<int64_t>(p->m, p->T);
+  pl->lambda = p->lambda > 0 ? p->lambda : 1.0 / sqrt((double)mT);
+  Ctrl c;
+  memset(&c, 0, sizeof(c));
+  c.max_iter = p->max_iter;
+  c.schedule = p->mu_schedule == RPCA_MU_IALM ? 0 : 1;
+  c.lambda = pl->lambda;
+  c.rho = p->rho;
+  c.mu0_scale = p->mu0_scale;
+  c.mu_max_factor = p->mu_max_factor;
+  c.tol = p->tol;
+  c.jacobi_eps = pl->eig_fp64 ? 1e-12 : 1e-6;
+  c.warm_sweeps = 4;
+  c.cold_sweeps = 30;
+  cudaError_t e = cudaMemset(pl->ws, 0, pl->lay.gram_part);  // ctrl, eig, red (counters), job
+  if (e == cudaSuccess) e = cudaMemcpy(b.ctrl, &c, sizeof(c), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&pl->ctrl_host, sizeof(Ctrl));
+  if (e != cudaSuccess) {
+    if (pl->own_ws) cudaFree(pl->ws);
+    delete pl;
+    return cuda_status(e);
+  }
+  // Dual buffer 1 lives in the workspace; buffer 0 is the caller's L.
+  float* y1 = (float*)(pl->ws + pl->lay.ybuf);
+  e = cudaMemcpy(&b.job->Y1, &y1, sizeof(float*), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFreeHost(pl->ctrl_host);
+    if (pl->own_ws) cudaFree(pl->ws);
+    delete pl;
+    return cuda_status(e);
+  }
+  if (p->drive == RPCA_DRIVE_GRAPH) {
+    rpca_status gs = build_graph(pl);
+    if (gs != RPCA_OK) {
+      rpca_plan_destroy(pl);
+      return gs;
+    }
+  }
+  *out = pl;
+  return RPCA_OK;
+}
+
+static void fill_result(const rpca_plan_s* pl, const Ctrl& c, rpca_result* out) {
+  memset(out, 0, sizeof(*out));
+  out->status = c.status;
+  out->iters = c.k;
+  out->rank = c.rank;
+  out->sweeps = c.total_sweeps;
+  out->resid = c.resid;
+  out->mu = c.mu_cur;
+  out->normX = c.normX;
+  out->lambda = pl->lambda;
+  out->pass_us = c.pass_cnt ? (double)c.pass_ns / (double)c.pass_cnt * 1e-3 : 0.0;
+  out->eig_us = c.eig_cnt ? (double)c.eig_ns / (double)c.eig_cnt * 1e-3 : 0.0;
+  out->init_us = (double)c.init_ns * 1e-3;
+  out->passes_timed = (int32_t)c.pass_cnt;
+  out->eigs_timed = (int32_t)c.eig_cnt;
+}
+
+// The plain form: separate Gram and update passes, residual read back by the
+// host after every iteration (one host synchronisation per iteration).
+static rpca_status run_host_loop(rpca_plan_s* pl, cudaStream_t s) {
+  Bufs b = pl->bufs;
+  const dim3 pg(pl->lay.grid), pb(kPassThreads), eg(1), eb(pl->ks.eig_threads);
+  cudaGraphConditionalHandle h = 0;
+  const double* nulld = nullptr;
+  double* nullo = nullptr;
+  int use_cond = 0;
+  int f_init = EF_INIT | EF_EIG, f_check = EF_CHECK, f_eig = EF_EIG;
+  void* a_pass[] = {&b};
+  void* a_init[] = {&b, &f_init, &h, &use_cond, &nulld, &nullo, &nullo};
+  void* a_check[] = {&b, &f_check, &h, &use_cond, &nulld, &nullo, &nullo};
+  void* a_eig[] = {&b, &f_eig, &h, &use_cond, &nulld, &nullo, &nullo};
+  CK(launch(pl->ks.pass[PM_INIT], pg, pb, a_pass, s));
+  CK(launch(eig_fn(pl), eg, eb, a_init, s));
+  for (int it = 0; it <= pl->p.max_iter; ++it) {
+    CK(cudaMemcpyAsync(pl->ctrl_host, b.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (pl->ctrl_host->done) break;
+    CK(launch(pl->ks.pass[PM_UPDATE], pg, pb, a_pass, s));
+    CK(launch(eig_fn(pl), eg, eb, a_check, s));
+    CK(cudaMemcpyAsync(pl->ctrl_host, b.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (pl->ctrl_host->done) break;
+    CK(launch(pl->ks.pass[PM_GRAM], pg, pb, a_pass, s));
+    CK(launch(eig_fn(pl), eg, eb, a_eig, s));
+  }
+  const int fgrid = (int)std::min<int64_t>((pl->p.m + 255) / 256, 4096);
+  CK(launch((void*)final_kernel, dim3(fgrid), dim3(256), a_pass, s));
+  return RPCA_OK;
+}
+
+rpca_status rpca_solve(rpca_plan_t pl, const void* X, void* L, void* S, uint8_t* mask, float theta, void* stream,
+                       rpca_result* out) {
+  if (!pl || !X || !L || !S) return RPCA_ERR_ARG;
+  if (((uintptr_t)X | (uintptr_t)L | (uintptr_t)S) & 15u) return RPCA_ERR_ARG;
+  if (X == L || X == S || L == S) return RPCA_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  Bufs b = pl->bufs;
+  void* a_begin[] = {&b, (void*)&X, &L, &S, &mask, &theta};
+  CK(cudaLaunchKernel((void*)begin_kernel, dim3(1), dim3(32), a_begin, 0, s));
+  if (pl->p.drive == RPCA_DRIVE_GRAPH) {
+    CK(cudaGraphLaunch(pl->exec, s));
+  } else {
+    rpca_status st = run_host_loop(pl, s);
+    if (st != RPCA_OK) return st;
+  }
+  if (!out) return RPCA_OK;
+  CK(cudaMemcpyAsync(pl->ctrl_host, b.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  fill_result(pl, *pl->ctrl_host, out);
+  return (rpca_status)out->status;
+}
+
+rpca_status rpca_plan_result(rpca_plan_t pl, rpca_result* out) {
+  if (!pl || !out) return RPCA_ERR_ARG;
+  CK(cudaMemcpy(pl->ctrl_host, pl->bufs.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
+  fill_result(pl, *pl->ctrl_host, out);
+  return RPCA_OK;
+}
+
+rpca_status rpca_solve_host(rpca_plan_t pl, const void* X_host, void* L_host, void* S_host, uint8_t* mask_host,
+                            float theta, void* stream, rpca_result* out) {
+  if (!pl || !X_host || !L_host || !S_host) return RPCA_ERR_ARG;
+  const size_t bytes = sizeof(float) * (size_t)pl->p.m * pl->p.T;
+  if (!pl->stage_x) {
+    CK(cudaMalloc((void**)&pl->stage_x, bytes));
+    CK(cudaMalloc((void**)&pl->stage_l, bytes));
+    CK(cudaMalloc((void**)&pl->stage_s, bytes));
+    CK(cudaMalloc((void**)&pl->stage_mask, (size_t)pl->p.m));
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(pl->stage_x, X_host, bytes, cudaMemcpyHostToDevice, s));
+  rpca_status st = rpca_solve(pl, pl->stage_x, pl->stage_l, pl->stage_s, mask_host ? pl->stage_mask : nullptr, theta,
+                              stream, nullptr);
+  if (st != RPCA_OK) return st;
+  CK(cudaMemcpyAsync(L_host, pl->stage_l, bytes, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(S_host, pl->stage_s, bytes, cudaMemcpyDeviceToHost, s));
+  if (mask_host) CK(cudaMemcpyAsync(mask_host, pl->stage_mask, (size_t)pl->p.m, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(pl->ctrl_host, pl->bufs.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (!out) return (rpca_status)(pl->ctrl_host->status < 0 ? pl->ctrl_host->status : RPCA_OK);
+  fill_result(pl, *pl->ctrl_host, out);
+  return (rpca_status)out->status;
+}
+
+void rpca_plan_destroy(rpca_plan_t pl) {
+  if (!pl) return;
+  if (pl->stage_x) cudaFree(pl->stage_x);
+  if (pl->stage_l) cudaFree(pl->stage_l);
+  if (pl->stage_s) cudaFree(pl->stage_s);
+  if (pl->stage_mask) cudaFree(pl->stage_mask);
+  if (pl->exec) cudaGraphExecDestroy(pl->exec);
+  if (pl->graph) cudaGraphDestroy(pl->graph);
+  if (pl->ctrl_host) cudaFreeHost(pl->ctrl_host);
+  if (pl->own_ws && pl->ws) cudaFree(pl->ws);
+  delete pl;
+}
+
+const char* rpca_status_str(int32_t s) {
+  switch (s) {
+    case RPCA_OK: return "ok";
+    case RPCA_NOT_CONVERGED: return "not converged (max_iter reached)";
+    case RPCA_PENDING: return "pending";
+    case RPCA_ERR_ARG: return "invalid argument";
+    case RPCA_ERR_CUDA: return "CUDA error";
+    case RPCA_ERR_NOMEM: return "out of device memory";
+    case RPCA_ERR_BUDGET: return "HBM budget exceeded";
+    case RPCA_ERR_TIMEOUT: return "device wait timed out";
+    case RPCA_ERR_NONFINITE: return "non-finite residual";
+    case RPCA_ERR_UNSUPPORTED: return "unsupported shape or precision";
+    case RPCA_ERR_NOTFOUND: return "unknown request";
+    default: return "unknown status";
+  }
+}
+
+rpca_status rpca_gram(const float* X, int64_t m, int32_t T, const float* V, double* G, int32_t precision,
+                      void* stream) {
+  if (!X || !G || m < 1 || T < 1) return RPCA_ERR_ARG;
+  if (T > RPCA_MAX_T) return RPCA_ERR_UNSUPPORTED;
+  if (precision != RPCA_PREC_FP32) return RPCA_ERR_UNSUPPORTED;
+  rpca_params p;
+  rpca_params_default(&p, m, T);
+  p.drive = RPCA_DRIVE_HOST;
+  rpca_plan_t pl = nullptr;
+  rpca_status st = rpca_plan_create(&p, nullptr, 0, &pl);
+  if (st != RPCA_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<float> v32(kMaxT * kMaxT, 0.f);
+  if (V) {
+    std::vector<float> vh((size_t)T * T);
+    cudaError_t e = cudaMemcpy(vh.data(), V, sizeof(float) * T * T, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+      rpca_plan_destroy(pl);
+      return cuda_status(e);
+    }
+    for (int r = 0; r < T; ++r)
+      for (int c = 0; c < T; ++c) v32[r * kMaxT + c] = vh[r * T + c];
+  } else {
+    for (int r = 0; r < T; ++r) v32[r * kMaxT + r] = 1.f;
+  }
+  Bufs b = pl->bufs;
+  Job j;
+  memset(&j, 0, sizeof(j));
+  j.X = X;
+  float* y1 = (float*)(pl->ws + pl->lay.ybuf);
+  j.Y1 = y1;
+  Ctrl c;
+  cudaError_t e = cudaMemcpy(&c, b.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost);
+  c.k = 0;
+  c.done = 0;
+  c.f_inv_mu = 1.f;
+  std::vector<float> gred(kMaxT * kMaxT);
+  if (e == cudaSuccess) e = cudaMemcpy(b.ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b.job, &j, sizeof(Job), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b.eig->V32, v32.data(), sizeof(float) * kMaxT * kMaxT, cudaMemcpyHostToDevice);
+  void* a_pass[] = {&b};
+  if (e == cudaSuccess) e = launch(pl->ks.pass[PM_GRAM], dim3(pl->lay.grid), dim3(kPassThreads), a_pass, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemcpy(gred.data(), b.red->G, sizeof(float) * kMaxT * kMaxT, cudaMemcpyDeviceToHost);
+  std::vector<double> gh((size_t)T * T);
+  for (int r = 0; r < T; ++r)
+    for (int cc = 0; cc < T; ++cc) gh[r * T + cc] = gred[r * kMaxT + cc];
+  if (e == cudaSuccess) e = cudaMemcpy(G, gh.data(), sizeof(double) * T * T, cudaMemcpyHostToDevice);
+  rpca_plan_destroy(pl);
+  return cuda_status(e);
+}
+
+rpca_status rpca_eig(const double* G, int32_t T, double* evals, double* evecs, void* stream) {
+  if (!G || !evals || !evecs || T < 1) return RPCA_ERR_ARG;
+  if (T > RPCA_MAX_T) return RPCA_ERR_UNSUPPORTED;
+  rpca_params p;
+  rpca_params_default(&p, 1, T);
+  p.drive = RPCA_DRIVE_HOST;
+  rpca_plan_t pl = nullptr;
+  rpca_status st = rpca_plan_create(&p, nullptr, 0, &pl);
+  if (st != RPCA_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  Bufs b = pl->bufs;
+  int flags = EF_RAW;
+  cudaGraphConditionalHandle h = 0;
+  int use_cond = 0;
+  double *ev = nullptr, *vv = nullptr;
+  cudaError_t e = cudaMalloc(&ev, sizeof(double) * T);
+  if (e == cudaSuccess) e = cudaMalloc(&vv, sizeof(double) * T * T);
+  void* args[] = {&b, &flags, &h, &use_cond, (void*)&G, &vv, &ev};
+  if (e == cudaSuccess) e = launch(pl->ks.eig64, dim3(1), dim3(pl->ks.eig_threads), args, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  std::vector<double> evh(T), vvh((size_t)T * T), evs(T), vvs((size_t)T * T);
+  if (e == cudaSuccess) e = cudaMemcpy(evh.data(), ev, sizeof(double) * T, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(vvh.data(), vv, sizeof(double) * T * T, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) {
+    std::vector<int> idx(T);
+    for (int i = 0; i < T; ++i) idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) { return evh[a] > evh[c]; });
+    for (int i = 0; i < T; ++i) {
+      evs[i] = evh[idx[i]];
+      for (int r = 0; r < T; ++r) vvs[r * T + i] = vvh[r * T + idx[i]];
+    }
+    e = cudaMemcpy(evals, evs.data(), sizeof(double) * T, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(evecs, vvs.data(), sizeof(double) * T * T, cudaMemcpyHostToDevice);
+  }
+  if (ev) cudaFree(ev);
+  if (vv) cudaFree(vv);
+  rpca_plan_destroy(pl);
+  return cuda_status(e);
+}
+
+}  // extern "C"

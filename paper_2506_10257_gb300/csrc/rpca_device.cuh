@@ -1,0 +1,113 @@
+// rpca_device.cuh -- device side of the GB300 PCP solver (kernels + shared state).
+//
+// One iteration of the augmented-Lagrangian method (Sec. II-A, Eq. 4-6) on the
+// m x T Casorati matrix X (frame-major: element (p, t) at X[t*m + p]):
+//
+//   Z   = X - S + Y/mu                       (argument of Eq. 4)
+//   L   = D_{1/mu}(Z) = Z - Z Wbar,  Wbar = V diag(min(1, tau/sigma)) V^T,
+//         with Z^T Z = V diag(sigma^2) V^T, tau = 1/mu      (Eq. 4 through the Gram)
+//   R   = X - L + Y/mu  (= S + Z Wbar)       (argument of Eq. 5)
+//   S'  = shrink_{lambda/mu}(R)              (Eq. 5)
+//   Y'  = Y + mu (X - L - S') = mu * clip(R, +-lambda/mu)   (Eq. 6)
+//   E   = X - L - S' = clip(R) - Y/mu        (stopping test, Sec. II-A)
+//
+// The identities on the right are exact rearrangements (R - S' = clip(R)).
+// The fused pass computes all of that per pixel row in one sweep over
+// X, S, Y, and in the same sweep accumulates the Gram of the NEXT iteration's
+// Z' = X - S' + Y'/mu' in the basis V of the current eigenvectors, so the
+// eigen-decomposition of the next iteration starts from a nearly diagonal
+// matrix whose FP32 accumulation error is relative to each eigenvalue.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rpca {
+
+constexpr int kMaxT = 32;            // largest frame count of this build
+constexpr int kPassThreads = 256;    // one pixel per thread per tile
+constexpr int kTile = kPassThreads;  // pixels per CTA tile
+constexpr int kGroup = 16;           // CTAs per first-level reduction group
+constexpr int kMaxGroups = 64;
+
+// Pass kinds.
+enum PassMode { PM_INIT = 0, PM_FUSED = 1, PM_UPDATE = 2, PM_GRAM = 3 };
+// Eig-kernel phases.
+enum EigFlags { EF_INIT = 1, EF_CHECK = 2, EF_EIG = 4 };
+
+// Iteration control block (device resident, one per plan).
+struct Ctrl {
+  int k;             // completed iterations
+  int done;          // 1 once converged, out of iterations or failed
+  int status;        // rpca_status
+  int rank;          // singular values above tau in the last SVT
+  int sweeps;        // Jacobi sweeps of the last eigensolve
+  int total_sweeps;  // over the whole solve
+  int max_iter;
+  int schedule;      // 0 IALM, 1 FIXED_L1
+  double mu_cur;     // mu of the next pass (iteration k+1)
+  double mu_nxt;     // mu of iteration k+2 (forms Z' in the fused pass)
+  double mu_max;
+  double lambda;
+  double rho;
+  double mu0_scale;
+  double mu_max_factor;
+  double tol;
+  double normX2;     // ||X||_F^2
+  double normX;      // ||X||_F
+  double normX1;     // sum |X_ij|
+  double resid;      // relative residual of iteration k
+  double jacobi_eps; // graded off-diagonal threshold of the Jacobi sweeps
+  int warm_sweeps;   // sweep cap once warm started
+  int cold_sweeps;   // sweep cap of the first eigensolve
+  // FP32 copies used by the passes (rounded once from the FP64 values).
+  float f_mu, f_inv_mu, f_gamma, f_inv_mu_nxt;
+  // Device-side timing of the solve (globaltimer, ns): fused/update passes
+  // after the first, eigen-steps, and the init pass.
+  unsigned long long pass_ns, pass_cnt, eig_ns, eig_cnt, init_ns;
+};
+
+// Eigen data handed from the eig kernel to the passes.
+struct EigState {
+  float Wbar[kMaxT * kMaxT];   // row-major T x T (row t, col j)
+  float V32[kMaxT * kMaxT];    // basis of the next rotated Gram, row-major
+  double evals[kMaxT];
+};
+
+// Cross-CTA reduction state (two levels, last-arriving CTA reduces).
+struct RedState {
+  float G[kMaxT * kMaxT];      // final Gram (row-major), written by the last CTA
+  double e2;                   // sum of E^2 (or ||X||_F^2 in the init pass)
+  double l1;                   // sum |X| (init pass)
+  unsigned long long t_start;  // earliest CTA start of the last pass (globaltimer)
+  unsigned long long t_end;    // end of its final reduction
+  unsigned int cnt[kMaxGroups + 1];
+};
+
+// Pointers of the current solve (written by a tiny kernel before each graph
+// launch, so one instantiated graph serves every call).
+struct Job {
+  const float* X;
+  float* S;
+  float* Y0;        // dual ping-pong buffer 0 (the caller's L buffer)
+  float* Y1;        // dual ping-pong buffer 1 (workspace)
+  float* L;
+  uint8_t* mask;
+  float theta;
+};
+
+struct Bufs {
+  Ctrl* ctrl;
+  EigState* eig;
+  RedState* red;
+  Job* job;
+  float* gram_part;    // [grid][T*T]
+  float* group_part;   // [ngroups][T*T]
+  double* scal_part;   // [grid][2]
+  double* gscal_part;  // [ngroups][2]
+  int64_t m;
+  int T;
+  int grid;
+  int ngroups;
+};
+
+}  // namespace rpca

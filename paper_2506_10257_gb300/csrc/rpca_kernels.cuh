@@ -1,0 +1,670 @@
+// rpca_kernels.cuh -- CUDA kernels of the PCP iteration (SIMT FP32 passes,
+// one-CTA Jacobi eigensolve).  See rpca_device.cuh for the algebra.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include "rpca_device.cuh"
+
+namespace rpca {
+
+// Status codes mirrored from rpca.h (kept numeric here to avoid a host header).
+constexpr int ST_OK = 0, ST_NOT_CONVERGED = 1, ST_ERR_NONFINITE = -6;
+
+// Z = X - S + Y/mu, formed identically wherever it is needed, so that the Gram
+// accumulated in one pass belongs to exactly the Z the next pass uses.
+__device__ __forceinline__ float form_z(float x, float s, float y, float inv_mu) {
+  return (x - s) + y * inv_mu;
+}
+
+// Jacobi round-robin pairing (circle method) on n indices, round r in [0, n-1).
+__device__ __forceinline__ void rr_pair(int r, int i, int n, int& a, int& b) {
+  const int k = n - 1;
+  if (i == 0) {
+    a = 0;
+    b = (r % k) + 1;
+  } else {
+    a = ((r + i) % k) + 1;
+    b = ((r - i + k) % k) + 1;
+  }
+}
+
+// Layout of the 4x4 register blocks that accumulate the upper triangle of a
+// TB x TB Gram; NGRP thread groups split the pixels of a tile.
+template <int TB>
+struct GramMap {
+  static constexpr int NB = TB / 4;
+  static constexpr int NBLK = NB * (NB + 1) / 2;
+  static constexpr int NGRP = (NBLK * 64 <= kPassThreads)   ? 64
+                              : (NBLK * 32 <= kPassThreads) ? 32
+                              : (NBLK * 16 <= kPassThreads) ? 16
+                              : (NBLK * 8 <= kPassThreads)  ? 8
+                                                            : 4;
+  static_assert(TB % 4 == 0, "bucket must be a multiple of 4");
+  static_assert(NBLK * NGRP <= kPassThreads, "gram blocks exceed the CTA");
+};
+
+__device__ __forceinline__ void blk_coords(int blk, int nb, int& bi, int& bj) {
+  bi = 0;
+  bj = 0;
+  for (int i = 0; i < nb; ++i) {
+    const int len = nb - i;
+    if (blk < len) {
+      bi = i;
+      bj = i + blk;
+      return;
+    }
+    blk -= len;
+  }
+}
+
+__device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
+  const float y = v - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Per-pixel pass.  MODE:
+//   PM_INIT   Gram of X (standard basis), ||X||_F^2, ||X||_1
+//   PM_FUSED  Eq. 4-6 update of S, Y + residual + Gram of the next Z in basis V
+//   PM_UPDATE Eq. 4-6 update of S, Y + residual (no Gram)
+//   PM_GRAM   Gram of the current Z in basis V (no update)
+// One thread owns one pixel row (its T frames) of a 256-pixel tile; CTAs
+// stride over tiles; partial Grams and scalars are reduced across CTAs by the
+// last CTA to arrive (two levels, fixed summation order => deterministic).
+// ---------------------------------------------------------------------------
+template <int TB, int MODE>
+__global__ void __launch_bounds__(kPassThreads) pass_kernel(Bufs b) {
+  constexpr bool kGram = (MODE != PM_UPDATE);
+  constexpr int ZS = TB + 4;  // staged row stride in floats (16-byte aligned rows)
+  using GM = GramMap<TB>;
+  __shared__ __align__(16) float sW[TB * TB];
+  __shared__ __align__(16) float sV[TB * TB];
+  __shared__ __align__(16) float sZ[kTile * ZS];
+  __shared__ double sRed[2][kPassThreads / 32];
+  __shared__ int sLast;
+
+  const Ctrl* ctrl = b.ctrl;
+  if (ctrl->done) return;
+  const int tid = threadIdx.x;
+  if (tid == 0) atomicMin(&b.red->t_start, gtimer());
+  const int T = b.T;
+  const int64_t m = b.m;
+  const Job job = *b.job;
+  const int kc = ctrl->k;
+  const bool first = (kc == 0);
+  const float f_mu = ctrl->f_mu, inv_mu = ctrl->f_inv_mu, gamma = ctrl->f_gamma;
+  const float inv_mu_nxt = ctrl->f_inv_mu_nxt;
+  const float* Yin = (kc & 1) ? job.Y1 : job.Y0;
+  float* Yout = (kc & 1) ? job.Y0 : job.Y1;
+
+  if (MODE != PM_INIT) {
+    for (int i = tid; i < TB * TB; i += kPassThreads) {
+      const int r = i / TB, c = i % TB;
+      const bool in = (r < T && c < T);
+      sW[i] = in ? b.eig->Wbar[r * kMaxT + c] : 0.f;
+      sV[i] = in ? b.eig->V32[r * kMaxT + c] : 0.f;
+    }
+  }
+  __syncthreads();
+
+  const bool gthr = kGram && (tid < GM::NBLK * GM::NGRP);
+  const int gblk = tid % GM::NBLK, ggrp = tid / GM::NBLK;
+  int bi, bj;
+  blk_coords(gblk, GM::NB, bi, bj);
+  float acc[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) acc[i] = 0.f;
+  float e2 = 0.f, l1 = 0.f;
+
+  const int64_t ntiles = (m + kTile - 1) / kTile;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t p = tile * kTile + tid;
+    const bool valid = p < m;
+    float zt[TB];
+    if (MODE == PM_INIT) {
+#pragma unroll
+      for (int t = 0; t < TB; ++t) {
+        const float x = (valid && t < T) ? job.X[t * m + p] : 0.f;
+        zt[t] = x;
+        e2 = fmaf(x, x, e2);
+        l1 += fabsf(x);
+      }
+    } else {
+      float x[TB], s[TB], d[TB], z[TB];
+#pragma unroll
+      for (int t = 0; t < TB; ++t) {
+        const bool in = valid && t < T;
+        x[t] = in ? job.X[t * m + p] : 0.f;
+        s[t] = (in && !first) ? job.S[t * m + p] : 0.f;
+        const float y = (in && !first) ? Yin[t * m + p] : 0.f;
+        d[t] = y * inv_mu;
+        z[t] = form_z(x[t], s[t], y, inv_mu);
+      }
+      if (MODE == PM_GRAM) {
+#pragma unroll
+        for (int j = 0; j < TB; ++j) zt[j] = 0.f;
+#pragma unroll
+        for (int t = 0; t < TB; ++t) {
+#pragma unroll
+          for (int j = 0; j < TB; ++j) zt[j] = fmaf(z[t], sV[t * TB + j], zt[j]);
+        }
+      } else {
+        float q[TB];
+#pragma unroll
+        for (int j = 0; j < TB; ++j) q[j] = 0.f;
+#pragma unroll
+        for (int t = 0; t < TB; ++t) {
+#pragma unroll
+          for (int j = 0; j < TB; ++j) q[j] = fmaf(z[t], sW[t * TB + j], q[j]);
+        }
+#pragma unroll
+        for (int t = 0; t < TB; ++t) {
+          if (t < T) {
+            const float r = s[t] + q[t];                       // X - L + Y/mu
+            const float c = fminf(fmaxf(r, -gamma), gamma);    // clip to +-lambda/mu
+            const float sn = r - c;                            // Eq. 5
+            const float yn = f_mu * c;                         // Eq. 6
+            const float e = c - d[t];                          // X - L - S'
+            e2 = fmaf(e, e, e2);
+            if (valid) {
+              job.S[t * m + p] = sn;
+              Yout[t * m + p] = yn;
+            }
+            z[t] = valid ? form_z(x[t], sn, yn, inv_mu_nxt) : 0.f;
+          }
+        }
+        if (MODE == PM_FUSED) {
+#pragma unroll
+          for (int j = 0; j < TB; ++j) zt[j] = 0.f;
+#pragma unroll
+          for (int t = 0; t < TB; ++t) {
+#pragma unroll
+            for (int j = 0; j < TB; ++j) zt[j] = fmaf(z[t], sV[t * TB + j], zt[j]);
+          }
+        }
+      }
+    }
+    if (kGram) {
+      float4* dst = reinterpret_cast<float4*>(&sZ[tid * ZS]);
+#pragma unroll
+      for (int j4 = 0; j4 < TB / 4; ++j4)
+        dst[j4] = make_float4(zt[4 * j4], zt[4 * j4 + 1], zt[4 * j4 + 2], zt[4 * j4 + 3]);
+      __syncthreads();
+      if (gthr) {
+        for (int pp = ggrp; pp < kTile; pp += GM::NGRP) {
+          const float4 a = *reinterpret_cast<const float4*>(&sZ[pp * ZS + 4 * bi]);
+          const float4 c = *reinterpret_cast<const float4*>(&sZ[pp * ZS + 4 * bj]);
+          const float av[4] = {a.x, a.y, a.z, a.w};
+          const float cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u * 4 + v] = fmaf(av[u], cv[v], acc[u * 4 + v]);
+        }
+      }
+      __syncthreads();
+    }
+  }
+
+  // ---- CTA partials ----
+  const int TT = T * T;
+  if (kGram) {
+    float* red = sZ;  // [NGRP][NBLK][16]
+    if (gthr) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) red[(ggrp * GM::NBLK + gblk) * 16 + i] = acc[i];
+    }
+    __syncthreads();
+    for (int e = tid; e < GM::NBLK * 16; e += kPassThreads) {
+      float sum = 0.f;
+      for (int g = 0; g < GM::NGRP; ++g) sum += red[g * GM::NBLK * 16 + e];
+      int ebi, ebj;
+      blk_coords(e / 16, GM::NB, ebi, ebj);
+      const int a = 4 * ebi + (e % 16) / 4, c = 4 * ebj + (e % 4);
+      if (a < T && c < T) {
+        b.gram_part[(int64_t)blockIdx.x * TT + a * T + c] = sum;
+        b.gram_part[(int64_t)blockIdx.x * TT + c * T + a] = sum;
+      }
+    }
+  }
+  {
+    double v0 = warp_sum_d((double)e2), v1 = warp_sum_d((double)l1);
+    if ((tid & 31) == 0) {
+      sRed[0][tid >> 5] = v0;
+      sRed[1][tid >> 5] = v1;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double s0 = 0, s1 = 0;
+      for (int w = 0; w < kPassThreads / 32; ++w) {
+        s0 += sRed[0][w];
+        s1 += sRed[1][w];
+      }
+      b.scal_part[2 * blockIdx.x] = s0;
+      b.scal_part[2 * blockIdx.x + 1] = s1;
+    }
+  }
+
+  // ---- level 1: last CTA of each group of kGroup CTAs ----
+  __threadfence();
+  __syncthreads();
+  const int grp = blockIdx.x / kGroup;
+  const int c0 = grp * kGroup;
+  const int c1 = min(c0 + kGroup, (int)gridDim.x);
+  if (tid == 0) {
+    const unsigned t = atomicAdd(&b.red->cnt[grp], 1u);
+    sLast = (t == (unsigned)(c1 - c0 - 1));
+  }
+  __syncthreads();
+  if (!sLast) return;
+  __threadfence();
+  if (kGram) {
+    for (int e = tid; e < TT; e += kPassThreads) {
+      float s = 0.f, comp = 0.f;
+      for (int c = c0; c < c1; ++c) kahan_add(s, comp, __ldcg(&b.gram_part[(int64_t)c * TT + e]));
+      b.group_part[grp * TT + e] = s;
+    }
+  }
+  if (tid == 0) {
+    double s0 = 0, s1 = 0;
+    for (int c = c0; c < c1; ++c) {
+      s0 += __ldcg(&b.scal_part[2 * c]);
+      s1 += __ldcg(&b.scal_part[2 * c + 1]);
+    }
+    b.gscal_part[2 * grp] = s0;
+    b.gscal_part[2 * grp + 1] = s1;
+    b.red->cnt[grp] = 0u;
+  }
+  // ---- level 2: last group reducer writes the final sums ----
+  __threadfence();
+  __syncthreads();
+  const int ngroups = (gridDim.x + kGroup - 1) / kGroup;
+  if (tid == 0) {
+    const unsigned t = atomicAdd(&b.red->cnt[kMaxGroups], 1u);
+    sLast = (t == (unsigned)(ngroups - 1));
+  }
+  __syncthreads();
+  if (!sLast) return;
+  __threadfence();
+  if (kGram) {
+    for (int e = tid; e < TT; e += kPassThreads) {
+      float s = 0.f, comp = 0.f;
+      for (int g = 0; g < ngroups; ++g) kahan_add(s, comp, __ldcg(&b.group_part[g * TT + e]));
+      const int a = e / T, c = e % T;
+      b.red->G[a * kMaxT + c] = s;
+    }
+  }
+  if (tid == 0) {
+    double s0 = 0, s1 = 0;
+    for (int g = 0; g < ngroups; ++g) {
+      s0 += __ldcg(&b.gscal_part[2 * g]);
+      s1 += __ldcg(&b.gscal_part[2 * g + 1]);
+    }
+    b.red->e2 = s0;
+    b.red->l1 = s1;
+    b.red->cnt[kMaxGroups] = 0u;
+    b.red->t_end = gtimer();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Iteration control + eigensolve, one CTA.
+//   EF_INIT  : ||X|| from the init pass; X == 0 finishes with L = S = 0
+//   EF_CHECK : residual test of the iteration just done (Sec. II-A), mu update
+//   EF_EIG   : cyclic Jacobi on the rotated Gram (warm start from V), then
+//              sigma = sqrt(lambda), the sigma > tau decision and
+//              Wbar = V diag(min(1, tau/sigma)) V^T (FP64 decisions)
+//   EF_RAW   : decompose an external FP64 matrix only (kernel-level tests)
+// Real is the arithmetic of the Jacobi rotations (float or double).
+// ---------------------------------------------------------------------------
+enum { EF_RAW = 8 };
+
+__device__ __forceinline__ void set_cond(cudaGraphConditionalHandle h, int use, unsigned v) {
+  if (use) cudaGraphSetConditional(h, v);
+}
+
+__device__ __forceinline__ void refresh_f32(Ctrl* c) {
+  c->f_mu = (float)c->mu_cur;
+  c->f_inv_mu = (float)(1.0 / c->mu_cur);
+  c->f_gamma = (float)(c->lambda / c->mu_cur);
+  c->f_inv_mu_nxt = (float)(1.0 / c->mu_nxt);
+}
+
+template <int TB, typename Real>
+__global__ void __launch_bounds__(512) eig_kernel(Bufs b, int flags, cudaGraphConditionalHandle h,
+                                                  int use_cond, const double* Gin, double* Vout,
+                                                  double* evals_out) {
+  constexpr int NP = TB / 2;
+  constexpr int LD = TB + 1;
+  __shared__ Real sG[2][TB * LD];
+  __shared__ Real sV[2][TB * LD];
+  __shared__ Real sWt[TB][2];
+  __shared__ int sI[TB][2];
+  __shared__ int sAct[TB];
+  __shared__ double sEv[TB];
+  __shared__ double sGd[TB];
+  __shared__ int sFlag;
+  __shared__ double sTau;
+
+  Ctrl* ctrl = b.ctrl;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int T = b.T;
+  const bool raw = (flags & EF_RAW) != 0;
+  const unsigned long long t0 = gtimer();
+
+  if (!raw) {
+    if (tid == 0) {
+      sFlag = ctrl->done;
+      // account the pass that just ran (the first iteration's pass reads no S, Y
+      // and is left out of the steady-state average)
+      const unsigned long long ts = b.red->t_start, te = b.red->t_end;
+      if (ts != ~0ull && te > ts) {
+        if (flags & EF_INIT) {
+          ctrl->init_ns = te - ts;
+        } else if ((flags & EF_CHECK) && ctrl->k >= 1) {
+          ctrl->pass_ns += te - ts;
+          ctrl->pass_cnt += 1;
+        }
+      }
+      b.red->t_start = ~0ull;
+    }
+    __syncthreads();
+    if (sFlag) {
+      if (tid == 0) set_cond(h, use_cond, 0u);
+      return;
+    }
+    if (flags & EF_CHECK) {
+      if (tid == 0) {
+        const int k = ctrl->k + 1;
+        ctrl->k = k;
+        const double resid = sqrt(b.red->e2) / ctrl->normX;
+        ctrl->resid = resid;
+        int done = 0, st = ST_OK;
+        if (!isfinite(resid)) {
+          done = 1;
+          st = ST_ERR_NONFINITE;
+        } else if (resid <= ctrl->tol) {
+          done = 1;
+        } else if (k >= ctrl->max_iter) {
+          done = 1;
+          st = ST_NOT_CONVERGED;
+        }
+        if (!done) {
+          ctrl->mu_cur = ctrl->mu_nxt;
+          ctrl->mu_nxt = (ctrl->schedule == 0) ? fmin(ctrl->rho * ctrl->mu_cur, ctrl->mu_max) : ctrl->mu_cur;
+          refresh_f32(ctrl);
+        }
+        ctrl->done = done;
+        ctrl->status = st;
+        sFlag = done;
+      }
+      __syncthreads();
+      if (sFlag) {
+        if (tid == 0) set_cond(h, use_cond, 0u);
+        return;
+      }
+    }
+    if (flags & EF_INIT) {
+      if (tid == 0) {
+        const double x2 = b.red->e2;
+        ctrl->normX2 = x2;
+        ctrl->normX = sqrt(x2);
+        ctrl->normX1 = b.red->l1;
+        int done = 0;
+        if (!isfinite(x2)) {
+          done = 1;
+          ctrl->status = ST_ERR_NONFINITE;
+        } else if (x2 == 0.0) {
+          done = 1;
+          ctrl->status = ST_OK;
+          ctrl->resid = 0.0;
+        }
+        ctrl->done = done;
+        sFlag = done;
+      }
+      __syncthreads();
+      if (sFlag) {
+        if (tid == 0) set_cond(h, use_cond, 0u);
+        return;
+      }
+    }
+    if (!(flags & EF_EIG)) {
+      if (tid == 0) set_cond(h, use_cond, 1u);
+      return;
+    }
+  }
+
+  // ---- load the Gram and the basis ----
+  const bool cold = raw || (flags & EF_INIT);
+  for (int i = tid; i < TB * TB; i += nthr) {
+    const int r = i / TB, c = i % TB;
+    const bool in = (r < T && c < T);
+    Real g = 0;
+    if (in) g = Gin ? (Real)Gin[r * T + c] : (Real)b.red->G[r * kMaxT + c];
+    sG[0][r * LD + c] = g;
+    Real v = (r == c) ? (Real)1 : (Real)0;
+    if (!cold && in) v = (Real)b.eig->V32[r * kMaxT + c];
+    sV[0][r * LD + c] = v;
+  }
+  if (tid < TB) sAct[tid] = 0;
+  __syncthreads();
+
+  // ---- cyclic Jacobi, parallel round-robin ordering ----
+  int cur = 0;
+  const Real eps = raw ? (Real)(sizeof(Real) == 8 ? 1e-15 : 1e-7) : (Real)ctrl->jacobi_eps;
+  const int max_sweeps = raw ? 40 : (cold ? ctrl->cold_sweeps : ctrl->warm_sweeps);
+  int sweeps = 0;
+  while (sweeps < max_sweeps) {
+    int need = 0;
+    for (int i = tid; i < TB * TB; i += nthr) {
+      const int r = i / TB, c = i % TB;
+      if (r < c) {
+        const Real apq = sG[cur][r * LD + c];
+        if (apq != (Real)0) {
+          const Real app = sG[cur][r * LD + r], aqq = sG[cur][c * LD + c];
+          if (fabs(apq) > eps * sqrt(fabs(app * aqq))) need = 1;
+        }
+      }
+    }
+    if (!__syncthreads_or(need)) break;
+    ++sweeps;
+    for (int rnd = 0; rnd < TB - 1; ++rnd) {
+      int act = 0;
+      if (tid < NP) {
+        int pa, pb;
+        rr_pair(rnd, tid, TB, pa, pb);
+        const int p = min(pa, pb), q = max(pa, pb);
+        const Real app = sG[cur][p * LD + p], aqq = sG[cur][q * LD + q], apq = sG[cur][p * LD + q];
+        Real c = 1, s = 0;
+        if (apq != (Real)0 && fabs(apq) > eps * sqrt(fabs(app * aqq))) {
+          act = 1;
+          const Real th = (aqq - app) / (2 * apq);
+          const Real t = copysign((Real)1, th) / (fabs(th) + sqrt((Real)1 + th * th));
+          c = (Real)1 / sqrt((Real)1 + t * t);
+          s = t * c;
+        }
+        // column p of J = (c at p, -s at q); column q of J = (s at p, c at q)
+        sI[p][0] = p;
+        sI[p][1] = q;
+        sWt[p][0] = c;
+        sWt[p][1] = -s;
+        sI[q][0] = p;
+        sI[q][1] = q;
+        sWt[q][0] = s;
+        sWt[q][1] = c;
+        sAct[p] = act;
+        sAct[q] = act;
+      }
+      if (!__syncthreads_or(act)) continue;
+      const int nxt = cur ^ 1;
+      for (int i = tid; i < 2 * TB * TB; i += nthr) {
+        if (i < TB * TB) {
+          const int a = i / TB, c = i % TB;
+          const int a0 = sI[a][0], a1 = sI[a][1], c0 = sI[c][0], c1 = sI[c][1];
+          const Real wa0 = sWt[a][0], wa1 = sWt[a][1], wc0 = sWt[c][0], wc1 = sWt[c][1];
+          Real v = wa0 * (wc0 * sG[cur][a0 * LD + c0] + wc1 * sG[cur][a0 * LD + c1]) +
+                   wa1 * (wc0 * sG[cur][a1 * LD + c0] + wc1 * sG[cur][a1 * LD + c1]);
+          if (a != c && a0 == c0 && a1 == c1 && sAct[a]) v = 0;  // the annihilated pair
+          sG[nxt][a * LD + c] = v;
+        } else {
+          const int j = i - TB * TB;
+          const int r = j / TB, a = j % TB;
+          sV[nxt][r * LD + a] = sV[cur][r * LD + sI[a][0]] * sWt[a][0] + sV[cur][r * LD + sI[a][1]] * sWt[a][1];
+        }
+      }
+      cur = nxt;
+      __syncthreads();
+    }
+  }
+
+  if (tid < TB) sEv[tid] = (double)sG[cur][tid * LD + tid];
+  __syncthreads();
+
+  if (raw) {
+    for (int i = tid; i < T * T; i += nthr) {
+      const int r = i / T, c = i % T;
+      Vout[r * T + c] = (double)sV[cur][r * LD + c];
+    }
+    if (tid < T) evals_out[tid] = sEv[tid];
+    if (tid == 0) ctrl->sweeps = sweeps;
+    return;
+  }
+
+  // ---- orthonormality refresh of the basis: V <- V (3I - V^T V)/2 ----
+  {
+    const int nxt = cur ^ 1;
+    // sG[nxt] <- V^T V  (T x T), then sV[nxt] <- V (1.5 I - 0.5 V^T V)
+    for (int i = tid; i < TB * TB; i += nthr) {
+      const int a = i / TB, c = i % TB;
+      Real s = 0;
+      for (int r = 0; r < TB; ++r) s += sV[cur][r * LD + a] * sV[cur][r * LD + c];
+      sG[nxt][a * LD + c] = (a == c ? (Real)1.5 : (Real)0) - (Real)0.5 * s;
+    }
+    __syncthreads();
+    for (int i = tid; i < TB * TB; i += nthr) {
+      const int r = i / TB, c = i % TB;
+      Real s = 0;
+      for (int a = 0; a < TB; ++a) s += sV[cur][r * LD + a] * sG[nxt][a * LD + c];
+      sV[nxt][r * LD + c] = s;
+    }
+    __syncthreads();
+    cur = nxt;
+  }
+
+  // ---- FP64 decisions: mu (first call), tau, sigma > tau, g ----
+  if (tid == 0) {
+    if (flags & EF_INIT) {
+      double lmax = 0.0;
+      for (int a = 0; a < T; ++a) lmax = fmax(lmax, sEv[a]);
+      double mu1;
+      if (ctrl->schedule == 0)
+        mu1 = ctrl->mu0_scale / sqrt(lmax);
+      else
+        mu1 = ((double)b.m * (double)T) / (4.0 * ctrl->normX1);
+      ctrl->mu_cur = mu1;
+      ctrl->mu_max = ctrl->mu_max_factor * mu1;
+      ctrl->mu_nxt = (ctrl->schedule == 0) ? fmin(ctrl->rho * mu1, ctrl->mu_max) : mu1;
+      ctrl->k = 0;
+      refresh_f32(ctrl);
+    }
+    sTau = 1.0 / ctrl->mu_cur;
+  }
+  __syncthreads();
+  int keep = 0;
+  if (tid < TB) {
+    const double sig = sqrt(fmax(sEv[tid], 0.0));
+    keep = (tid < T) && (sig > sTau);
+    sGd[tid] = keep ? sTau / sig : 1.0;
+  }
+  const int rank = __syncthreads_count(keep);
+
+  for (int i = tid; i < T * T; i += nthr) {
+    const int a = i / T, c = i % T;
+    Real s = 0;
+    for (int j = 0; j < T; ++j) s += sV[cur][a * LD + j] * (Real)sGd[j] * sV[cur][c * LD + j];
+    b.eig->Wbar[a * kMaxT + c] = (float)s;
+    b.eig->V32[a * kMaxT + c] = (float)sV[cur][a * LD + c];
+  }
+  if (tid < T) b.eig->evals[tid] = sEv[tid];
+  if (tid == 0) {
+    ctrl->rank = rank;
+    ctrl->sweeps = sweeps;
+    ctrl->total_sweeps += sweeps;
+    ctrl->eig_ns += gtimer() - t0;
+    ctrl->eig_cnt += 1;
+    set_cond(h, use_cond, 1u);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Final outputs: L = X - S - E with E = (Y_k - Y_{k-1})/mu_k (Eq. 6 rearranged),
+// and the bound-bubble mask: temporal mean of |L| >= theta (Sec. II-F).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) final_kernel(Bufs b) {
+  const Ctrl* ctrl = b.ctrl;
+  const Job job = *b.job;
+  const int T = b.T;
+  const int64_t m = b.m;
+  const int kc = ctrl->k;
+  const float inv_mu = ctrl->f_inv_mu;
+  const float* Yk = (kc & 1) ? job.Y1 : job.Y0;
+  const float* Ykm1 = (kc & 1) ? job.Y0 : job.Y1;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x) {
+    float acc = 0.f;
+    for (int t = 0; t < T; ++t) {
+      const int64_t i = t * m + p;
+      float l = 0.f;
+      if (kc == 0) {
+        job.S[i] = 0.f;
+      } else {
+        const float x = job.X[i], s = job.S[i];
+        const float yk = Yk[i];
+        const float ym = (kc >= 2) ? Ykm1[i] : 0.f;
+        l = (x - s) - (yk * inv_mu - ym * inv_mu);
+      }
+      job.L[i] = l;
+      acc += fabsf(l);
+    }
+    if (job.mask) job.mask[p] = (acc / (float)T >= job.theta) ? 1 : 0;
+  }
+}
+
+// Per-solve reset and pointer hand-off (runs before each graph launch).
+__global__ void begin_kernel(Bufs b, const float* X, float* L, float* S, uint8_t* mask, float theta) {
+  if (threadIdx.x == 0) {
+    Job* j = b.job;
+    j->X = X;
+    j->S = S;
+    j->Y0 = L;
+    j->L = L;
+    j->mask = mask;
+    j->theta = theta;
+    Ctrl* c = b.ctrl;
+    c->k = 0;
+    c->done = 0;
+    c->status = 0;
+    c->rank = 0;
+    c->sweeps = 0;
+    c->total_sweeps = 0;
+    c->resid = 0.0;
+    c->pass_ns = c->pass_cnt = c->eig_ns = c->eig_cnt = c->init_ns = 0ull;
+    b.red->t_start = ~0ull;
+    b.red->t_end = 0ull;
+  }
+}
+
+}  // namespace rpca

@@ -1,0 +1,248 @@
+"""Python binding of librpca.so (ctypes; argument marshalling only).
+
+Every step of the solve runs in the CUDA library.  PyTorch provides device
+memory (the workspace, outputs) and streams.  There is no CPU fallback: if
+the library is missing or no GPU is present, these calls raise.
+
+Layout convention: a window is a (T, m) tensor of frames (frame t is row t,
+pixels contiguous), which is the frame-major Casorati matrix X (m x T) of the
+C ABI.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+# ---- C ABI mirrors (include/rpca.h) ----------------------------------------
+OK, NOT_CONVERGED, PENDING = 0, 1, 2
+ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_BUDGET, ERR_TIMEOUT, ERR_NONFINITE, ERR_UNSUPPORTED, ERR_NOTFOUND = \
+    -1, -2, -3, -4, -5, -6, -7, -8
+R32, C64 = 0, 1
+PREC_FP32, PREC_TF32X3, PREC_BF16X3, PREC_TF32 = 0, 1, 2, 3
+MU_IALM, MU_FIXED_L1 = 0, 1
+DRIVE_GRAPH, DRIVE_HOST = 0, 1
+MAX_T = 32
+
+EXPORTED = ["rpca_params_default", "rpca_workspace_size", "rpca_plan_create", "rpca_solve", "rpca_solve_host",
+            "rpca_plan_result", "rpca_plan_destroy", "rpca_status_str", "rpca_gram", "rpca_eig"]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("T", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("mu_schedule", ctypes.c_int32),
+                ("drive", ctypes.c_int32), ("max_iter", ctypes.c_int32),
+                ("lambda_", ctypes.c_double), ("mu0_scale", ctypes.c_double),
+                ("rho", ctypes.c_double), ("mu_max_factor", ctypes.c_double),
+                ("tol", ctypes.c_double)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("rank", ctypes.c_int32),
+                ("sweeps", ctypes.c_int32), ("resid", ctypes.c_double), ("mu", ctypes.c_double),
+                ("normX", ctypes.c_double), ("lambda_", ctypes.c_double), ("pass_us", ctypes.c_double),
+                ("eig_us", ctypes.c_double), ("init_us", ctypes.c_double), ("passes_timed", ctypes.c_int32),
+                ("eigs_timed", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class RpcaError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__(f"{what}: {status_str(status)} ({status})")
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load librpca.so (building it first if asked); raise if it cannot be loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"CUDA library not built: {path}")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
+    lib.rpca_params_default.argtypes = [ctypes.POINTER(Params), i64, i32]
+    lib.rpca_workspace_size.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_size_t)]
+    lib.rpca_plan_create.argtypes = [ctypes.POINTER(Params), vp, ctypes.c_size_t, ctypes.POINTER(vp)]
+    lib.rpca_solve.argtypes = [vp, vp, vp, vp, vp, f32, vp, ctypes.POINTER(Result)]
+    lib.rpca_solve_host.argtypes = [vp, vp, vp, vp, vp, f32, vp, ctypes.POINTER(Result)]
+    lib.rpca_plan_result.argtypes = [vp, ctypes.POINTER(Result)]
+    lib.rpca_plan_destroy.argtypes = [vp]
+    lib.rpca_plan_destroy.restype = None
+    lib.rpca_status_str.argtypes = [i32]
+    lib.rpca_status_str.restype = ctypes.c_char_p
+    lib.rpca_gram.argtypes = [vp, i64, i32, vp, vp, i32, vp]
+    lib.rpca_eig.argtypes = [vp, i32, vp, vp, vp]
+    _lib = lib
+    return lib
+
+
+def status_str(st: int) -> str:
+    return load().rpca_status_str(st).decode()
+
+
+def default_params(m: int, T: int, **kw) -> Params:
+    p = Params()
+    load().rpca_params_default(ctypes.byref(p), int(m), int(T))
+    for k, v in kw.items():
+        if k == "lam":
+            k = "lambda_"
+        if not hasattr(p, k):
+            raise TypeError(f"unknown parameter {k}")
+        setattr(p, k, v)
+    return p
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("rpca needs a CUDA device (no CPU fallback)")
+    return torch
+
+
+def _stream_handle(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Plan:
+    """A solver plan for windows of shape (T, m); owns a torch workspace."""
+
+    def __init__(self, m: int, T: int, **kw):
+        torch = _torch()
+        self.lib = load()
+        self.params = default_params(m, T, **kw)
+        nbytes = ctypes.c_size_t()
+        st = self.lib.rpca_workspace_size(ctypes.byref(self.params), ctypes.byref(nbytes))
+        if st != OK:
+            raise RpcaError(st, "rpca_workspace_size")
+        self.workspace = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device="cuda")
+        h = ctypes.c_void_p()
+        st = self.lib.rpca_plan_create(ctypes.byref(self.params), ctypes.c_void_p(self.workspace.data_ptr()),
+                                       nbytes.value, ctypes.byref(h))
+        if st != OK:
+            raise RpcaError(st, "rpca_plan_create")
+        self.handle = h
+        self.m, self.T = int(m), int(T)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.rpca_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, frames, L=None, S=None, mask=None, theta: float = 0.0, stream=None, wait: bool = True):
+        """Solve one window.  frames: (T, m) float32 CUDA tensor.
+
+        Returns (L, S, result) where result is a dict (None when wait=False).
+        """
+        torch = _torch()
+        if frames.dtype != torch.float32 or not frames.is_cuda or not frames.is_contiguous():
+            raise ValueError("frames must be a contiguous float32 CUDA tensor")
+        if tuple(frames.shape) != (self.T, self.m):
+            raise ValueError(f"frames shape {tuple(frames.shape)} != {(self.T, self.m)}")
+        if L is None:
+            L = torch.empty_like(frames)
+        if S is None:
+            S = torch.empty_like(frames)
+        res = Result()
+        st = self.lib.rpca_solve(self.handle, ctypes.c_void_p(frames.data_ptr()), ctypes.c_void_p(L.data_ptr()),
+                                 ctypes.c_void_p(S.data_ptr()),
+                                 ctypes.c_void_p(mask.data_ptr() if mask is not None else 0),
+                                 ctypes.c_float(theta), _stream_handle(stream),
+                                 ctypes.byref(res) if wait else None)
+        if st < 0:
+            raise RpcaError(st, "rpca_solve")
+        return L, S, (res.as_dict() if wait else None)
+
+    def solve_host(self, frames, L=None, S=None, mask=None, theta: float = 0.0, stream=None):
+        """Solve a window held in HOST memory (numpy arrays or CPU tensors, (T, m) float32).
+
+        The C library copies it to the device, solves, and copies L, S (and the
+        mask) back into the given host buffers.  Returns (L, S, result)."""
+        import numpy as np
+        F = np.ascontiguousarray(np.asarray(frames), dtype=np.float32)
+        if F.shape != (self.T, self.m):
+            raise ValueError(f"frames shape {F.shape} != {(self.T, self.m)}")
+        if L is None:
+            L = np.empty_like(F)
+        if S is None:
+            S = np.empty_like(F)
+        res = Result()
+        st = self.lib.rpca_solve_host(self.handle, ctypes.c_void_p(F.ctypes.data), ctypes.c_void_p(L.ctypes.data),
+                                      ctypes.c_void_p(S.ctypes.data),
+                                      ctypes.c_void_p(mask.ctypes.data if mask is not None else 0),
+                                      ctypes.c_float(theta), _stream_handle(stream), ctypes.byref(res))
+        if st < 0:
+            raise RpcaError(st, "rpca_solve_host")
+        return L, S, res.as_dict()
+
+    def result(self) -> dict:
+        res = Result()
+        st = self.lib.rpca_plan_result(self.handle, ctypes.byref(res))
+        if st != OK:
+            raise RpcaError(st, "rpca_plan_result")
+        return res.as_dict()
+
+
+def solve(frames, **kw):
+    """One-shot solve of a (T, m) CUDA window; returns (L, S, result)."""
+    T, m = frames.shape
+    mask = kw.pop("mask", None)
+    theta = kw.pop("theta", 0.0)
+    plan = Plan(m, T, **kw)
+    try:
+        return plan.solve(frames, mask=mask, theta=theta)
+    finally:
+        plan.close()
+
+
+def gram(frames, V=None, precision: int = PREC_FP32):
+    """G = (Z V)^T (Z V) with Z = frames.T; returns a (T, T) float64 CUDA tensor."""
+    torch = _torch()
+    T, m = frames.shape
+    G = torch.empty((T, T), dtype=torch.float64, device="cuda")
+    vptr = 0
+    if V is not None:
+        V = V.to(device="cuda", dtype=torch.float32).contiguous()
+        vptr = V.data_ptr()
+    st = load().rpca_gram(ctypes.c_void_p(frames.data_ptr()), m, T, ctypes.c_void_p(vptr),
+                          ctypes.c_void_p(G.data_ptr()), precision, _stream_handle(None))
+    if st != OK:
+        raise RpcaError(st, "rpca_gram")
+    return G
+
+
+def eig(G):
+    """Eigen-decomposition of a symmetric (T, T) float64 CUDA tensor (FP64 Jacobi).
+
+    Returns (evals descending, evecs as columns)."""
+    torch = _torch()
+    G = G.to(device="cuda", dtype=torch.float64).contiguous()
+    T = G.shape[0]
+    ev = torch.empty(T, dtype=torch.float64, device="cuda")
+    V = torch.empty((T, T), dtype=torch.float64, device="cuda")
+    st = load().rpca_eig(ctypes.c_void_p(G.data_ptr()), T, ctypes.c_void_p(ev.data_ptr()),
+                         ctypes.c_void_p(V.data_ptr()), _stream_handle(None))
+    if st != OK:
+        raise RpcaError(st, "rpca_eig")
+    return ev, V

@@ -1,0 +1,199 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU FP64 oracle.
+
+Tolerances: relative Frobenius error of L and S <= 1e-5 for the FP32 path and
+bound-bubble mask Dice >= 0.999 against the oracle's mask (same threshold on
+both sides).  Kernel-level steps are checked against plain FP64 definitions.
+"""
+import numpy as np
+import pytest
+
+from oracle import rpca_oracle as O
+from paper_2506_10257_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def rp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_10257_gb300 import rpca
+    rpca.load()
+    return rpca
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def gpu_solve(rp, frames, theta=None, **kw):
+    X = torch.from_numpy(np.ascontiguousarray(frames, dtype=np.float32)).cuda()
+    T, m = X.shape
+    plan = rp.Plan(m, T, **kw)
+    mask = torch.zeros(m, dtype=torch.uint8, device="cuda") if theta is not None else None
+    L, S, res = plan.solve(X, mask=mask, theta=0.0 if theta is None else theta)
+    torch.cuda.synchronize()
+    plan.close()
+    out = dict(L=L.cpu().numpy(), S=S.cpu().numpy(), res=res)
+    if mask is not None:
+        out["mask"] = mask.cpu().numpy().astype(bool)
+    return out
+
+
+# ---- kernel-level steps -------------------------------------------------------
+
+@pytest.mark.parametrize("m,T", [(8, 4), (33, 5), (4096, 20), (1000, 20), (300, 7), (70000, 32), (257, 1)])
+def test_gram_matches_fp64(rp, m, T):
+    F = synth.random_dense(10 + m + T, m, T)
+    G = rp.gram(torch.from_numpy(F).cuda()).cpu().numpy()
+    Z = F.T.astype(np.float64)
+    want = Z.T @ Z
+    assert np.abs(G - want).max() <= 2e-6 * np.abs(want).max()
+
+
+def test_gram_in_rotated_basis(rp):
+    m, T = 5000, 20
+    F = synth.random_dense(3, m, T)
+    V, _ = np.linalg.qr(np.random.default_rng(4).standard_normal((T, T)))
+    V32 = V.astype(np.float32)
+    G = rp.gram(torch.from_numpy(F).cuda(), V=torch.from_numpy(V32)).cpu().numpy()
+    Zr = F.T.astype(np.float64) @ V32.astype(np.float64)
+    want = Zr.T @ Zr
+    assert np.abs(G - want).max() <= 2e-6 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("T", [2, 5, 20, 32])
+def test_eig_matches_lapack(rp, T):
+    rng = np.random.default_rng(T)
+    A = rng.standard_normal((3 * T, T))
+    G = A.T @ A
+    ev, V = rp.eig(torch.from_numpy(G).cuda())
+    ev, V = ev.cpu().numpy(), V.cpu().numpy()
+    want = np.linalg.eigvalsh(G)[::-1]
+    np.testing.assert_allclose(ev, want, rtol=1e-12, atol=1e-12 * want[0])
+    np.testing.assert_allclose(V.T @ V, np.eye(T), atol=1e-12)
+    np.testing.assert_allclose(G @ V, V * ev, atol=1e-11 * want[0])
+
+
+def test_eig_degenerate_spectrum(rp):
+    T = 12
+    rng = np.random.default_rng(9)
+    Q, _ = np.linalg.qr(rng.standard_normal((T, T)))
+    lam = np.array([5.0, 5.0, 5.0, 2.0, 2.0, 1.0, 0, 0, 0, 0, 0, 0])
+    G = (Q * lam) @ Q.T
+    ev, V = rp.eig(torch.from_numpy(G).cuda())
+    ev, V = ev.cpu().numpy(), V.cpu().numpy()
+    np.testing.assert_allclose(ev, lam, atol=1e-12)
+    np.testing.assert_allclose(V.T @ V, np.eye(T), atol=1e-12)
+    np.testing.assert_allclose(G @ V, V * ev, atol=1e-11)
+
+
+# ---- full solve -----------------------------------------------------------------
+
+def _check_parity(gpu, ref, tol=FP32_TOL):
+    eL, eS = rel(gpu["L"], ref.L), rel(gpu["S"], ref.S)
+    assert eL <= tol and eS <= tol, (eL, eS, gpu["res"], ref.iters)
+    assert abs(gpu["res"]["iters"] - ref.iters) <= 1
+
+
+def test_solve_64x64x20_matches_oracle(rp):
+    w = synth.make_preset("w64x64_t20", seed=1)
+    ref = O.rpca_frames(w.frames)
+    theta = O.mask_threshold(O.temporal_mean_abs(ref.L), w.bound_mask_gt)
+    gpu = gpu_solve(rp, w.frames, theta=theta)
+    assert gpu["res"]["status"] == rp.OK
+    assert gpu["res"]["resid"] <= 1e-7
+    _check_parity(gpu, ref)
+    mask_ref = O.bound_mask(O.temporal_mean_abs(ref.L), theta)
+    assert O.dice(gpu["mask"], mask_ref) >= 0.999
+    # the residual reported equals the one recomputed from the outputs
+    r2 = rel(w.frames.astype(np.float64) - gpu["L"] - gpu["S"], np.zeros(1)) / np.linalg.norm(w.frames.astype(np.float64))
+    assert r2 <= 2e-7
+
+
+@pytest.mark.parametrize("ny,nx,T", [(63, 64, 20), (20, 17, 7), (31, 33, 13), (16, 16, 32), (40, 40, 3)])
+def test_solve_ragged_shapes(rp, ny, nx, T):
+    w = synth.make_window(seed=ny * nx + T, ny=ny, nx=nx, T=T, n_bound=4, n_free=6)
+    ref = O.rpca_frames(w.frames)
+    gpu = gpu_solve(rp, w.frames)
+    _check_parity(gpu, ref)
+
+
+def test_host_drive_equals_graph_drive(rp):
+    w = synth.make_preset("w64x64_t20", seed=7)
+    a = gpu_solve(rp, w.frames, drive=rp.DRIVE_GRAPH)
+    b = gpu_solve(rp, w.frames, drive=rp.DRIVE_HOST)
+    assert a["res"]["iters"] == b["res"]["iters"]
+    assert rel(a["L"], b["L"]) <= 1e-6 and rel(a["S"], b["S"]) <= 1e-6
+
+
+def test_fixed_l1_schedule(rp):
+    w = synth.make_window(seed=5, ny=32, nx=32, T=10, n_bound=5, n_free=8)
+    ref = O.rpca_frames(w.frames, schedule=O.SCHEDULE_FIXED_L1, max_iter=60, tol=1e-6)
+    gpu = gpu_solve(rp, w.frames, mu_schedule=rp.MU_FIXED_L1, max_iter=60, tol=1e-6)
+    assert gpu["res"]["iters"] == ref.iters
+    assert rel(gpu["L"], ref.L) <= 1e-4 and rel(gpu["S"], ref.S) <= 1e-4
+
+
+def test_max_iter_not_converged(rp):
+    w = synth.make_preset("w64x64_t20", seed=8)
+    ref = O.rpca_frames(w.frames, max_iter=6)
+    gpu = gpu_solve(rp, w.frames, max_iter=6)
+    assert gpu["res"]["status"] == rp.NOT_CONVERGED and gpu["res"]["iters"] == 6
+    _check_parity(gpu, ref)
+
+
+def test_zero_window(rp):
+    F = np.zeros((5, 1000), np.float32)
+    gpu = gpu_solve(rp, F, theta=0.5)
+    assert gpu["res"]["status"] == rp.OK and gpu["res"]["iters"] == 0
+    assert not gpu["L"].any() and not gpu["S"].any() and not gpu["mask"].any()
+
+
+def test_nonfinite_input_reports_error(rp):
+    F = synth.random_dense(1, 2000, 8)
+    F[3, 17] = np.nan
+    X = torch.from_numpy(F).cuda()
+    plan = rp.Plan(2000, 8)
+    with pytest.raises(rp.RpcaError) as ei:
+        plan.solve(X)
+    assert ei.value.status == rp.ERR_NONFINITE
+    plan.close()
+
+
+def test_invalid_arguments(rp):
+    with pytest.raises(rp.RpcaError) as ei:
+        rp.Plan(100, 64)
+    assert ei.value.status == rp.ERR_UNSUPPORTED
+    with pytest.raises(rp.RpcaError):
+        rp.Plan(100, 8, tol=0.0)
+    with pytest.raises(rp.RpcaError):
+        rp.Plan(0, 8)
+
+
+def test_plan_reuse_is_repeatable(rp):
+    w = synth.make_preset("w64x64_t20", seed=9)
+    X = torch.from_numpy(w.frames).cuda()
+    plan = rp.Plan(X.shape[1], X.shape[0])
+    L1, S1, r1 = plan.solve(X)
+    L1, S1 = L1.clone(), S1.clone()
+    L2, S2, r2 = plan.solve(X)
+    assert r1["iters"] == r2["iters"]
+    assert torch.equal(L1, L2) and torch.equal(S1, S2)
+    plan.close()
+
+
+@pytest.mark.slow
+def test_solve_512x512x20_full_size(rp):
+    # the benchmark's workload (262144 x 20) in the benchmark's launch configuration
+    w = synth.make_preset("w512x512_t20", seed=1)
+    ref = O.rpca_frames(w.frames)
+    gpu = gpu_solve(rp, w.frames)
+    assert gpu["res"]["status"] == rp.OK
+    _check_parity(gpu, ref)
