@@ -166,6 +166,33 @@ rpca_status rpca_gram(const float* X, int64_t m, int32_t T, const float* V, doub
  * evals in descending order.  Synchronous on `stream`. */
 rpca_status rpca_eig(const double* G, int32_t T, double* evals, double* evecs, void* stream);
 
+/* ---- entry point that allocates no device memory ------------------------ */
+
+/* The paper has no counterpart to this entry point; it serves callers that may
+ * not allocate device memory once they are running: a real-time scanner
+ * pipeline that reserves all device memory at start-up and must not block on
+ * cudaMalloc (which can synchronise the whole device) while frames stream in,
+ * or a process whose device memory belongs to another framework's pool.
+ *
+ * Computes the same G = (Z V)^T (Z V) as rpca_gram (Z = X, frame-major m x T
+ * real float32 on the device; V row-major T x T float32 on the device or NULL
+ * for the identity; G row-major T x T float64 on the device, written by the
+ * call), but asynchronously on `stream` and with no cudaMalloc, cudaFree or
+ * other allocating call: its scratch (about 2.2 MB: partial Grams of at most
+ * 512 CTAs, reduction counters, control block) is a fixed array compiled into
+ * the library, one copy on every GPU that loads it, held until the process
+ * exits.  The caller still provides X, V and G.
+ *   - T must be <= RPCA_MAX_T (else RPCA_ERR_UNSUPPORTED); m is not limited
+ *     (the CTAs stride over the pixels).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call shares the one array and clears its counters first; calls
+ *     whose work overlaps on the GPU (other streams, other host threads) race
+ *     on it and must be serialised by the caller.
+ *   - G is valid once `stream` has been synchronised. */
+rpca_status rpca_gram_noalloc(const float* X, int64_t m, int32_t T, const float* V, double* G, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

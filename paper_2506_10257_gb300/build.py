@@ -15,6 +15,7 @@ CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "librpca.so")
 GENCODE = "arch=compute_103a,code=sm_103a"
+UNITS = ["rpca_capi.cu", "rpca_noalloc.cu"]
 
 
 def _sources():
@@ -43,7 +44,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     tmp = LIB + ".tmp"
     cmd = [nvcc_path(), "-gencode", GENCODE, "-O3", "-lineinfo", "-std=c++17",
            "-Xcompiler", "-fPIC", "-shared", "-I", os.path.join(ROOT, "include"),
-           "-o", tmp, os.path.join(CSRC, "rpca_capi.cu")]
+           "-o", tmp] + [os.path.join(CSRC, f) for f in UNITS]
     if verbose:
         print(" ".join(cmd))
     subprocess.run(cmd, check=True)

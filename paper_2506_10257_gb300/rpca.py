@@ -26,7 +26,8 @@ DRIVE_GRAPH, DRIVE_HOST = 0, 1
 MAX_T = 32
 
 EXPORTED = ["rpca_params_default", "rpca_workspace_size", "rpca_plan_create", "rpca_solve", "rpca_solve_host",
-            "rpca_plan_result", "rpca_plan_destroy", "rpca_status_str", "rpca_gram", "rpca_eig"]
+            "rpca_plan_result", "rpca_plan_destroy", "rpca_status_str", "rpca_gram", "rpca_eig",
+            "rpca_gram_noalloc"]
 
 
 class Params(ctypes.Structure):
@@ -86,6 +87,7 @@ def load(build_if_missing: bool = True):
     lib.rpca_status_str.restype = ctypes.c_char_p
     lib.rpca_gram.argtypes = [vp, i64, i32, vp, vp, i32, vp]
     lib.rpca_eig.argtypes = [vp, i32, vp, vp, vp]
+    lib.rpca_gram_noalloc.argtypes = [vp, i64, i32, vp, vp, vp]
     _lib = lib
     return lib
 
@@ -246,3 +248,22 @@ def eig(G):
     if st != OK:
         raise RpcaError(st, "rpca_eig")
     return ev, V
+
+
+def gram_noalloc(frames, V=None, G=None, stream=None):
+    """Same Gram as ``gram`` through rpca_gram_noalloc, which allocates no device
+    memory (its scratch is a fixed array inside the library).  The output G
+    (T, T) float64 is allocated here by the caller side unless given."""
+    torch = _torch()
+    T, m = frames.shape
+    if G is None:
+        G = torch.empty((T, T), dtype=torch.float64, device="cuda")
+    vptr = 0
+    if V is not None:
+        V = V.to(device="cuda", dtype=torch.float32).contiguous()
+        vptr = V.data_ptr()
+    st = load().rpca_gram_noalloc(ctypes.c_void_p(frames.data_ptr()), m, T, ctypes.c_void_p(vptr),
+                                  ctypes.c_void_p(G.data_ptr()), _stream_handle(stream))
+    if st != OK:
+        raise RpcaError(st, "rpca_gram_noalloc")
+    return G
