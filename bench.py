@@ -77,7 +77,7 @@ def kernel_source_hash() -> str:
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms during the timed region."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -92,7 +92,7 @@ class ClockSampler:
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -129,6 +129,15 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def launches_per_solve(drive: str, iters: int) -> int:
+    """Kernels of this library launched by one solve."""
+    if drive == "graph":      # begin, init pass, eig, iters x (pass, eig), final
+        return 4 + 2 * iters
+    if drive == "stream":     # same, with up to 7 no-op (pass, eig) pairs after convergence
+        return 4 + 2 * (-(-iters // 8) * 8)
+    return 4 + 4 * iters      # host: update pass, check, gram pass, eig per iteration
 
 
 def window(seed: int):
@@ -190,8 +199,10 @@ def run_ours(args):
     w = window(1 + 1000 * rank)
     T, m = w.frames.shape
     X = torch.from_numpy(w.frames).cuda()
-    prec = {"fp32": rpca.PREC_FP32}[args.precision]
-    plan = rpca.Plan(m, T, precision=prec, drive=rpca.DRIVE_GRAPH)
+    prec = {"fp32": rpca.PREC_FP32, "tf32x3": rpca.PREC_TF32X3, "bf16x3": rpca.PREC_BF16X3,
+            "tf32": rpca.PREC_TF32}[args.precision]
+    drive = {"graph": rpca.DRIVE_GRAPH, "stream": rpca.DRIVE_STREAM, "host": rpca.DRIVE_HOST}[args.drive]
+    plan = rpca.Plan(m, T, precision=prec, drive=drive)
     L = torch.empty_like(X)
     S = torch.empty_like(X)
     # threshold of the bound-bubble mask: half the mean ground-truth image at bound-bubble cores
@@ -262,14 +273,17 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded microbubble window, in HBM)",
         "config": {"workload": WORKLOAD + " (512x512 px x 20 frames, Casorati 262144x20, fp32)",
-                   "precision": args.precision, "drive": "cuda-graph device loop",
+                   "precision": args.precision,
+                   "drive": {"graph": "cuda-graph device loop", "stream": "kernels launched one by one",
+                             "host": "plain form: host loop, unfused passes"}[args.drive],
                    "tol": 1e-7, "l2": "flushed before every step (256 MB write, outside step events)",
                    "parallelism": f"replicas x{world} (independent windows)"},
         "latency_ms": {"p50": statistics.median(step_ms), "p99": float(np.percentile(step_ms, 99)),
                        "min": min(step_ms), "max": max(step_ms)},
         "iters": res["iters"], "ms_per_iter": ms_per_step / max(res["iters"], 1),
-        "kernel_us": {"pass": pass_us, "eig": res["eig_us"], "init": res["init_us"]},
-        "gpu_launches": args.steps * (4 + 2 * res["iters"]),
+        "kernel_us": {"pass": pass_us, "eig": res["eig_us"], "init": res["init_us"],
+                      "eig_split": {k: round(v, 3) for k, v in plan.timings().items()}},
+        "gpu_launches": args.steps * launches_per_solve(args.drive, res["iters"]),
         "roofline": {"bound": "hbm", "kernel": "pass_kernel<20,FUSED>",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": ncu_traffic(src_hash),
@@ -309,11 +323,14 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp32"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "tf32x3", "bf16x3", "tf32"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--drive", choices=["graph", "stream", "host"], default="graph",
+                    help="graph: the product path; stream: same kernels launched one by one (for ncu); "
+                         "host: the plain unfused form")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -66,8 +66,11 @@ typedef enum { RPCA_MU_IALM = 0, RPCA_MU_FIXED_L1 = 1 } rpca_mu_schedule;
 /* How the iterations are driven. */
 typedef enum {
   RPCA_DRIVE_GRAPH = 0,     /* one CUDA graph per solve, device-side while loop, fused pass */
-  RPCA_DRIVE_HOST = 1       /* host loop, separate Gram / update passes, residual read back
+  RPCA_DRIVE_HOST = 1,      /* host loop, separate Gram / update passes, residual read back
                                every iteration (the plain form) */
+  RPCA_DRIVE_STREAM = 2     /* the graph's kernels launched one by one on the stream, the host
+                               reading the convergence flag every 8 iterations (for profilers
+                               that cannot look inside a graph with a conditional node) */
 } rpca_drive;
 
 typedef struct {
@@ -145,6 +148,16 @@ rpca_status rpca_solve_host(rpca_plan_t plan, const void* X_host, void* L_host, 
 
 /* Result of the last solve on this plan (call after synchronising its stream). */
 rpca_status rpca_plan_result(rpca_plan_t plan, rpca_result* out);
+
+/* Device-timer breakdown of the last solve (after synchronising its stream),
+ * written to out[0..n): [0] mean eigen-step time in its control + load phase,
+ * [1] in the Jacobi sweeps, [2] forming the rotation product, [3] basis update
+ * and Wbar, all in microseconds; [4] Jacobi rounds executed per eigen-step;
+ * [5] eigen-steps timed; [6] mean per-iteration pass time until the last CTA
+ * has written its partial sums, [7] in the first-level cross-CTA reduction,
+ * [8] in the final reduction (microseconds).  Entries past 9 are left
+ * untouched.  Implementation instrumentation: the paper has no counterpart. */
+rpca_status rpca_plan_timings(rpca_plan_t plan, double* out, int32_t n);
 
 void rpca_plan_destroy(rpca_plan_t plan);
 

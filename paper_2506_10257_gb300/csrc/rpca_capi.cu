@@ -1,5 +1,7 @@
 // rpca_capi.cu -- C ABI of the GB300 PCP solver: plans, CUDA-graph driver,
 // host-driven plain form, kernel-level entry points.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdlib.h>
@@ -17,8 +19,14 @@ namespace {
 
 struct KernelSet {
   void* pass[4];
-  void* eig32;
-  void* eig64;
+  void* pass_tc[4];        // fused pass with tensor-core contractions, per rpca_precision (0 unused)
+  size_t pass_tc_smem[4];
+  void* pass_ws[4];        // the same, warp-specialised and fed by TMA (needs m % 4 == 0)
+  size_t pass_ws_smem[4];
+  void* eig32;       // smem Jacobi, FP32 rotations (reference form)
+  void* eig64;       // smem Jacobi, FP64 rotations
+  void* eig_fast;    // FP32 rotations, logged and accumulated once
+  size_t eig_fast_smem;
   int TB;
   int eig_threads;
 };
@@ -32,6 +40,8 @@ KernelSet make_set() {
   k.pass[PM_GRAM] = (void*)pass_kernel<TB, PM_GRAM>;
   k.eig32 = (void*)eig_kernel<TB, float>;
   k.eig64 = (void*)eig_kernel<TB, double>;
+  k.eig_fast = (void*)eig_fast_kernel<TB>;
+  k.eig_fast_smem = sizeof(EigFastSmem<TB>);
   k.TB = TB;
   k.eig_threads = TB > 20 ? 512 : 256;
   return k;
@@ -45,6 +55,34 @@ int bucket_of(int T) {
   if (T <= 24) return 24;
   if (T <= 32) return 32;
   return 0;
+}
+
+template <int TB>
+void add_tc(KernelSet& k) {
+  constexpr int KP = TB <= 16 ? 16 : 32;
+  k.pass_tc[RPCA_PREC_FP32] = nullptr;
+  k.pass_tc_smem[RPCA_PREC_FP32] = 0;
+  k.pass_tc[RPCA_PREC_TF32X3] = (void*)pass_tc_kernel<TB, KP, false, true>;
+  k.pass_tc_smem[RPCA_PREC_TF32X3] = pass_tc_smem<TB, KP, false>();
+  k.pass_tc[RPCA_PREC_BF16X3] = (void*)pass_tc_kernel<TB, KP, true, true>;
+  k.pass_tc_smem[RPCA_PREC_BF16X3] = pass_tc_smem<TB, KP, true>();
+  k.pass_tc[RPCA_PREC_TF32] = (void*)pass_tc_kernel<TB, KP, false, false>;
+  k.pass_tc_smem[RPCA_PREC_TF32] = pass_tc_smem<TB, KP, false>();
+  k.pass_ws[RPCA_PREC_FP32] = nullptr;
+  k.pass_ws_smem[RPCA_PREC_FP32] = 0;
+  k.pass_ws[RPCA_PREC_TF32X3] = (void*)pass_ws_kernel<TB, KP, false, true>;
+  k.pass_ws_smem[RPCA_PREC_TF32X3] = pass_ws_smem<TB, KP, false>();
+  k.pass_ws[RPCA_PREC_BF16X3] = (void*)pass_ws_kernel<TB, KP, true, true>;
+  k.pass_ws_smem[RPCA_PREC_BF16X3] = pass_ws_smem<TB, KP, true>();
+  k.pass_ws[RPCA_PREC_TF32] = (void*)pass_ws_kernel<TB, KP, false, false>;
+  k.pass_ws_smem[RPCA_PREC_TF32] = pass_ws_smem<TB, KP, false>();
+}
+
+// Tensor-core pass buckets: T <= 16, 20, 32.
+void set_tc(int T, KernelSet* k) {
+  if (T <= 16) add_tc<16>(*k);
+  else if (T <= 20) add_tc<20>(*k);
+  else add_tc<32>(*k);
 }
 
 bool get_set(int T, KernelSet* out) {
@@ -64,6 +102,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 struct Layout {
   size_t ctrl, eig, red, job, gram_part, group_part, scal_part, gscal_part, ybuf, total;
   int grid, ngroups;
+  int ws_grid;   // CTAs of the warp-specialised pass (one per SM, 128-pixel tiles)
 };
 
 int device_sms() {
@@ -80,7 +119,9 @@ Layout make_layout(int64_t m, int T, int sms) {
   int64_t grid = std::min<int64_t>(ntiles, (int64_t)std::max(sms, 1) * 2);
   grid = std::min<int64_t>(grid, (int64_t)kGroup * kMaxGroups);
   L.grid = (int)std::max<int64_t>(grid, 1);
-  L.ngroups = (L.grid + kGroup - 1) / kGroup;
+  L.ws_grid = (int)std::max<int64_t>(std::min<int64_t>((m + 127) / 128, std::max(sms, 1)), 1);
+  const int maxgrid = std::max(L.grid, L.ws_grid);
+  L.ngroups = (maxgrid + kGroup - 1) / kGroup;
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t o = off;
@@ -91,9 +132,9 @@ Layout make_layout(int64_t m, int T, int sms) {
   L.eig = take(sizeof(EigState));
   L.red = take(sizeof(RedState));
   L.job = take(sizeof(Job));
-  L.gram_part = take(sizeof(float) * (size_t)L.grid * T * T);
+  L.gram_part = take(sizeof(float) * (size_t)maxgrid * T * T);
   L.group_part = take(sizeof(float) * (size_t)L.ngroups * T * T);
-  L.scal_part = take(sizeof(double) * 2 * (size_t)L.grid);
+  L.scal_part = take(sizeof(double) * 2 * (size_t)maxgrid);
   L.gscal_part = take(sizeof(double) * 2 * (size_t)L.ngroups);
   L.ybuf = take(sizeof(float) * (size_t)m * T);
   L.total = off;
@@ -108,9 +149,11 @@ rpca_status validate(const rpca_params* p) {
   if (p->mu_schedule != RPCA_MU_IALM && p->mu_schedule != RPCA_MU_FIXED_L1) return RPCA_ERR_ARG;
   if (p->mu_schedule == RPCA_MU_IALM && (!(p->rho >= 1.0) || !(p->mu0_scale > 0) || !(p->mu_max_factor >= 1.0)))
     return RPCA_ERR_ARG;
-  if (p->drive != RPCA_DRIVE_GRAPH && p->drive != RPCA_DRIVE_HOST) return RPCA_ERR_ARG;
+  if (p->drive != RPCA_DRIVE_GRAPH && p->drive != RPCA_DRIVE_HOST && p->drive != RPCA_DRIVE_STREAM)
+    return RPCA_ERR_ARG;
   if (p->dtype != RPCA_R32) return RPCA_ERR_UNSUPPORTED;
-  if (p->precision != RPCA_PREC_FP32) return RPCA_ERR_UNSUPPORTED;
+  if (p->precision < RPCA_PREC_FP32 || p->precision > RPCA_PREC_TF32) return RPCA_ERR_ARG;
+  if (p->precision != RPCA_PREC_FP32 && p->drive == RPCA_DRIVE_HOST) return RPCA_ERR_UNSUPPORTED;
   if (p->m * (int64_t)p->T > (int64_t)1 << 40) return RPCA_ERR_ARG;
   return RPCA_OK;
 }
@@ -129,12 +172,41 @@ struct rpca_plan_s {
   cudaGraph_t graph;
   cudaGraphExec_t exec;
   Ctrl* ctrl_host;  // pinned
+  bool use_ws;      // fused pass = warp-specialised TMA kernel
   // device staging of rpca_solve_host (allocated on first use)
   float* stage_x;
   float* stage_l;
   float* stage_s;
   uint8_t* stage_mask;
 };
+
+// cuTensorMapEncodeTiled from the driver (looked up once; NULL if unavailable).
+static PFN_cuTensorMapEncodeTiled_v12000 tma_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+  }
+  return fn;
+}
+
+// 2D map of a frame-major m x T float32 matrix, box 128 pixels x T frames.
+static bool encode_map(CUtensorMap* map, const void* ptr, int64_t m, int T) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tma_encoder();
+  if (!enc) return false;
+  cuuint64_t gdim[2] = {(cuuint64_t)m, (cuuint64_t)T};
+  cuuint64_t gstride[1] = {(cuuint64_t)m * 4};
+  cuuint32_t box[2] = {128, (cuuint32_t)T};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(ptr), gdim, gstride, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 static rpca_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return RPCA_OK;
@@ -147,20 +219,37 @@ static rpca_status cuda_status(cudaError_t e) {
     if (_e != cudaSuccess) return cuda_status(_e); \
   } while (0)
 
-static cudaError_t launch(void* fn, dim3 g, dim3 blk, void** args, cudaStream_t s) {
-  return cudaLaunchKernel(fn, g, blk, args, 0, s);
+static cudaError_t launch(void* fn, dim3 g, dim3 blk, void** args, cudaStream_t s, size_t smem = 0) {
+  return cudaLaunchKernel(fn, g, blk, args, smem, s);
 }
 
-static void* eig_fn(const rpca_plan_s* pl) { return pl->eig_fp64 ? pl->ks.eig64 : pl->ks.eig32; }
+// Eigen-step kernel of a plan: FP64 rotations when RPCA_EIG_FP64 is set, else
+// the fast FP32 form.  Both take (Bufs, flags, handle, use_cond, ...); the
+// extra pointer arguments only exist in the smem form and are ignored by the
+// fast one.
+static void* eig_fn(const rpca_plan_s* pl) { return pl->eig_fp64 ? pl->ks.eig64 : pl->ks.eig_fast; }
+static size_t eig_smem(const rpca_plan_s* pl) { return pl->eig_fp64 ? 0 : pl->ks.eig_fast_smem; }
+static dim3 eig_block(const rpca_plan_s* pl) { return dim3(pl->eig_fp64 ? pl->ks.eig_threads : 256); }
+// Fused per-iteration pass: CUDA-core FP32 or the tensor-core form of the plan's precision.
+static void* fused_fn(const rpca_plan_s* pl) {
+  if (pl->p.precision == RPCA_PREC_FP32) return pl->ks.pass[PM_FUSED];
+  return pl->use_ws ? pl->ks.pass_ws[pl->p.precision] : pl->ks.pass_tc[pl->p.precision];
+}
+static size_t fused_smem(const rpca_plan_s* pl) {
+  if (pl->p.precision == RPCA_PREC_FP32) return 0;
+  return pl->use_ws ? pl->ks.pass_ws_smem[pl->p.precision] : pl->ks.pass_tc_smem[pl->p.precision];
+}
+static dim3 fused_grid(const rpca_plan_s* pl) { return dim3(pl->use_ws ? pl->lay.ws_grid : pl->lay.grid); }
+static dim3 fused_block(const rpca_plan_s* pl) { return dim3(pl->use_ws ? kWsThreads : kPassThreads); }
 
 static cudaError_t add_kernel(cudaGraph_t g, cudaGraphNode_t* node, const cudaGraphNode_t* deps, size_t ndeps,
-                              void* fn, dim3 grid, dim3 blk, void** args) {
+                              void* fn, dim3 grid, dim3 blk, void** args, size_t smem = 0) {
   cudaKernelNodeParams kp;
   memset(&kp, 0, sizeof(kp));
   kp.func = fn;
   kp.gridDim = grid;
   kp.blockDim = blk;
-  kp.sharedMemBytes = 0;
+  kp.sharedMemBytes = (unsigned)smem;
   kp.kernelParams = args;
   kp.extra = nullptr;
   return cudaGraphAddKernelNode(node, g, deps, ndeps, &kp);
@@ -172,7 +261,8 @@ static rpca_status build_graph(rpca_plan_s* pl) {
   cudaGraphConditionalHandle h;
   CK(cudaGraphConditionalHandleCreate(&h, pl->graph, 0, cudaGraphCondAssignDefault));
   Bufs b = pl->bufs;
-  const dim3 pg(pl->lay.grid), pb(kPassThreads), eg(1), eb(pl->ks.eig_threads);
+  const dim3 pg(pl->lay.grid), pb(kPassThreads), eg(1), eb = eig_block(pl);
+  const size_t es = eig_smem(pl);
   const double* nulld = nullptr;
   double* nullo = nullptr;
   int use_cond = 1;
@@ -183,7 +273,7 @@ static rpca_status build_graph(rpca_plan_s* pl) {
   void* a_eig1[] = {&b, &f_iter, &h, &use_cond, &nulld, &nullo, &nullo};
   cudaGraphNode_t n_init, n_eig0, n_while, n_fin, n_pass, n_eig;
   CK(add_kernel(pl->graph, &n_init, nullptr, 0, pl->ks.pass[PM_INIT], pg, pb, a_pass));
-  CK(add_kernel(pl->graph, &n_eig0, &n_init, 1, eig_fn(pl), eg, eb, a_eig0));
+  CK(add_kernel(pl->graph, &n_eig0, &n_init, 1, eig_fn(pl), eg, eb, a_eig0, es));
 
   alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
   memset(cp_raw, 0, sizeof(cp_raw));
@@ -194,8 +284,8 @@ static rpca_status build_graph(rpca_plan_s* pl) {
   cp.conditional.size = 1;
   CK(cudaGraphAddNode(&n_while, pl->graph, &n_eig0, nullptr, 1, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
-  CK(add_kernel(body, &n_pass, nullptr, 0, pl->ks.pass[PM_FUSED], pg, pb, a_pass));
-  CK(add_kernel(body, &n_eig, &n_pass, 1, eig_fn(pl), eg, eb, a_eig1));
+  CK(add_kernel(body, &n_pass, nullptr, 0, fused_fn(pl), fused_grid(pl), fused_block(pl), a_pass, fused_smem(pl)));
+  CK(add_kernel(body, &n_eig, &n_pass, 1, eig_fn(pl), eg, eb, a_eig1, es));
 
   const int fgrid = (int)std::min<int64_t>((pl->p.m + 255) / 256, 4096);
   CK(add_kernel(pl->graph, &n_fin, &n_while, 1, (void*)final_kernel, dim3(fgrid), dim3(256), a_pass));
@@ -246,7 +336,29 @@ rpca_status rpca_plan_create(const rpca_params* p, void* workspace, size_t works
     delete pl;
     return RPCA_ERR_UNSUPPORTED;
   }
+  set_tc(p->T, &pl->ks);
+  pl->use_ws = (p->precision != RPCA_PREC_FP32) && (p->m % 4 == 0) && tma_encoder() != nullptr &&
+               !(getenv("RPCA_NO_WS") && atoi(getenv("RPCA_NO_WS")) != 0);
+  if (p->precision != RPCA_PREC_FP32) {
+    cudaError_t ea = cudaFuncSetAttribute(pl->ks.pass_tc[p->precision], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)pl->ks.pass_tc_smem[p->precision]);
+    if (ea == cudaSuccess && pl->use_ws)
+      ea = cudaFuncSetAttribute(pl->ks.pass_ws[p->precision], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)pl->ks.pass_ws_smem[p->precision]);
+    if (ea != cudaSuccess) {
+      delete pl;
+      return cuda_status(ea);
+    }
+  }
   pl->lay = make_layout(p->m, p->T, sms);
+  if (pl->ks.eig_fast_smem > 48 * 1024) {
+    cudaError_t ea = cudaFuncSetAttribute(pl->ks.eig_fast, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)pl->ks.eig_fast_smem);
+    if (ea != cudaSuccess) {
+      delete pl;
+      return cuda_status(ea);
+    }
+  }
   pl->eig_fp64 = (getenv("RPCA_EIG_FP64") && atoi(getenv("RPCA_EIG_FP64")) != 0) ? 1 : 0;
   if (workspace) {
     if (workspace_bytes < pl->lay.total || ((uintptr_t)workspace & 255u)) {
@@ -340,7 +452,8 @@ static void fill_result(const rpca_plan_s* pl, const Ctrl& c, rpca_result* out) 
 // host after every iteration (one host synchronisation per iteration).
 static rpca_status run_host_loop(rpca_plan_s* pl, cudaStream_t s) {
   Bufs b = pl->bufs;
-  const dim3 pg(pl->lay.grid), pb(kPassThreads), eg(1), eb(pl->ks.eig_threads);
+  const dim3 pg(pl->lay.grid), pb(kPassThreads), eg(1), eb = eig_block(pl);
+  const size_t es = eig_smem(pl);
   cudaGraphConditionalHandle h = 0;
   const double* nulld = nullptr;
   double* nullo = nullptr;
@@ -351,18 +464,49 @@ static rpca_status run_host_loop(rpca_plan_s* pl, cudaStream_t s) {
   void* a_check[] = {&b, &f_check, &h, &use_cond, &nulld, &nullo, &nullo};
   void* a_eig[] = {&b, &f_eig, &h, &use_cond, &nulld, &nullo, &nullo};
   CK(launch(pl->ks.pass[PM_INIT], pg, pb, a_pass, s));
-  CK(launch(eig_fn(pl), eg, eb, a_init, s));
+  CK(launch(eig_fn(pl), eg, eb, a_init, s, es));
   for (int it = 0; it <= pl->p.max_iter; ++it) {
     CK(cudaMemcpyAsync(pl->ctrl_host, b.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (pl->ctrl_host->done) break;
     CK(launch(pl->ks.pass[PM_UPDATE], pg, pb, a_pass, s));
-    CK(launch(eig_fn(pl), eg, eb, a_check, s));
+    CK(launch(eig_fn(pl), eg, eb, a_check, s, es));
     CK(cudaMemcpyAsync(pl->ctrl_host, b.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (pl->ctrl_host->done) break;
     CK(launch(pl->ks.pass[PM_GRAM], pg, pb, a_pass, s));
-    CK(launch(eig_fn(pl), eg, eb, a_eig, s));
+    CK(launch(eig_fn(pl), eg, eb, a_eig, s, es));
+  }
+  const int fgrid = (int)std::min<int64_t>((pl->p.m + 255) / 256, 4096);
+  CK(launch((void*)final_kernel, dim3(fgrid), dim3(256), a_pass, s));
+  return RPCA_OK;
+}
+
+// The graph's kernels launched one by one (no conditional node), convergence
+// flag read back every 8 iterations; kernels launched after convergence return
+// at once.
+static rpca_status run_stream_loop(rpca_plan_s* pl, cudaStream_t s) {
+  Bufs b = pl->bufs;
+  const dim3 pg(pl->lay.grid), pb(kPassThreads), eg(1), eb = eig_block(pl);
+  const size_t es = eig_smem(pl);
+  cudaGraphConditionalHandle h = 0;
+  const double* nulld = nullptr;
+  double* nullo = nullptr;
+  int use_cond = 0;
+  int f_init = EF_INIT | EF_EIG, f_iter = EF_CHECK | EF_EIG;
+  void* a_pass[] = {&b};
+  void* a_init[] = {&b, &f_init, &h, &use_cond, &nulld, &nullo, &nullo};
+  void* a_iter[] = {&b, &f_iter, &h, &use_cond, &nulld, &nullo, &nullo};
+  CK(launch(pl->ks.pass[PM_INIT], pg, pb, a_pass, s));
+  CK(launch(eig_fn(pl), eg, eb, a_init, s, es));
+  for (int it = 0; it < pl->p.max_iter; ++it) {
+    if (it % 8 == 0) {
+      CK(cudaMemcpyAsync(pl->ctrl_host, b.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (pl->ctrl_host->done) break;
+    }
+    CK(launch(fused_fn(pl), fused_grid(pl), fused_block(pl), a_pass, s, fused_smem(pl)));
+    CK(launch(eig_fn(pl), eg, eb, a_iter, s, es));
   }
   const int fgrid = (int)std::min<int64_t>((pl->p.m + 255) / 256, 4096);
   CK(launch((void*)final_kernel, dim3(fgrid), dim3(256), a_pass, s));
@@ -376,12 +520,22 @@ rpca_status rpca_solve(rpca_plan_t pl, const void* X, void* L, void* S, uint8_t*
   if (X == L || X == S || L == S) return RPCA_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   Bufs b = pl->bufs;
-  void* a_begin[] = {&b, (void*)&X, &L, &S, &mask, &theta};
-  CK(cudaLaunchKernel((void*)begin_kernel, dim3(1), dim3(32), a_begin, 0, s));
+  TmaMaps maps;
+  memset(&maps, 0, sizeof(maps));
+  int use_maps = 0;
+  if (pl->use_ws) {
+    const float* y1 = (const float*)(pl->ws + pl->lay.ybuf);
+    if (!encode_map(&maps.x, X, pl->p.m, pl->p.T) || !encode_map(&maps.s, S, pl->p.m, pl->p.T) ||
+        !encode_map(&maps.y0, L, pl->p.m, pl->p.T) || !encode_map(&maps.y1, y1, pl->p.m, pl->p.T))
+      return RPCA_ERR_CUDA;
+    use_maps = 1;
+  }
+  void* a_begin[] = {&b, (void*)&X, &L, &S, &mask, &theta, &maps, &use_maps};
+  CK(cudaLaunchKernel((void*)begin_kernel, dim3(1), dim3(64), a_begin, 0, s));
   if (pl->p.drive == RPCA_DRIVE_GRAPH) {
     CK(cudaGraphLaunch(pl->exec, s));
   } else {
-    rpca_status st = run_host_loop(pl, s);
+    rpca_status st = pl->p.drive == RPCA_DRIVE_HOST ? run_host_loop(pl, s) : run_stream_loop(pl, s);
     if (st != RPCA_OK) return st;
   }
   if (!out) return RPCA_OK;
@@ -421,6 +575,21 @@ rpca_status rpca_solve_host(rpca_plan_t pl, const void* X_host, void* L_host, vo
   if (!out) return (rpca_status)(pl->ctrl_host->status < 0 ? pl->ctrl_host->status : RPCA_OK);
   fill_result(pl, *pl->ctrl_host, out);
   return (rpca_status)out->status;
+}
+
+rpca_status rpca_plan_timings(rpca_plan_t pl, double* out, int32_t n) {
+  if (!pl || !out || n < 0) return RPCA_ERR_ARG;
+  CK(cudaMemcpy(pl->ctrl_host, pl->bufs.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
+  const Ctrl& c = *pl->ctrl_host;
+  const double cnt = c.eig_cnt ? (double)c.eig_cnt : 1.0;
+  const double pcnt = c.pass_cnt ? (double)c.pass_cnt : 1.0;
+  double v[9];
+  for (int i = 0; i < 4; ++i) v[i] = (double)c.eig_phase_ns[i] * 1e-3 / cnt;
+  v[4] = (double)c.eig_rounds / cnt;
+  v[5] = (double)c.eig_cnt;
+  for (int i = 0; i < 3; ++i) v[6 + i] = (double)c.pass_phase_ns[i] * 1e-3 / pcnt;
+  for (int i = 0; i < n && i < 9; ++i) out[i] = v[i];
+  return RPCA_OK;
 }
 
 void rpca_plan_destroy(rpca_plan_t pl) {

@@ -18,6 +18,7 @@
 // eigen-decomposition of the next iteration starts from a nearly diagonal
 // matrix whose FP32 accumulation error is relative to each eigenvalue.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -64,6 +65,14 @@ struct Ctrl {
   // Device-side timing of the solve (globaltimer, ns): fused/update passes
   // after the first, eigen-steps, and the init pass.
   unsigned long long pass_ns, pass_cnt, eig_ns, eig_cnt, init_ns;
+  // eigen-step phase split (ns, summed over calls): control+load, sweeps,
+  // rotation product, basis update + Wbar
+  unsigned long long eig_phase_ns[4];
+  // pass phase split (ns, summed over the timed passes): CTA work up to the
+  // last CTA's partials, first-level reduction, final reduction
+  unsigned long long pass_phase_ns[3];
+  int eig_rounds;    // Jacobi rounds executed (summed)
+  int pad_;
 };
 
 // Eigen data handed from the eig kernel to the passes.
@@ -79,13 +88,19 @@ struct RedState {
   double e2;                   // sum of E^2 (or ||X||_F^2 in the init pass)
   double l1;                   // sum |X| (init pass)
   unsigned long long t_start;  // earliest CTA start of the last pass (globaltimer)
-  unsigned long long t_end;    // end of its final reduction
+ unsigned long long t_end;    // end of its final reduction
+  unsigned long long t_loop;   // latest time a CTA finished its partials
+  unsigned long long t_l1;     // latest end of a first-level group reduction
+  int err;                     // set by a pass whose bounded device wait ran out
   unsigned int cnt[kMaxGroups + 1];
 };
 
 // Pointers of the current solve (written by a tiny kernel before each graph
 // launch, so one instantiated graph serves every call).
 struct Job {
+  // TMA descriptors of the frame-major X, S, Y0, Y1 (box 128 pixels x T frames),
+  // written per solve when the pixel count allows TMA (m % 4 == 0)
+  CUtensorMap map_x, map_s, map_y0, map_y1;
   const float* X;
   float* S;
   float* Y0;        // dual ping-pong buffer 0 (the caller's L buffer)
@@ -93,6 +108,11 @@ struct Job {
   float* L;
   uint8_t* mask;
   float theta;
+};
+
+// Per-solve tensor maps handed to the begin kernel as a kernel parameter.
+struct TmaMaps {
+  CUtensorMap x, s, y0, y1;
 };
 
 struct Bufs {

@@ -1,6 +1,7 @@
 // rpca_kernels.cuh -- CUDA kernels of the PCP iteration (SIMT FP32 passes,
 // one-CTA Jacobi eigensolve).  See rpca_device.cuh for the algebra.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include "rpca_device.cuh"
@@ -8,7 +9,7 @@
 namespace rpca {
 
 // Status codes mirrored from rpca.h (kept numeric here to avoid a host header).
-constexpr int ST_OK = 0, ST_NOT_CONVERGED = 1, ST_ERR_NONFINITE = -6;
+constexpr int ST_OK = 0, ST_NOT_CONVERGED = 1, ST_ERR_TIMEOUT = -5, ST_ERR_NONFINITE = -6;
 
 // Z = X - S + Y/mu, formed identically wherever it is needed, so that the Gram
 // accumulated in one pass belongs to exactly the Z the next pass uses.
@@ -57,11 +58,65 @@ __device__ __forceinline__ void blk_coords(int blk, int nb, int& bi, int& bj) {
   }
 }
 
+// sum_t z[t] * w[t] with w a 16-byte aligned shared-memory row (vector loads)
+template <int TB>
+__device__ __forceinline__ float row_dot(const float (&z)[TB], const float* w) {
+  const float4* w4 = reinterpret_cast<const float4*>(w);
+  float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+  for (int k = 0; k < TB / 4; ++k) {
+    const float4 v = w4[k];
+    a0 = fmaf(z[4 * k], v.x, a0);
+    a1 = fmaf(z[4 * k + 1], v.y, a1);
+    a0 = fmaf(z[4 * k + 2], v.z, a0);
+    a1 = fmaf(z[4 * k + 3], v.w, a1);
+  }
+  return a0 + a1;
+}
+
 __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
   const float y = v - c;
   const float t = s + y;
   c = (t - s) - y;
   s = t;
+}
+
+// Sums rows [r0, r1) of a row-major [rows][TT] float array entry by entry in a
+// fixed order (Kahan), calling out(e, sum) for every entry; each thread takes
+// entries tid, tid + blockDim, ... and issues its loads in batches of 16 so
+// that their L2 latencies overlap.
+template <typename Out>
+__device__ __forceinline__ void sum_rows(const float* src, int r0, int r1, int TT, Out out) {
+  for (int e = threadIdx.x; e < TT; e += blockDim.x) {
+    float s = 0.f, comp = 0.f;
+    for (int rb = r0; rb < r1; rb += 16) {
+      float v[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) v[u] = (rb + u < r1) ? __ldcg(&src[(int64_t)(rb + u) * TT + e]) : 0.f;
+#pragma unroll
+      for (int u = 0; u < 16; ++u)
+        if (rb + u < r1) kahan_add(s, comp, v[u]);
+    }
+    out(e, s);
+  }
+}
+
+// Sums the (first, second) doubles of rows [r0, r1) of a [rows][2] array in a
+// fixed order; loads in parallel into shared memory, thread 0 adds and calls
+// out(s0, s1).  r1 - r0 <= kMaxGroups.
+template <typename Out>
+__device__ __forceinline__ void sum_scalars(const double* src, int r0, int r1, double* sh, Out out) {
+  const int n = 2 * (r1 - r0);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) sh[i] = __ldcg(&src[2 * r0 + i]);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0, s1 = 0;
+    for (int i = 0; i < r1 - r0; ++i) {
+      s0 += sh[2 * i];
+      s1 += sh[2 * i + 1];
+    }
+    out(s0, s1);
+  }
 }
 
 __device__ __forceinline__ unsigned long long gtimer() {
@@ -76,150 +131,89 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-// ---------------------------------------------------------------------------
-// Per-pixel pass.  MODE:
-//   PM_INIT   Gram of X (standard basis), ||X||_F^2, ||X||_1
-//   PM_FUSED  Eq. 4-6 update of S, Y + residual + Gram of the next Z in basis V
-//   PM_UPDATE Eq. 4-6 update of S, Y + residual (no Gram)
-//   PM_GRAM   Gram of the current Z in basis V (no update)
-// One thread owns one pixel row (its T frames) of a 256-pixel tile; CTAs
-// stride over tiles; partial Grams and scalars are reduced across CTAs by the
-// last CTA to arrive (two levels, fixed summation order => deterministic).
-// ---------------------------------------------------------------------------
-template <int TB, int MODE>
-__global__ void __launch_bounds__(kPassThreads) pass_kernel(Bufs b) {
-  constexpr bool kGram = (MODE != PM_UPDATE);
-  constexpr int ZS = TB + 4;  // staged row stride in floats (16-byte aligned rows)
-  using GM = GramMap<TB>;
-  __shared__ __align__(16) float sW[TB * TB];
-  __shared__ __align__(16) float sV[TB * TB];
-  __shared__ __align__(16) float sZ[kTile * ZS];
-  __shared__ double sRed[2][kPassThreads / 32];
-  __shared__ int sLast;
-
-  const Ctrl* ctrl = b.ctrl;
-  if (ctrl->done) return;
+// Reduction across CTAs after every CTA wrote its partial Gram (gram_part)
+// and scalar sums (scal_part): the last CTA of each group of kGroup sums its
+// group, the last group reducer sums the groups, in fixed order, into red->G,
+// red->e2 and red->l1.  Called by all threads of every CTA.
+__device__ __noinline__ void cross_cta_reduce(Bufs b, bool kGram, double* sScal, int* sLastp) {
   const int tid = threadIdx.x;
-  if (tid == 0) atomicMin(&b.red->t_start, gtimer());
   const int T = b.T;
-  const int64_t m = b.m;
-  const Job job = *b.job;
-  const int kc = ctrl->k;
-  const bool first = (kc == 0);
-  const float f_mu = ctrl->f_mu, inv_mu = ctrl->f_inv_mu, gamma = ctrl->f_gamma;
-  const float inv_mu_nxt = ctrl->f_inv_mu_nxt;
-  const float* Yin = (kc & 1) ? job.Y1 : job.Y0;
-  float* Yout = (kc & 1) ? job.Y0 : job.Y1;
-
-  if (MODE != PM_INIT) {
-    for (int i = tid; i < TB * TB; i += kPassThreads) {
-      const int r = i / TB, c = i % TB;
-      const bool in = (r < T && c < T);
-      sW[i] = in ? b.eig->Wbar[r * kMaxT + c] : 0.f;
-      sV[i] = in ? b.eig->V32[r * kMaxT + c] : 0.f;
-    }
+  const int TT = T * T;
+  int& sLast = *sLastp;
+  // ---- level 1: last CTA of each group of kGroup CTAs ----
+  __threadfence();
+  __syncthreads();
+  const int grp = blockIdx.x / kGroup;
+  const int c0 = grp * kGroup;
+  const int c1 = min(c0 + kGroup, (int)gridDim.x);
+  if (tid == 0) {
+    atomicMax(&b.red->t_loop, gtimer());
+    const unsigned t = atomicAdd(&b.red->cnt[grp], 1u);
+    sLast = (t == (unsigned)(c1 - c0 - 1));
   }
   __syncthreads();
-
-  const bool gthr = kGram && (tid < GM::NBLK * GM::NGRP);
-  const int gblk = tid % GM::NBLK, ggrp = tid / GM::NBLK;
-  int bi, bj;
-  blk_coords(gblk, GM::NB, bi, bj);
-  float acc[16];
-#pragma unroll
-  for (int i = 0; i < 16; ++i) acc[i] = 0.f;
-  float e2 = 0.f, l1 = 0.f;
-
-  const int64_t ntiles = (m + kTile - 1) / kTile;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t p = tile * kTile + tid;
-    const bool valid = p < m;
-    float zt[TB];
-    if (MODE == PM_INIT) {
-#pragma unroll
-      for (int t = 0; t < TB; ++t) {
-        const float x = (valid && t < T) ? job.X[t * m + p] : 0.f;
-        zt[t] = x;
-        e2 = fmaf(x, x, e2);
-        l1 += fabsf(x);
-      }
-    } else {
-      float x[TB], s[TB], d[TB], z[TB];
-#pragma unroll
-      for (int t = 0; t < TB; ++t) {
-        const bool in = valid && t < T;
-        x[t] = in ? job.X[t * m + p] : 0.f;
-        s[t] = (in && !first) ? job.S[t * m + p] : 0.f;
-        const float y = (in && !first) ? Yin[t * m + p] : 0.f;
-        d[t] = y * inv_mu;
-        z[t] = form_z(x[t], s[t], y, inv_mu);
-      }
-      if (MODE == PM_GRAM) {
-#pragma unroll
-        for (int j = 0; j < TB; ++j) zt[j] = 0.f;
-#pragma unroll
-        for (int t = 0; t < TB; ++t) {
-#pragma unroll
-          for (int j = 0; j < TB; ++j) zt[j] = fmaf(z[t], sV[t * TB + j], zt[j]);
-        }
-      } else {
-        float q[TB];
-#pragma unroll
-        for (int j = 0; j < TB; ++j) q[j] = 0.f;
-#pragma unroll
-        for (int t = 0; t < TB; ++t) {
-#pragma unroll
-          for (int j = 0; j < TB; ++j) q[j] = fmaf(z[t], sW[t * TB + j], q[j]);
-        }
-#pragma unroll
-        for (int t = 0; t < TB; ++t) {
-          if (t < T) {
-            const float r = s[t] + q[t];                       // X - L + Y/mu
-            const float c = fminf(fmaxf(r, -gamma), gamma);    // clip to +-lambda/mu
-            const float sn = r - c;                            // Eq. 5
-            const float yn = f_mu * c;                         // Eq. 6
-            const float e = c - d[t];                          // X - L - S'
-            e2 = fmaf(e, e, e2);
-            if (valid) {
-              job.S[t * m + p] = sn;
-              Yout[t * m + p] = yn;
-            }
-            z[t] = valid ? form_z(x[t], sn, yn, inv_mu_nxt) : 0.f;
-          }
-        }
-        if (MODE == PM_FUSED) {
-#pragma unroll
-          for (int j = 0; j < TB; ++j) zt[j] = 0.f;
-#pragma unroll
-          for (int t = 0; t < TB; ++t) {
-#pragma unroll
-            for (int j = 0; j < TB; ++j) zt[j] = fmaf(z[t], sV[t * TB + j], zt[j]);
-          }
-        }
-      }
-    }
-    if (kGram) {
-      float4* dst = reinterpret_cast<float4*>(&sZ[tid * ZS]);
-#pragma unroll
-      for (int j4 = 0; j4 < TB / 4; ++j4)
-        dst[j4] = make_float4(zt[4 * j4], zt[4 * j4 + 1], zt[4 * j4 + 2], zt[4 * j4 + 3]);
-      __syncthreads();
-      if (gthr) {
-        for (int pp = ggrp; pp < kTile; pp += GM::NGRP) {
-          const float4 a = *reinterpret_cast<const float4*>(&sZ[pp * ZS + 4 * bi]);
-          const float4 c = *reinterpret_cast<const float4*>(&sZ[pp * ZS + 4 * bj]);
-          const float av[4] = {a.x, a.y, a.z, a.w};
-          const float cv[4] = {c.x, c.y, c.z, c.w};
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u * 4 + v] = fmaf(av[u], cv[v], acc[u * 4 + v]);
-        }
-      }
-      __syncthreads();
-    }
+  if (!sLast) return;
+  __threadfence();
+  if (kGram) {
+    float* gp = b.group_part + (int64_t)grp * TT;
+    sum_rows(b.gram_part, c0, c1, TT, [&](int e, float v) { gp[e] = v; });
   }
+  sum_scalars(b.scal_part, c0, c1, sScal, [&](double s0, double s1) {
+    b.gscal_part[2 * grp] = s0;
+    b.gscal_part[2 * grp + 1] = s1;
+    b.red->cnt[grp] = 0u;
+    atomicMax(&b.red->t_l1, gtimer());
+  });
+  // ---- level 2: last group reducer writes the final sums ----
+  __threadfence();
+  __syncthreads();
+  const int ngroups = (gridDim.x + kGroup - 1) / kGroup;
+  if (tid == 0) {
+    const unsigned t = atomicAdd(&b.red->cnt[kMaxGroups], 1u);
+    sLast = (t == (unsigned)(ngroups - 1));
+  }
+  __syncthreads();
+  if (!sLast) return;
+  __threadfence();
+  if (kGram) {
+    float* G = b.red->G;
+    sum_rows(b.group_part, 0, ngroups, TT, [&](int e, float v) { G[(e / T) * kMaxT + e % T] = v; });
+  }
+  sum_scalars(b.gscal_part, 0, ngroups, sScal, [&](double s0, double s1) {
+    b.red->e2 = s0;
+    b.red->l1 = s1;
+    b.red->cnt[kMaxGroups] = 0u;
+    b.red->t_end = gtimer();
+  });
+}
 
+// sum over the pixels of a staged tile of the 4x4 Gram block (bi, bj) owned by
+// this thread (its pixel group ggrp strides by GramMap<TB>::NGRP)
+template <int TB>
+__device__ __forceinline__ void gram_tile(const float* sZ, float (&acc)[16], int ggrp, int bi, int bj) {
+  constexpr int ZS = TB + 4;
+  for (int pp = ggrp; pp < kTile; pp += GramMap<TB>::NGRP) {
+    const float4 a = *reinterpret_cast<const float4*>(&sZ[pp * ZS + 4 * bi]);
+    const float4 c = *reinterpret_cast<const float4*>(&sZ[pp * ZS + 4 * bj]);
+    const float av[4] = {a.x, a.y, a.z, a.w};
+    const float cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u * 4 + v] = fmaf(av[u], cv[v], acc[u * 4 + v]);
+  }
+}
+
+// End of a pass (all threads of the CTA): write this CTA's partial Gram and
+// scalar sums, then the two-level last-arriving-CTA reduction (fixed order)
+// that leaves the final Gram in red->G and the sums in red->e2, red->l1.
+template <int TB, bool kGram>
+__device__ __forceinline__ void pass_epilogue(Bufs b, const float (&acc)[16], float e2, float l1, float* sZ,
+                                              double (*sRed)[kPassThreads / 32], double* sScal, int* sLastp,
+                                              bool gthr, int ggrp, int gblk) {
+  using GM = GramMap<TB>;
+  const int tid = threadIdx.x;
+  const int T = b.T;
   // ---- CTA partials ----
   const int TT = T * T;
   if (kGram) {
@@ -259,66 +253,130 @@ __global__ void __launch_bounds__(kPassThreads) pass_kernel(Bufs b) {
     }
   }
 
-  // ---- level 1: last CTA of each group of kGroup CTAs ----
-  __threadfence();
-  __syncthreads();
-  const int grp = blockIdx.x / kGroup;
-  const int c0 = grp * kGroup;
-  const int c1 = min(c0 + kGroup, (int)gridDim.x);
-  if (tid == 0) {
-    const unsigned t = atomicAdd(&b.red->cnt[grp], 1u);
-    sLast = (t == (unsigned)(c1 - c0 - 1));
-  }
-  __syncthreads();
-  if (!sLast) return;
-  __threadfence();
-  if (kGram) {
-    for (int e = tid; e < TT; e += kPassThreads) {
-      float s = 0.f, comp = 0.f;
-      for (int c = c0; c < c1; ++c) kahan_add(s, comp, __ldcg(&b.gram_part[(int64_t)c * TT + e]));
-      b.group_part[grp * TT + e] = s;
+  cross_cta_reduce(b, kGram, sScal, sLastp);
+}
+
+// ---------------------------------------------------------------------------
+// Per-pixel pass.  MODE:
+//   PM_INIT   Gram of X (standard basis), ||X||_F^2, ||X||_1
+//   PM_FUSED  Eq. 4-6 update of S, Y + residual + Gram of the next Z in basis V
+//   PM_UPDATE Eq. 4-6 update of S, Y + residual (no Gram)
+//   PM_GRAM   Gram of the current Z in basis V (no update)
+// One thread owns one pixel row (its T frames) of a 256-pixel tile; CTAs
+// stride over tiles; partial Grams and scalars are reduced across CTAs by the
+// last CTA to arrive (two levels, fixed summation order => deterministic).
+// ---------------------------------------------------------------------------
+template <int TB, int MODE>
+__global__ void __launch_bounds__(kPassThreads) pass_kernel(Bufs b) {
+  constexpr bool kGram = (MODE != PM_UPDATE);
+  constexpr int ZS = TB + 4;  // staged row stride in floats (16-byte aligned rows)
+  using GM = GramMap<TB>;
+  __shared__ __align__(16) float sWT[TB * TB];  // Wbar transposed: sWT[j*TB + t] = Wbar[t][j]
+  __shared__ __align__(16) float sVT[TB * TB];  // V transposed
+  __shared__ __align__(16) float sZ[kTile * ZS];
+  __shared__ double sRed[2][kPassThreads / 32];
+  __shared__ double sScal[2 * kMaxGroups];
+  __shared__ int sLast;
+
+  const Ctrl* ctrl = b.ctrl;
+  if (ctrl->done) return;
+  const int tid = threadIdx.x;
+  if (tid == 0) atomicMin(&b.red->t_start, gtimer());
+  const int T = b.T;
+  const int64_t m = b.m;
+  const Job job = *b.job;
+  const int kc = ctrl->k;
+  const bool first = (kc == 0);
+  const float f_mu = ctrl->f_mu, inv_mu = ctrl->f_inv_mu, gamma = ctrl->f_gamma;
+  const float inv_mu_nxt = ctrl->f_inv_mu_nxt;
+  const float* Yin = (kc & 1) ? job.Y1 : job.Y0;
+  float* Yout = (kc & 1) ? job.Y0 : job.Y1;
+
+  if (MODE != PM_INIT) {
+    for (int i = tid; i < TB * TB; i += kPassThreads) {
+      const int r = i / TB, c = i % TB;
+      const bool in = (r < T && c < T);
+      sWT[c * TB + r] = in ? b.eig->Wbar[r * kMaxT + c] : 0.f;
+      sVT[c * TB + r] = in ? b.eig->V32[r * kMaxT + c] : 0.f;
     }
   }
-  if (tid == 0) {
-    double s0 = 0, s1 = 0;
-    for (int c = c0; c < c1; ++c) {
-      s0 += __ldcg(&b.scal_part[2 * c]);
-      s1 += __ldcg(&b.scal_part[2 * c + 1]);
-    }
-    b.gscal_part[2 * grp] = s0;
-    b.gscal_part[2 * grp + 1] = s1;
-    b.red->cnt[grp] = 0u;
-  }
-  // ---- level 2: last group reducer writes the final sums ----
-  __threadfence();
   __syncthreads();
-  const int ngroups = (gridDim.x + kGroup - 1) / kGroup;
-  if (tid == 0) {
-    const unsigned t = atomicAdd(&b.red->cnt[kMaxGroups], 1u);
-    sLast = (t == (unsigned)(ngroups - 1));
-  }
-  __syncthreads();
-  if (!sLast) return;
-  __threadfence();
-  if (kGram) {
-    for (int e = tid; e < TT; e += kPassThreads) {
-      float s = 0.f, comp = 0.f;
-      for (int g = 0; g < ngroups; ++g) kahan_add(s, comp, __ldcg(&b.group_part[g * TT + e]));
-      const int a = e / T, c = e % T;
-      b.red->G[a * kMaxT + c] = s;
+
+  const bool gthr = kGram && (tid < GM::NBLK * GM::NGRP);
+  const int gblk = tid % GM::NBLK, ggrp = tid / GM::NBLK;
+  int bi, bj;
+  blk_coords(gblk, GM::NB, bi, bj);
+  float acc[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) acc[i] = 0.f;
+  float e2 = 0.f, l1 = 0.f;
+
+  const int64_t ntiles = (m + kTile - 1) / kTile;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t p = tile * kTile + tid;
+    const bool valid = p < m;
+    float zt[TB];
+    if (MODE == PM_INIT) {
+#pragma unroll
+      for (int t = 0; t < TB; ++t) {
+        const float x = (valid && t < T) ? job.X[t * m + p] : 0.f;
+        zt[t] = x;
+        e2 = fmaf(x, x, e2);
+        l1 += fabsf(x);
+      }
+    } else {
+      // z = X - S + Y/mu for this pixel row (the argument of Eq. 4)
+      float x[TB], s[TB], d[TB], z[TB];
+#pragma unroll
+      for (int t = 0; t < TB; ++t) {
+        const bool in = valid && t < T;
+        x[t] = in ? job.X[t * m + p] : 0.f;
+        s[t] = (in && !first) ? job.S[t * m + p] : 0.f;
+        const float y = (in && !first) ? Yin[t * m + p] : 0.f;
+        d[t] = y * inv_mu;
+        z[t] = form_z(x[t], s[t], y, inv_mu);
+      }
+      if (MODE == PM_GRAM) {
+#pragma unroll
+        for (int j = 0; j < TB; ++j) zt[j] = row_dot<TB>(z, &sVT[j * TB]);
+      } else {
+        float q[TB];
+#pragma unroll
+        for (int j = 0; j < TB; ++j) q[j] = row_dot<TB>(z, &sWT[j * TB]);   // (Z Wbar)_j
+#pragma unroll
+        for (int t = 0; t < TB; ++t) {
+          if (t < T) {
+            const float r = s[t] + q[t];                       // X - L + Y/mu
+            const float c = fminf(fmaxf(r, -gamma), gamma);    // clip to +-lambda/mu
+            const float sn = r - c;                            // Eq. 5
+            const float yn = f_mu * c;                         // Eq. 6
+            const float e = c - d[t];                          // X - L - S'
+            e2 = fmaf(e, e, e2);
+            if (valid) {
+              job.S[t * m + p] = sn;
+              Yout[t * m + p] = yn;
+            }
+            z[t] = valid ? form_z(x[t], sn, yn, inv_mu_nxt) : 0.f;
+          }
+        }
+        if (MODE == PM_FUSED) {
+#pragma unroll
+          for (int j = 0; j < TB; ++j) zt[j] = row_dot<TB>(z, &sVT[j * TB]);
+        }
+      }
+    }
+    if (kGram) {
+      float4* dst = reinterpret_cast<float4*>(&sZ[tid * ZS]);
+#pragma unroll
+      for (int j4 = 0; j4 < TB / 4; ++j4)
+        dst[j4] = make_float4(zt[4 * j4], zt[4 * j4 + 1], zt[4 * j4 + 2], zt[4 * j4 + 3]);
+      __syncthreads();
+      if (gthr) gram_tile<TB>(sZ, acc, ggrp, bi, bj);
+      __syncthreads();
     }
   }
-  if (tid == 0) {
-    double s0 = 0, s1 = 0;
-    for (int g = 0; g < ngroups; ++g) {
-      s0 += __ldcg(&b.gscal_part[2 * g]);
-      s1 += __ldcg(&b.gscal_part[2 * g + 1]);
-    }
-    b.red->e2 = s0;
-    b.red->l1 = s1;
-    b.red->cnt[kMaxGroups] = 0u;
-    b.red->t_end = gtimer();
-  }
+
+  pass_epilogue<TB, kGram>(b, acc, e2, l1, sZ, sRed, sScal, &sLast, gthr, ggrp, gblk);
 }
 
 // ---------------------------------------------------------------------------
@@ -338,10 +396,114 @@ __device__ __forceinline__ void set_cond(cudaGraphConditionalHandle h, int use, 
 }
 
 __device__ __forceinline__ void refresh_f32(Ctrl* c) {
+  // one FP64 division when mu_nxt = mu_cur (fixed or capped), else two
+  const double inv = 1.0 / c->mu_cur;
   c->f_mu = (float)c->mu_cur;
-  c->f_inv_mu = (float)(1.0 / c->mu_cur);
-  c->f_gamma = (float)(c->lambda / c->mu_cur);
-  c->f_inv_mu_nxt = (float)(1.0 / c->mu_nxt);
+  c->f_inv_mu = (float)inv;
+  c->f_gamma = (float)(c->lambda * inv);
+  c->f_inv_mu_nxt = (float)(c->mu_nxt == c->mu_cur ? inv : 1.0 / c->mu_nxt);
+}
+
+// Control part of an eigen-step, shared by both eigen kernels (all threads call
+// it): accounts the timing of the pass that just ran, applies EF_CHECK (the
+// residual test of Sec. II-A after the iteration, then the mu update) and
+// EF_INIT (||X|| from the init pass; X == 0 finishes with L = S = 0), and sets
+// the graph's loop condition when the solve ends here.  Returns true when the
+// caller goes on to the eigensolve.
+__device__ bool eig_control(Bufs b, int flags, cudaGraphConditionalHandle h, int use_cond, int* sFlag) {
+  Ctrl* ctrl = b.ctrl;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    (*sFlag) = ctrl->done;
+    // account the pass that just ran (the first iteration's pass reads no S, Y
+    // and is left out of the steady-state average)
+    const unsigned long long ts = b.red->t_start, te = b.red->t_end;
+    const unsigned long long tl = b.red->t_loop, t1 = b.red->t_l1;
+    if (ts != ~0ull && te > ts) {
+      if (flags & EF_INIT) {
+        ctrl->init_ns = te - ts;
+      } else if ((flags & EF_CHECK) && ctrl->k >= 1) {
+        ctrl->pass_ns += te - ts;
+        ctrl->pass_cnt += 1;
+        if (tl >= ts && t1 >= tl && te >= t1) {
+          ctrl->pass_phase_ns[0] += tl - ts;
+          ctrl->pass_phase_ns[1] += t1 - tl;
+          ctrl->pass_phase_ns[2] += te - t1;
+        }
+      }
+    }
+    b.red->t_start = ~0ull;
+    b.red->t_loop = 0ull;
+    b.red->t_l1 = 0ull;
+  }
+  __syncthreads();
+  if ((*sFlag)) {
+    if (tid == 0) set_cond(h, use_cond, 0u);
+    return false;
+  }
+  if (flags & EF_CHECK) {
+    if (tid == 0) {
+      const int k = ctrl->k + 1;
+      ctrl->k = k;
+      const double resid = sqrt(b.red->e2) / ctrl->normX;
+      ctrl->resid = resid;
+      int done = 0, st = ST_OK;
+      if (b.red->err) {
+        done = 1;
+        st = ST_ERR_TIMEOUT;
+      } else if (!isfinite(resid)) {
+        done = 1;
+        st = ST_ERR_NONFINITE;
+      } else if (resid <= ctrl->tol) {
+        done = 1;
+      } else if (k >= ctrl->max_iter) {
+        done = 1;
+        st = ST_NOT_CONVERGED;
+      }
+      if (!done) {
+        ctrl->mu_cur = ctrl->mu_nxt;
+        ctrl->mu_nxt = (ctrl->schedule == 0) ? fmin(ctrl->rho * ctrl->mu_cur, ctrl->mu_max) : ctrl->mu_cur;
+        refresh_f32(ctrl);
+      }
+      ctrl->done = done;
+      ctrl->status = st;
+      (*sFlag) = done;
+    }
+    __syncthreads();
+    if ((*sFlag)) {
+      if (tid == 0) set_cond(h, use_cond, 0u);
+      return false;
+    }
+  }
+  if (flags & EF_INIT) {
+    if (tid == 0) {
+      const double x2 = b.red->e2;
+      ctrl->normX2 = x2;
+      ctrl->normX = sqrt(x2);
+      ctrl->normX1 = b.red->l1;
+      int done = 0;
+      if (!isfinite(x2)) {
+        done = 1;
+        ctrl->status = ST_ERR_NONFINITE;
+      } else if (x2 == 0.0) {
+        done = 1;
+        ctrl->status = ST_OK;
+        ctrl->resid = 0.0;
+      }
+      ctrl->done = done;
+      (*sFlag) = done;
+    }
+    __syncthreads();
+    if ((*sFlag)) {
+      if (tid == 0) set_cond(h, use_cond, 0u);
+      return false;
+    }
+  }
+  if (!(flags & EF_EIG)) {
+    if (tid == 0) set_cond(h, use_cond, 1u);
+    return false;
+  }
+  return true;
 }
 
 template <int TB, typename Real>
@@ -366,87 +528,7 @@ __global__ void __launch_bounds__(512) eig_kernel(Bufs b, int flags, cudaGraphCo
   const bool raw = (flags & EF_RAW) != 0;
   const unsigned long long t0 = gtimer();
 
-  if (!raw) {
-    if (tid == 0) {
-      sFlag = ctrl->done;
-      // account the pass that just ran (the first iteration's pass reads no S, Y
-      // and is left out of the steady-state average)
-      const unsigned long long ts = b.red->t_start, te = b.red->t_end;
-      if (ts != ~0ull && te > ts) {
-        if (flags & EF_INIT) {
-          ctrl->init_ns = te - ts;
-        } else if ((flags & EF_CHECK) && ctrl->k >= 1) {
-          ctrl->pass_ns += te - ts;
-          ctrl->pass_cnt += 1;
-        }
-      }
-      b.red->t_start = ~0ull;
-    }
-    __syncthreads();
-    if (sFlag) {
-      if (tid == 0) set_cond(h, use_cond, 0u);
-      return;
-    }
-    if (flags & EF_CHECK) {
-      if (tid == 0) {
-        const int k = ctrl->k + 1;
-        ctrl->k = k;
-        const double resid = sqrt(b.red->e2) / ctrl->normX;
-        ctrl->resid = resid;
-        int done = 0, st = ST_OK;
-        if (!isfinite(resid)) {
-          done = 1;
-          st = ST_ERR_NONFINITE;
-        } else if (resid <= ctrl->tol) {
-          done = 1;
-        } else if (k >= ctrl->max_iter) {
-          done = 1;
-          st = ST_NOT_CONVERGED;
-        }
-        if (!done) {
-          ctrl->mu_cur = ctrl->mu_nxt;
-          ctrl->mu_nxt = (ctrl->schedule == 0) ? fmin(ctrl->rho * ctrl->mu_cur, ctrl->mu_max) : ctrl->mu_cur;
-          refresh_f32(ctrl);
-        }
-        ctrl->done = done;
-        ctrl->status = st;
-        sFlag = done;
-      }
-      __syncthreads();
-      if (sFlag) {
-        if (tid == 0) set_cond(h, use_cond, 0u);
-        return;
-      }
-    }
-    if (flags & EF_INIT) {
-      if (tid == 0) {
-        const double x2 = b.red->e2;
-        ctrl->normX2 = x2;
-        ctrl->normX = sqrt(x2);
-        ctrl->normX1 = b.red->l1;
-        int done = 0;
-        if (!isfinite(x2)) {
-          done = 1;
-          ctrl->status = ST_ERR_NONFINITE;
-        } else if (x2 == 0.0) {
-          done = 1;
-          ctrl->status = ST_OK;
-          ctrl->resid = 0.0;
-        }
-        ctrl->done = done;
-        sFlag = done;
-      }
-      __syncthreads();
-      if (sFlag) {
-        if (tid == 0) set_cond(h, use_cond, 0u);
-        return;
-      }
-    }
-    if (!(flags & EF_EIG)) {
-      if (tid == 0) set_cond(h, use_cond, 1u);
-      return;
-    }
-  }
+  if (!raw && !eig_control(b, flags, h, use_cond, &sFlag)) return;
 
   // ---- load the Gram and the basis ----
   const bool cold = raw || (flags & EF_INIT);
@@ -644,7 +726,14 @@ __global__ void __launch_bounds__(256) final_kernel(Bufs b) {
 }
 
 // Per-solve reset and pointer hand-off (runs before each graph launch).
-__global__ void begin_kernel(Bufs b, const float* X, float* L, float* S, uint8_t* mask, float theta) {
+__global__ void begin_kernel(Bufs b, const float* X, float* L, float* S, uint8_t* mask, float theta,
+                             const __grid_constant__ TmaMaps maps, int use_maps) {
+  if (use_maps) {
+    // 4 x 128-byte descriptors, copied by 64 threads as 16-byte chunks
+    const uint4* src = reinterpret_cast<const uint4*>(&maps);
+    uint4* dst = reinterpret_cast<uint4*>(&b.job->map_x);
+    for (int i = threadIdx.x; i < (int)(sizeof(TmaMaps) / 16); i += blockDim.x) dst[i] = src[i];
+  }
   if (threadIdx.x == 0) {
     Job* j = b.job;
     j->X = X;
@@ -662,9 +751,20 @@ __global__ void begin_kernel(Bufs b, const float* X, float* L, float* S, uint8_t
     c->total_sweeps = 0;
     c->resid = 0.0;
     c->pass_ns = c->pass_cnt = c->eig_ns = c->eig_cnt = c->init_ns = 0ull;
+    for (int i = 0; i < 4; ++i) c->eig_phase_ns[i] = 0ull;
+    for (int i = 0; i < 3; ++i) c->pass_phase_ns[i] = 0ull;
+    b.red->t_loop = 0ull;
+    b.red->t_l1 = 0ull;
+    c->eig_rounds = 0;
     b.red->t_start = ~0ull;
     b.red->t_end = 0ull;
+    b.red->err = 0;
   }
 }
+
+#include "rpca_tc.cuh"
+#include "rpca_pass_tc.cuh"
+#include "rpca_pass_ws.cuh"
+#include "rpca_eig_fast.cuh"
 
 }  // namespace rpca

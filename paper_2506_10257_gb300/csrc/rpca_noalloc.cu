@@ -7,6 +7,7 @@
 // framework's pool.  rpca_gram_noalloc computes the same Gram as rpca_gram
 // with its scratch (partial Grams, reduction counters, control block) in a
 // fixed array compiled into this library instead of allocated memory.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>

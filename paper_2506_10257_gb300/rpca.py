@@ -22,12 +22,12 @@ ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_BUDGET, ERR_TIMEOUT, ERR_NONFINITE, ERR_UNSUPP
 R32, C64 = 0, 1
 PREC_FP32, PREC_TF32X3, PREC_BF16X3, PREC_TF32 = 0, 1, 2, 3
 MU_IALM, MU_FIXED_L1 = 0, 1
-DRIVE_GRAPH, DRIVE_HOST = 0, 1
+DRIVE_GRAPH, DRIVE_HOST, DRIVE_STREAM = 0, 1, 2
 MAX_T = 32
 
 EXPORTED = ["rpca_params_default", "rpca_workspace_size", "rpca_plan_create", "rpca_solve", "rpca_solve_host",
             "rpca_plan_result", "rpca_plan_destroy", "rpca_status_str", "rpca_gram", "rpca_eig",
-            "rpca_gram_noalloc"]
+            "rpca_gram_noalloc", "rpca_plan_timings"]
 
 
 class Params(ctypes.Structure):
@@ -88,6 +88,7 @@ def load(build_if_missing: bool = True):
     lib.rpca_gram.argtypes = [vp, i64, i32, vp, vp, i32, vp]
     lib.rpca_eig.argtypes = [vp, i32, vp, vp, vp]
     lib.rpca_gram_noalloc.argtypes = [vp, i64, i32, vp, vp, vp]
+    lib.rpca_plan_timings.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i32]
     _lib = lib
     return lib
 
@@ -197,6 +198,16 @@ class Plan:
         if st < 0:
             raise RpcaError(st, "rpca_solve_host")
         return L, S, res.as_dict()
+
+    def timings(self) -> dict:
+        """Device-timer breakdown of the eigen-steps of the last solve (microseconds)."""
+        buf = (ctypes.c_double * 9)()
+        st = self.lib.rpca_plan_timings(self.handle, buf, 9)
+        if st != OK:
+            raise RpcaError(st, "rpca_plan_timings")
+        keys = ["eig_load_us", "eig_sweeps_us", "eig_rotprod_us", "eig_basis_us", "eig_rounds", "eigs_timed",
+                "pass_work_us", "pass_red1_us", "pass_red2_us"]
+        return dict(zip(keys, list(buf)))
 
     def result(self) -> dict:
         res = Result()

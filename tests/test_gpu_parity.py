@@ -197,3 +197,44 @@ def test_solve_512x512x20_full_size(rp):
     gpu = gpu_solve(rp, w.frames)
     assert gpu["res"]["status"] == rp.OK
     _check_parity(gpu, ref)
+
+
+def test_stream_drive_equals_graph_drive(rp):
+    w = synth.make_preset("w64x64_t20", seed=12)
+    a = gpu_solve(rp, w.frames, drive=rp.DRIVE_GRAPH)
+    b = gpu_solve(rp, w.frames, drive=rp.DRIVE_STREAM)
+    assert a["res"]["iters"] == b["res"]["iters"]
+    assert np.array_equal(a["L"], b["L"]) and np.array_equal(a["S"], b["S"])
+
+
+# ---- tensor-core contractions (TF32x3, BF16x3, TF32) ---------------------------
+
+PREC_TOL = {"TF32X3": 1e-5, "BF16X3": 1e-4, "TF32": 1e-2}
+
+
+@pytest.mark.parametrize("prec", ["TF32X3", "BF16X3", "TF32"])
+@pytest.mark.parametrize("ny,nx,T", [(64, 64, 20), (63, 64, 20), (20, 17, 7), (16, 16, 32), (40, 40, 13)])
+def test_tensor_core_precisions(rp, prec, ny, nx, T):
+    w = synth.make_window(seed=ny * nx + 3 * T, ny=ny, nx=nx, T=T, n_bound=6, n_free=10)
+    ref = O.rpca_frames(w.frames)
+    gpu = gpu_solve(rp, w.frames, precision=getattr(rp, "PREC_" + prec))
+    tol = PREC_TOL[prec]
+    eL, eS = rel(gpu["L"], ref.L), rel(gpu["S"], ref.S)
+    assert gpu["res"]["status"] in (rp.OK, rp.NOT_CONVERGED)
+    assert eL <= tol and eS <= tol, (prec, eL, eS, gpu["res"], ref.iters)
+
+
+def test_tensor_core_mask_dice(rp):
+    w = synth.make_preset("w64x64_t20", seed=21)
+    ref = O.rpca_frames(w.frames)
+    theta = O.mask_threshold(O.temporal_mean_abs(ref.L), w.bound_mask_gt)
+    mask_ref = O.bound_mask(O.temporal_mean_abs(ref.L), theta)
+    for prec in ("TF32X3", "BF16X3"):
+        gpu = gpu_solve(rp, w.frames, theta=theta, precision=getattr(rp, "PREC_" + prec))
+        assert O.dice(gpu["mask"], mask_ref) >= 0.999
+
+
+def test_host_drive_rejects_tensor_core_precision(rp):
+    with pytest.raises(rp.RpcaError) as ei:
+        rp.Plan(4096, 20, precision=rp.PREC_BF16X3, drive=rp.DRIVE_HOST)
+    assert ei.value.status == rp.ERR_UNSUPPORTED
