@@ -229,7 +229,7 @@ static cudaError_t launch(void* fn, dim3 g, dim3 blk, void** args, cudaStream_t 
 // fast one.
 static void* eig_fn(const rpca_plan_s* pl) { return pl->eig_fp64 ? pl->ks.eig64 : pl->ks.eig_fast; }
 static size_t eig_smem(const rpca_plan_s* pl) { return pl->eig_fp64 ? 0 : pl->ks.eig_fast_smem; }
-static dim3 eig_block(const rpca_plan_s* pl) { return dim3(pl->eig_fp64 ? pl->ks.eig_threads : 256); }
+static dim3 eig_block(const rpca_plan_s* pl) { return dim3(pl->eig_fp64 ? pl->ks.eig_threads : kEigThreads); }
 // Fused per-iteration pass: CUDA-core FP32 or the tensor-core form of the plan's precision.
 static void* fused_fn(const rpca_plan_s* pl) {
   if (pl->p.precision == RPCA_PREC_FP32) return pl->ks.pass[PM_FUSED];
@@ -388,6 +388,7 @@ rpca_status rpca_plan_create(const rpca_params* p, void* workspace, size_t works
   b.T = p->T;
   b.grid = pl->lay.grid;
   b.ngroups = pl->lay.ngroups;
+  b.finalize = 0;
 
   const int mT = (int)std::max<int64_t>(p->m, p->T);
   pl->lambda = p->lambda > 0 ? p->lambda : 1.0 / sqrt((double)mT);
@@ -648,6 +649,7 @@ rpca_status rpca_gram(const float* X, int64_t m, int32_t T, const float* V, doub
     for (int r = 0; r < T; ++r) v32[r * kMaxT + r] = 1.f;
   }
   Bufs b = pl->bufs;
+  b.finalize = 1;
   Job j;
   memset(&j, 0, sizeof(j));
   j.X = X;

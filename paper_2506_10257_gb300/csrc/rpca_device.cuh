@@ -91,6 +91,8 @@ struct RedState {
  unsigned long long t_end;    // end of its final reduction
   unsigned long long t_loop;   // latest time a CTA finished its partials
   unsigned long long t_l1;     // latest end of a first-level group reduction
+  int ngroups_last;            // group partials left by the last pass
+  int gram_last;               // whether that pass produced a Gram
   int err;                     // set by a pass whose bounded device wait ran out
   unsigned int cnt[kMaxGroups + 1];
 };
@@ -128,6 +130,8 @@ struct Bufs {
   int T;
   int grid;
   int ngroups;
+  int finalize;        // 1: the pass itself sums the group partials into red->G, e2, l1;
+                       // 0: the next eigen-step does (saves a serial reduction level)
 };
 
 }  // namespace rpca

@@ -18,6 +18,7 @@
 #pragma once
 
 constexpr int kEigLogSweeps = 10;  // sweeps one eigen-step may take (and log)
+constexpr int kEigThreads = 256;   // threads of the eigen-step CTA
 
 template <int TB>
 struct EigFastSmem {
@@ -34,13 +35,13 @@ struct EigFastSmem {
 };
 
 template <int TB>
-__global__ void __launch_bounds__(256) eig_fast_kernel(Bufs b, int flags, cudaGraphConditionalHandle h,
+__global__ void __launch_bounds__(kEigThreads) eig_fast_kernel(Bufs b, int flags, cudaGraphConditionalHandle h,
                                                        int use_cond) {
   constexpr int K = TB / 2;
   constexpr int NR = TB - 1;
   constexpr int LD = TB + 1;
   constexpr int NE = TB * (TB + 1) / 2;
-  constexpr int EPT = (NE + 255) / 256;  // upper-triangle entries per thread
+  constexpr int EPT = (NE + kEigThreads - 1) / kEigThreads;  // upper-triangle entries per thread
   extern __shared__ __align__(16) unsigned char eig_smem_raw[];
   EigFastSmem<TB>& S = *reinterpret_cast<EigFastSmem<TB>*>(eig_smem_raw);
   __shared__ int sFlag;

@@ -164,10 +164,19 @@ __device__ __noinline__ void cross_cta_reduce(Bufs b, bool kGram, double* sScal,
     b.red->cnt[grp] = 0u;
     atomicMax(&b.red->t_l1, gtimer());
   });
+  const int ngroups = (gridDim.x + kGroup - 1) / kGroup;
+  if (!b.finalize) {
+    // the next eigen-step sums the group partials
+    if (tid == 0) {
+      b.red->ngroups_last = ngroups;
+      b.red->gram_last = kGram ? 1 : 0;
+      atomicMax(&b.red->t_end, gtimer());
+    }
+    return;
+  }
   // ---- level 2: last group reducer writes the final sums ----
   __threadfence();
   __syncthreads();
-  const int ngroups = (gridDim.x + kGroup - 1) / kGroup;
   if (tid == 0) {
     const unsigned t = atomicAdd(&b.red->cnt[kMaxGroups], 1u);
     sLast = (t == (unsigned)(ngroups - 1));
@@ -404,6 +413,24 @@ __device__ __forceinline__ void refresh_f32(Ctrl* c) {
   c->f_inv_mu_nxt = (float)(c->mu_nxt == c->mu_cur ? inv : 1.0 / c->mu_nxt);
 }
 
+// Final sums of a pass that left them as group partials (finalize == 0):
+// red->G, red->e2, red->l1 from the group partials, fixed order.  All threads
+// of the calling CTA take part.
+__device__ void finalize_sums(Bufs b, double* sh) {
+  if (b.finalize) return;
+  const int T = b.T, TT = T * T;
+  const int ng = b.red->ngroups_last;
+  if (b.red->gram_last) {
+    float* G = b.red->G;
+    sum_rows(b.group_part, 0, ng, TT, [&](int e, float v) { G[(e / T) * kMaxT + e % T] = v; });
+  }
+  sum_scalars(b.gscal_part, 0, ng, sh, [&](double s0, double s1) {
+    b.red->e2 = s0;
+    b.red->l1 = s1;
+  });
+  __syncthreads();
+}
+
 // Control part of an eigen-step, shared by both eigen kernels (all threads call
 // it): accounts the timing of the pass that just ran, applies EF_CHECK (the
 // residual test of Sec. II-A after the iteration, then the mu update) and
@@ -413,6 +440,8 @@ __device__ __forceinline__ void refresh_f32(Ctrl* c) {
 __device__ bool eig_control(Bufs b, int flags, cudaGraphConditionalHandle h, int use_cond, int* sFlag) {
   Ctrl* ctrl = b.ctrl;
   const int tid = threadIdx.x;
+  __shared__ double sFin[2 * kMaxGroups];
+  if (!ctrl->done) finalize_sums(b, sFin);
   if (tid == 0) {
     (*sFlag) = ctrl->done;
     // account the pass that just ran (the first iteration's pass reads no S, Y
@@ -435,6 +464,7 @@ __device__ bool eig_control(Bufs b, int flags, cudaGraphConditionalHandle h, int
     b.red->t_start = ~0ull;
     b.red->t_loop = 0ull;
     b.red->t_l1 = 0ull;
+    b.red->t_end = 0ull;
   }
   __syncthreads();
   if ((*sFlag)) {

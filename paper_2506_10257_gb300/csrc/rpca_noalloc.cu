@@ -137,6 +137,7 @@ extern "C" rpca_status rpca_gram_noalloc(const float* X, int64_t m, int32_t T, c
   b.T = T;
   b.grid = (int)grid;
   b.ngroups = (int)((grid + kGroup - 1) / kGroup);
+  b.finalize = 1;
 
   cudaStream_t s = (cudaStream_t)stream;
   // The array keeps the previous call's contents: clear the control block and

@@ -48,7 +48,7 @@ __host__ __device__ constexpr size_t pass_tc_smem() {
   return 4 * (size_t)TcShape<KP, BF16>::B_BYTES + pass_tc_aregion<TB, KP, BF16>();
 }
 
-constexpr uint32_t kTcWaitLimit = 1u << 22;  // polls of an MMA-completion barrier before giving up
+constexpr uint32_t kTcWaitLimit = 1u << 21;  // tries (each may suspend ~1 us) before a wait gives up
 
 template <int TB, int KP, bool BF16, bool SPLIT>
 __global__ void __launch_bounds__(kPassThreads, 1) pass_tc_kernel(Bufs b) {

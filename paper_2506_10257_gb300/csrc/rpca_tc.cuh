@@ -60,13 +60,14 @@ __device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
   asm volatile("fence.mbarrier_init.release.cluster;");
 }
 
-// Wait for phase `parity` of an mbarrier, giving up after `limit` polls.
+// Wait for phase `parity` of an mbarrier, giving up after `limit` tries.
 // Returns true when the phase completed.
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint32_t limit) {
   uint32_t done = 0;
   for (uint32_t it = 0; it < limit; ++it) {
+    // the thread may be suspended up to ~1 us inside try_wait instead of spinning
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 1000;\n selp.u32 %0, 1, 0, p;\n}"
         : "=r"(done)
         : "r"(smem_u32(mbar)), "r"(parity));
     if (done) return true;
