@@ -163,6 +163,56 @@ void rpca_plan_destroy(rpca_plan_t plan);
 
 const char* rpca_status_str(int32_t status);
 
+/* ---- batched persistent form --------------------------------------------- */
+
+/* Many independent windows (each its own Casorati matrix, Sec. II-A, with its
+ * own m, T and parameters) solved by one persistent cooperative launch,
+ * captured in a CUDA graph: every window runs the same iteration as
+ * rpca_solve (Eq. 4-6, stopping test of Sec. II-A), so each result equals the
+ * window's single solve within the precision's tolerance.  The paper solves
+ * one window at a time; batching is this library's throughput form. */
+typedef struct rpca_batch_s* rpca_batch_t;
+
+/* Device buffers of one window of a batch, laid out as in rpca_solve. */
+typedef struct {
+  const void* X;    /* m x T frame-major, read only, 16-byte aligned */
+  void* L;          /* m x T, written (also the first dual buffer during the solve) */
+  void* S;          /* m x T, written */
+  uint8_t* mask;    /* m bytes or NULL: temporal mean |L| >= theta */
+  float theta;
+  int32_t pad_;
+} rpca_window;
+
+/* Creates a batch of n windows with parameters params[0..n) (copied).  The
+ * batch owns one workspace per window (rpca_workspace_size bytes each) and the
+ * launch descriptor.  precision must be RPCA_PREC_FP32 (else
+ * RPCA_ERR_UNSUPPORTED); drive is ignored.  The CTA schedule is the one tuned
+ * before for the same window shapes in this process (rpca_batch_tune), else a
+ * default (one lane per window, CTAs proportional to m*T). */
+rpca_status rpca_batch_create(const rpca_params* params, int32_t n, rpca_batch_t* out);
+
+/* Solves windows win[0..n) in one launch on `stream`.  With out != NULL
+ * (n entries) the call waits and fills each window's rpca_result, returning the
+ * worst status (negative first); with out == NULL it returns at once.  The
+ * window buffers must stay alive until the stream reaches the launch's end. */
+rpca_status rpca_batch_solve(rpca_batch_t batch, const rpca_window* win, void* stream, rpca_result* out);
+
+/* Autotuner: times every candidate schedule (lanes, CTA share exponent, CTAs
+ * per SM) on these windows, `reps` timed solves each (median), keeps the
+ * fastest for this batch and for later batches of the same shapes in this
+ * process.  *best_ms (nullable) gets its median time per solve.  Synchronous. */
+rpca_status rpca_batch_tune(rpca_batch_t batch, const rpca_window* win, void* stream, int32_t reps,
+                            double* best_ms);
+
+/* Schedule in use: info[0..n) = {grid CTAs, lanes, CTAs per SM,
+ * 1000 * share exponent, max resident CTAs per SM, graph captured (0/1)}. */
+rpca_status rpca_batch_info(rpca_batch_t batch, int32_t* info, int32_t n);
+
+/* CTAs each window uses (n >= number of windows). */
+rpca_status rpca_batch_window_ctas(rpca_batch_t batch, int32_t* ctas, int32_t n);
+
+void rpca_batch_destroy(rpca_batch_t batch);
+
 /* ---- kernel-level entry points (each one step of the iteration) ---------- */
 
 /* Rotated Gram of a window: G = (Z V)^T (Z V) with Z = X (frame-major m x T,

@@ -15,7 +15,7 @@ CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "librpca.so")
 GENCODE = "arch=compute_103a,code=sm_103a"
-UNITS = ["rpca_capi.cu", "rpca_noalloc.cu"]
+UNITS = ["rpca_capi.cu", "rpca_batch.cu", "rpca_noalloc.cu"]
 
 
 def _sources():
@@ -42,9 +42,24 @@ def build(force: bool = False, verbose: bool = False) -> str:
             return LIB
     os.makedirs(LIBDIR, exist_ok=True)
     tmp = LIB + ".tmp"
-    cmd = [nvcc_path(), "-gencode", GENCODE, "-O3", "-lineinfo", "-std=c++17",
-           "-Xcompiler", "-fPIC", "-shared", "-I", os.path.join(ROOT, "include"),
-           "-o", tmp] + [os.path.join(CSRC, f) for f in UNITS]
+    # -dlcm=cg: global loads are cached in L2 only; persistent kernels read
+    # control data that other CTAs rewrite while they run.
+    flags = ["-gencode", GENCODE, "-O3", "-lineinfo", "-std=c++17", "-Xptxas", "-dlcm=cg",
+             "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
+    nvcc = nvcc_path()
+    objs = []
+    procs = []
+    for f in UNITS:  # the units compile in parallel
+        obj = os.path.join(LIBDIR, f.replace(".cu", ".o"))
+        objs.append(obj)
+        cmd = [nvcc] + flags + ["-c", "-o", obj, os.path.join(CSRC, f)]
+        if verbose:
+            print(" ".join(cmd))
+        procs.append((f, subprocess.Popen(cmd)))
+    failed = [f for f, p in procs if p.wait() != 0]
+    if failed:
+        raise RuntimeError("nvcc failed on " + ", ".join(failed))
+    cmd = [nvcc, "-gencode", GENCODE, "-shared", "-o", tmp] + objs
     if verbose:
         print(" ".join(cmd))
     subprocess.run(cmd, check=True)

@@ -1,0 +1,213 @@
+// rpca_batch.cuh -- many windows in one persistent, cooperative launch
+// (included inside namespace rpca).
+//
+// Every CTA of the grid is resident for the whole launch.  The CTAs are split
+// into contiguous ranges, one per window (sizes chosen on the host from the
+// windows' work); a window's CTAs run its whole solve without returning to the
+// host: the init pass, then per iteration the fused pass over the window's
+// pixels.  The CTA that completes a pass's cross-CTA reduction runs that
+// window's eigen-step right away and publishes it by bumping the window's
+// generation counter; the other CTAs of the window wait on that counter
+// (bounded, with back-off) and continue with the next pass.  While one
+// window's CTAs wait for its eigen-step, the other windows' CTAs on the same
+// GPU keep working, so one window's latency-bound step overlaps the others'
+// bandwidth-bound passes.  A final per-CTA step writes L and the mask.
+#pragma once
+
+constexpr int kMaxBatch = 1024;         // windows per launch
+constexpr int kMaxLanes = 1024;         // CTA ranges per launch
+constexpr int kBatchThreads = kPassThreads;
+static_assert(kEigThreads <= kBatchThreads, "the eigen-step runs on one batch CTA");
+
+struct WinDesc {
+  Bufs b;              // the window's plan buffers (finalize = 1, grid = CTAs it uses)
+  const float* X;      // the window's input and outputs (frame-major m x T)
+  float* L;
+  float* S;
+  uint8_t* mask;
+  float theta;
+  int TB;              // frame bucket of the window's kernels
+  unsigned int gen;    // publications so far (0 when the host uploads the batch)
+  int pad_;
+};
+
+// A lane: a contiguous range of CTAs that runs windows [w0, w1) one after the other.
+struct LaneDesc {
+  int cta0, ncta, w0, w1;
+};
+
+struct BatchDesc {
+  int nwin;
+  int nlanes;
+  unsigned long long spin_limit;   // polls of a publication wait before it gives up
+  unsigned int stop;               // set once any wait ran out: every later wait gives up at once
+  unsigned int pad_;
+  LaneDesc lane[kMaxLanes];
+  WinDesc w[kMaxBatch];
+};
+
+// largest dynamic shared memory any window's steps need
+template <int TB>
+__host__ __device__ constexpr size_t batch_smem_tb() {
+  return pass_simt_smem<TB>() > sizeof(EigFastSmem<TB>) ? pass_simt_smem<TB>() : sizeof(EigFastSmem<TB>);
+}
+__host__ __device__ constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
+template <int TBMAX>
+__host__ __device__ constexpr size_t batch_smem() {
+  size_t s = batch_smem_tb<8>();
+  if (TBMAX >= 12) s = cmax(s, batch_smem_tb<12>());
+  if (TBMAX >= 16) s = cmax(s, batch_smem_tb<16>());
+  if (TBMAX >= 20) s = cmax(s, batch_smem_tb<20>());
+  if (TBMAX >= 24) s = cmax(s, batch_smem_tb<24>());
+  if (TBMAX >= 32) s = cmax(s, batch_smem_tb<32>());
+  return s;
+}
+
+// Copies every window's control block into out[0..nwin) (one CTA per window).
+static __global__ void batch_gather_ctrl(const BatchDesc* bd, Ctrl* out) {
+  const int w = blockIdx.x;
+  if (w >= bd->nwin) return;
+  const unsigned* src = reinterpret_cast<const unsigned*>(bd->w[w].b.ctrl);
+  unsigned* dst = reinterpret_cast<unsigned*>(out + w);
+  for (int i = threadIdx.x; i < (int)(sizeof(Ctrl) / 4); i += blockDim.x) dst[i] = __ldcg(src + i);
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Wait until the window's publication counter reaches `target`; false if the
+// wait ran out.  Publications: 1 = state reset, 2 = first eigen-step, then one
+// per iteration, so every CTA knows which value to expect.
+// Once a wait of the launch has run out, `stop` makes every other wait give
+// up at once, so a fault costs one wait limit, not one per window.
+__device__ __forceinline__ bool gen_wait(const unsigned int* gen, unsigned int target, unsigned long long limit,
+                                         unsigned int* stop) {
+  __shared__ int sOk;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    unsigned long long n = 0;
+    unsigned int ns = 64;
+    while (ld_acquire_u32(gen) < target) {
+      if (++n > limit || ld_acquire_u32(stop) != 0u) {
+        ok = 0;
+        atomicExch(stop, 1u);
+        break;
+      }
+      __nanosleep(ns);
+      if (ns < 1024) ns <<= 1;
+    }
+    sOk = ok;
+  }
+  __syncthreads();
+  return sOk != 0;
+}
+
+__device__ __forceinline__ void gen_publish(unsigned int* gen) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(gen, 1u);
+  }
+}
+
+// A wait ran out: mark the window failed so its other CTAs stop as well.
+__device__ __forceinline__ void window_fail(Bufs b) {
+  if (threadIdx.x == 0) {
+    atomicExch(&b.red->err, 1);
+    atomicExch(&b.ctrl->status, ST_ERR_TIMEOUT);
+    atomicExch(&b.ctrl->done, 1);
+  }
+  __syncthreads();
+}
+
+template <int TB>
+__device__ void run_window(WinDesc& wd, int lc, unsigned char* dsm, unsigned long long limit, unsigned int* stop) {
+  const Bufs b = wd.b;
+  const int nc = b.grid;
+  if (lc >= nc) return;  // the window uses fewer CTAs than its lane has
+  unsigned int* gen = &wd.gen;
+  // ---- the window's first CTA resets its state, then everyone starts ----
+  if (lc == 0) {
+    if (threadIdx.x == 0) {
+      Job* j = b.job;
+      j->X = wd.X;
+      j->S = wd.S;
+      j->Y0 = wd.L;
+      j->L = wd.L;
+      j->mask = wd.mask;
+      j->theta = wd.theta;
+      Ctrl* c = b.ctrl;
+      c->k = 0;
+      c->done = 0;
+      c->status = 0;
+      c->rank = 0;
+      c->sweeps = 0;
+      c->total_sweeps = 0;
+      c->resid = 0.0;
+      c->pass_ns = c->pass_cnt = c->eig_ns = c->eig_cnt = c->init_ns = 0ull;
+      for (int i = 0; i < 4; ++i) c->eig_phase_ns[i] = 0ull;
+      for (int i = 0; i < 3; ++i) c->pass_phase_ns[i] = 0ull;
+      c->eig_rounds = 0;
+      b.red->t_start = ~0ull;
+      b.red->t_end = 0ull;
+      b.red->t_loop = 0ull;
+      b.red->t_l1 = 0ull;
+      b.red->err = 0;
+      // counters left behind by an aborted earlier solve
+      for (int g = 0; g <= kMaxGroups; ++g) b.red->cnt[g] = 0u;
+    }
+    gen_publish(gen);
+  }
+  if (!gen_wait(gen, 1u, limit, stop)) {
+    window_fail(b);
+    return;
+  }
+  // ---- init pass + first eigen-step, then the iterations ----
+  int flags = EF_INIT | EF_EIG;
+  const int max_iter = __ldcg(&b.ctrl->max_iter);
+  for (int it = 0; it <= max_iter + 1; ++it) {
+    const bool fin = (it == 0) ? pass_body<TB, PM_INIT>(b, lc, nc, dsm) : pass_body<TB, PM_FUSED>(b, lc, nc, dsm);
+    if (fin) {
+      __syncthreads();
+      eig_fast_body<TB>(b, flags, 0, 0, dsm);
+      gen_publish(gen);
+    }
+    if (!gen_wait(gen, 2u + (unsigned)it, limit, stop)) {
+      window_fail(b);
+      return;
+    }
+    flags = EF_CHECK | EF_EIG;
+    if (__ldcg(&b.ctrl->done)) break;
+  }
+  final_body(b, lc, nc);
+}
+
+// Windows of frame bucket <= TBMAX (the batch's largest), lane by lane.
+template <int TBMAX>
+__global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchDesc* bd) {
+  extern __shared__ __align__(16) unsigned char batch_dsm[];
+  const int nl = bd->nlanes;
+  int l = 0;
+  while (l + 1 < nl && (int)blockIdx.x >= bd->lane[l + 1].cta0) ++l;
+  const LaneDesc ld = bd->lane[l];
+  const int lc = (int)blockIdx.x - ld.cta0;
+  if (lc < 0 || lc >= ld.ncta) return;
+  const unsigned long long limit = bd->spin_limit;
+  for (int w = ld.w0; w < ld.w1; ++w) {
+    WinDesc& wd = bd->w[w];
+    switch (wd.TB) {
+      case 8: run_window<8>(wd, lc, batch_dsm, limit, &bd->stop); break;
+      case 12: if constexpr (TBMAX >= 12) run_window<12>(wd, lc, batch_dsm, limit, &bd->stop); break;
+      case 16: if constexpr (TBMAX >= 16) run_window<16>(wd, lc, batch_dsm, limit, &bd->stop); break;
+      case 20: if constexpr (TBMAX >= 20) run_window<20>(wd, lc, batch_dsm, limit, &bd->stop); break;
+      case 24: if constexpr (TBMAX >= 24) run_window<24>(wd, lc, batch_dsm, limit, &bd->stop); break;
+      case 32: if constexpr (TBMAX >= 32) run_window<32>(wd, lc, batch_dsm, limit, &bd->stop); break;
+      default: break;
+    }
+    __syncthreads();
+  }
+}

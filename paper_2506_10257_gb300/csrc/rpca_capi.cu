@@ -12,6 +12,7 @@
 
 #include "../../include/rpca.h"
 #include "rpca_kernels.cuh"
+#include "rpca_internal.h"
 
 using namespace rpca;
 
@@ -19,6 +20,7 @@ namespace {
 
 struct KernelSet {
   void* pass[4];
+  size_t pass_smem;        // dynamic shared memory of the CUDA-core passes
   void* pass_tc[4];        // fused pass with tensor-core contractions, per rpca_precision (0 unused)
   size_t pass_tc_smem[4];
   void* pass_ws[4];        // the same, warp-specialised and fed by TMA (needs m % 4 == 0)
@@ -38,6 +40,7 @@ KernelSet make_set() {
   k.pass[PM_FUSED] = (void*)pass_kernel<TB, PM_FUSED>;
   k.pass[PM_UPDATE] = (void*)pass_kernel<TB, PM_UPDATE>;
   k.pass[PM_GRAM] = (void*)pass_kernel<TB, PM_GRAM>;
+  k.pass_smem = pass_simt_smem<TB>();
   k.eig32 = (void*)eig_kernel<TB, float>;
   k.eig64 = (void*)eig_kernel<TB, double>;
   k.eig_fast = (void*)eig_fast_kernel<TB>;
@@ -232,11 +235,11 @@ static size_t eig_smem(const rpca_plan_s* pl) { return pl->eig_fp64 ? 0 : pl->ks
 static dim3 eig_block(const rpca_plan_s* pl) { return dim3(pl->eig_fp64 ? pl->ks.eig_threads : kEigThreads); }
 // Fused per-iteration pass: CUDA-core FP32 or the tensor-core form of the plan's precision.
 static void* fused_fn(const rpca_plan_s* pl) {
-  if (pl->p.precision == RPCA_PREC_FP32) return pl->ks.pass[PM_FUSED];
+  if (pl->p.precision == RPCA_PREC_FP32) return pl->ks.pass[PM_FUSED];  // dynamic smem: ks.pass_smem
   return pl->use_ws ? pl->ks.pass_ws[pl->p.precision] : pl->ks.pass_tc[pl->p.precision];
 }
 static size_t fused_smem(const rpca_plan_s* pl) {
-  if (pl->p.precision == RPCA_PREC_FP32) return 0;
+  if (pl->p.precision == RPCA_PREC_FP32) return pl->ks.pass_smem;
   return pl->use_ws ? pl->ks.pass_ws_smem[pl->p.precision] : pl->ks.pass_tc_smem[pl->p.precision];
 }
 static dim3 fused_grid(const rpca_plan_s* pl) { return dim3(pl->use_ws ? pl->lay.ws_grid : pl->lay.grid); }
@@ -272,7 +275,7 @@ static rpca_status build_graph(rpca_plan_s* pl) {
   void* a_eig0[] = {&b, &f_init, &h, &use_cond, &nulld, &nullo, &nullo};
   void* a_eig1[] = {&b, &f_iter, &h, &use_cond, &nulld, &nullo, &nullo};
   cudaGraphNode_t n_init, n_eig0, n_while, n_fin, n_pass, n_eig;
-  CK(add_kernel(pl->graph, &n_init, nullptr, 0, pl->ks.pass[PM_INIT], pg, pb, a_pass));
+  CK(add_kernel(pl->graph, &n_init, nullptr, 0, pl->ks.pass[PM_INIT], pg, pb, a_pass, pl->ks.pass_smem));
   CK(add_kernel(pl->graph, &n_eig0, &n_init, 1, eig_fn(pl), eg, eb, a_eig0, es));
 
   alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
@@ -291,6 +294,42 @@ static rpca_status build_graph(rpca_plan_s* pl) {
   CK(add_kernel(pl->graph, &n_fin, &n_while, 1, (void*)final_kernel, dim3(fgrid), dim3(256), a_pass));
   CK(cudaGraphInstantiate(&pl->exec, pl->graph, 0));
   return RPCA_OK;
+}
+
+namespace rpca {
+
+void result_from_ctrl(double lambda, const Ctrl& c, rpca_result* out) {
+  memset(out, 0, sizeof(*out));
+  out->status = c.status;
+  out->iters = c.k;
+  out->rank = c.rank;
+  out->sweeps = c.total_sweeps;
+  out->resid = c.resid;
+  out->mu = c.mu_cur;
+  out->normX = c.normX;
+  out->lambda = lambda;
+  out->pass_us = c.pass_cnt ? (double)c.pass_ns / (double)c.pass_cnt * 1e-3 : 0.0;
+  out->eig_us = c.eig_cnt ? (double)c.eig_ns / (double)c.eig_cnt * 1e-3 : 0.0;
+  out->init_us = (double)c.init_ns * 1e-3;
+  out->passes_timed = (int32_t)c.pass_cnt;
+  out->eigs_timed = (int32_t)c.eig_cnt;
+}
+
+rpca_status plan_view(rpca_plan_t pl, PlanView* v) {
+  if (!pl || !v) return RPCA_ERR_ARG;
+  v->bufs = pl->bufs;
+  v->m = pl->p.m;
+  v->T = pl->p.T;
+  v->max_grid = std::max(pl->lay.grid, pl->lay.ws_grid);
+  v->lambda = pl->lambda;
+  v->y1 = (float*)(pl->ws + pl->lay.ybuf);
+  return RPCA_OK;
+}
+
+}  // namespace rpca
+
+static void fill_result(const rpca_plan_s* pl, const Ctrl& c, rpca_result* out) {
+  result_from_ctrl(pl->lambda, c, out);
 }
 
 extern "C" {
@@ -432,22 +471,6 @@ rpca_status rpca_plan_create(const rpca_params* p, void* workspace, size_t works
   return RPCA_OK;
 }
 
-static void fill_result(const rpca_plan_s* pl, const Ctrl& c, rpca_result* out) {
-  memset(out, 0, sizeof(*out));
-  out->status = c.status;
-  out->iters = c.k;
-  out->rank = c.rank;
-  out->sweeps = c.total_sweeps;
-  out->resid = c.resid;
-  out->mu = c.mu_cur;
-  out->normX = c.normX;
-  out->lambda = pl->lambda;
-  out->pass_us = c.pass_cnt ? (double)c.pass_ns / (double)c.pass_cnt * 1e-3 : 0.0;
-  out->eig_us = c.eig_cnt ? (double)c.eig_ns / (double)c.eig_cnt * 1e-3 : 0.0;
-  out->init_us = (double)c.init_ns * 1e-3;
-  out->passes_timed = (int32_t)c.pass_cnt;
-  out->eigs_timed = (int32_t)c.eig_cnt;
-}
 
 // The plain form: separate Gram and update passes, residual read back by the
 // host after every iteration (one host synchronisation per iteration).
@@ -464,18 +487,18 @@ static rpca_status run_host_loop(rpca_plan_s* pl, cudaStream_t s) {
   void* a_init[] = {&b, &f_init, &h, &use_cond, &nulld, &nullo, &nullo};
   void* a_check[] = {&b, &f_check, &h, &use_cond, &nulld, &nullo, &nullo};
   void* a_eig[] = {&b, &f_eig, &h, &use_cond, &nulld, &nullo, &nullo};
-  CK(launch(pl->ks.pass[PM_INIT], pg, pb, a_pass, s));
+  CK(launch(pl->ks.pass[PM_INIT], pg, pb, a_pass, s, pl->ks.pass_smem));
   CK(launch(eig_fn(pl), eg, eb, a_init, s, es));
   for (int it = 0; it <= pl->p.max_iter; ++it) {
     CK(cudaMemcpyAsync(pl->ctrl_host, b.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (pl->ctrl_host->done) break;
-    CK(launch(pl->ks.pass[PM_UPDATE], pg, pb, a_pass, s));
+    CK(launch(pl->ks.pass[PM_UPDATE], pg, pb, a_pass, s, pl->ks.pass_smem));
     CK(launch(eig_fn(pl), eg, eb, a_check, s, es));
     CK(cudaMemcpyAsync(pl->ctrl_host, b.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (pl->ctrl_host->done) break;
-    CK(launch(pl->ks.pass[PM_GRAM], pg, pb, a_pass, s));
+    CK(launch(pl->ks.pass[PM_GRAM], pg, pb, a_pass, s, pl->ks.pass_smem));
     CK(launch(eig_fn(pl), eg, eb, a_eig, s, es));
   }
   const int fgrid = (int)std::min<int64_t>((pl->p.m + 255) / 256, 4096);
@@ -498,7 +521,7 @@ static rpca_status run_stream_loop(rpca_plan_s* pl, cudaStream_t s) {
   void* a_pass[] = {&b};
   void* a_init[] = {&b, &f_init, &h, &use_cond, &nulld, &nullo, &nullo};
   void* a_iter[] = {&b, &f_iter, &h, &use_cond, &nulld, &nullo, &nullo};
-  CK(launch(pl->ks.pass[PM_INIT], pg, pb, a_pass, s));
+  CK(launch(pl->ks.pass[PM_INIT], pg, pb, a_pass, s, pl->ks.pass_smem));
   CK(launch(eig_fn(pl), eg, eb, a_init, s, es));
   for (int it = 0; it < pl->p.max_iter; ++it) {
     if (it % 8 == 0) {
@@ -665,7 +688,8 @@ rpca_status rpca_gram(const float* X, int64_t m, int32_t T, const float* V, doub
   if (e == cudaSuccess) e = cudaMemcpy(b.job, &j, sizeof(Job), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(b.eig->V32, v32.data(), sizeof(float) * kMaxT * kMaxT, cudaMemcpyHostToDevice);
   void* a_pass[] = {&b};
-  if (e == cudaSuccess) e = launch(pl->ks.pass[PM_GRAM], dim3(pl->lay.grid), dim3(kPassThreads), a_pass, s);
+  if (e == cudaSuccess)
+    e = launch(pl->ks.pass[PM_GRAM], dim3(pl->lay.grid), dim3(kPassThreads), a_pass, s, pl->ks.pass_smem);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e == cudaSuccess) e = cudaMemcpy(gred.data(), b.red->G, sizeof(float) * kMaxT * kMaxT, cudaMemcpyDeviceToHost);
   std::vector<double> gh((size_t)T * T);

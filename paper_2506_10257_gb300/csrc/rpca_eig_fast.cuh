@@ -34,16 +34,16 @@ struct EigFastSmem {
   float g[TB];
 };
 
+// The eigen-step on one CTA of kEigThreads threads; `dsm` holds
+// sizeof(EigFastSmem<TB>) bytes of shared memory.
 template <int TB>
-__global__ void __launch_bounds__(kEigThreads) eig_fast_kernel(Bufs b, int flags, cudaGraphConditionalHandle h,
-                                                       int use_cond) {
+__device__ void eig_fast_body(Bufs b, int flags, cudaGraphConditionalHandle h, int use_cond, unsigned char* dsm) {
   constexpr int K = TB / 2;
   constexpr int NR = TB - 1;
   constexpr int LD = TB + 1;
   constexpr int NE = TB * (TB + 1) / 2;
   constexpr int EPT = (NE + kEigThreads - 1) / kEigThreads;  // upper-triangle entries per thread
-  extern __shared__ __align__(16) unsigned char eig_smem_raw[];
-  EigFastSmem<TB>& S = *reinterpret_cast<EigFastSmem<TB>*>(eig_smem_raw);
+  EigFastSmem<TB>& S = *reinterpret_cast<EigFastSmem<TB>*>(dsm);
   __shared__ int sFlag;
   __shared__ double sTau;
 
@@ -284,4 +284,11 @@ __global__ void __launch_bounds__(kEigThreads) eig_fast_kernel(Bufs b, int flags
     ctrl->eig_rounds += rounds_run;
     set_cond(h, use_cond, 1u);
   }
+}
+
+template <int TB>
+__global__ void __launch_bounds__(kEigThreads) eig_fast_kernel(Bufs b, int flags, cudaGraphConditionalHandle h,
+                                                               int use_cond) {
+  extern __shared__ __align__(16) unsigned char eig_smem_raw[];
+  eig_fast_body<TB>(b, flags, h, use_cond, eig_smem_raw);
 }

@@ -1,0 +1,24 @@
+// rpca_internal.h -- what the library's translation units share beyond the
+// public C ABI: a read-only view of a plan's device buffers.
+#pragma once
+#include "../../include/rpca.h"
+#include "rpca_device.cuh"
+
+namespace rpca {
+
+struct PlanView {
+  Bufs bufs;          // device buffers of the plan (finalize as created)
+  int64_t m;
+  int T;
+  int max_grid;       // CTAs whose partials fit in the plan's workspace
+  double lambda;      // resolved lambda
+  float* y1;          // second dual buffer (workspace)
+};
+
+// Fills *v from a plan; RPCA_ERR_ARG for a null plan.
+rpca_status plan_view(rpca_plan_t plan, PlanView* v);
+
+// rpca_result of a solve from its control block.
+void result_from_ctrl(double lambda, const Ctrl& c, rpca_result* out);
+
+}  // namespace rpca

@@ -131,11 +131,13 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-// Reduction across CTAs after every CTA wrote its partial Gram (gram_part)
-// and scalar sums (scal_part): the last CTA of each group of kGroup sums its
-// group, the last group reducer sums the groups, in fixed order, into red->G,
-// red->e2 and red->l1.  Called by all threads of every CTA.
-__device__ __noinline__ void cross_cta_reduce(Bufs b, bool kGram, double* sScal, int* sLastp) {
+// Reduction across the nc CTAs of a pass (this one is number lc) after every
+// CTA wrote its partial Gram (gram_part) and scalar sums (scal_part): the last
+// CTA of each group of kGroup sums its group, the last group reducer sums the
+// groups, in fixed order, into red->G, red->e2 and red->l1 (only when
+// b.finalize; otherwise the next eigen-step does).  Called by all threads of
+// every CTA; returns true in the CTA that wrote the final sums.
+static __device__ __noinline__ bool cross_cta_reduce(Bufs b, bool kGram, double* sScal, int* sLastp, int lc, int nc) {
   const int tid = threadIdx.x;
   const int T = b.T;
   const int TT = T * T;
@@ -143,16 +145,16 @@ __device__ __noinline__ void cross_cta_reduce(Bufs b, bool kGram, double* sScal,
   // ---- level 1: last CTA of each group of kGroup CTAs ----
   __threadfence();
   __syncthreads();
-  const int grp = blockIdx.x / kGroup;
+  const int grp = lc / kGroup;
   const int c0 = grp * kGroup;
-  const int c1 = min(c0 + kGroup, (int)gridDim.x);
+  const int c1 = min(c0 + kGroup, nc);
   if (tid == 0) {
     atomicMax(&b.red->t_loop, gtimer());
     const unsigned t = atomicAdd(&b.red->cnt[grp], 1u);
     sLast = (t == (unsigned)(c1 - c0 - 1));
   }
   __syncthreads();
-  if (!sLast) return;
+  if (!sLast) return false;
   __threadfence();
   if (kGram) {
     float* gp = b.group_part + (int64_t)grp * TT;
@@ -164,7 +166,7 @@ __device__ __noinline__ void cross_cta_reduce(Bufs b, bool kGram, double* sScal,
     b.red->cnt[grp] = 0u;
     atomicMax(&b.red->t_l1, gtimer());
   });
-  const int ngroups = (gridDim.x + kGroup - 1) / kGroup;
+  const int ngroups = (nc + kGroup - 1) / kGroup;
   if (!b.finalize) {
     // the next eigen-step sums the group partials
     if (tid == 0) {
@@ -172,7 +174,7 @@ __device__ __noinline__ void cross_cta_reduce(Bufs b, bool kGram, double* sScal,
       b.red->gram_last = kGram ? 1 : 0;
       atomicMax(&b.red->t_end, gtimer());
     }
-    return;
+    return false;
   }
   // ---- level 2: last group reducer writes the final sums ----
   __threadfence();
@@ -182,7 +184,7 @@ __device__ __noinline__ void cross_cta_reduce(Bufs b, bool kGram, double* sScal,
     sLast = (t == (unsigned)(ngroups - 1));
   }
   __syncthreads();
-  if (!sLast) return;
+  if (!sLast) return false;
   __threadfence();
   if (kGram) {
     float* G = b.red->G;
@@ -194,6 +196,7 @@ __device__ __noinline__ void cross_cta_reduce(Bufs b, bool kGram, double* sScal,
     b.red->cnt[kMaxGroups] = 0u;
     b.red->t_end = gtimer();
   });
+  return true;
 }
 
 // sum over the pixels of a staged tile of the 4x4 Gram block (bi, bj) owned by
@@ -217,9 +220,9 @@ __device__ __forceinline__ void gram_tile(const float* sZ, float (&acc)[16], int
 // scalar sums, then the two-level last-arriving-CTA reduction (fixed order)
 // that leaves the final Gram in red->G and the sums in red->e2, red->l1.
 template <int TB, bool kGram>
-__device__ __forceinline__ void pass_epilogue(Bufs b, const float (&acc)[16], float e2, float l1, float* sZ,
+__device__ __forceinline__ bool pass_epilogue(Bufs b, const float (&acc)[16], float e2, float l1, float* sZ,
                                               double (*sRed)[kPassThreads / 32], double* sScal, int* sLastp,
-                                              bool gthr, int ggrp, int gblk) {
+                                              bool gthr, int ggrp, int gblk, int lc, int nc) {
   using GM = GramMap<TB>;
   const int tid = threadIdx.x;
   const int T = b.T;
@@ -239,8 +242,8 @@ __device__ __forceinline__ void pass_epilogue(Bufs b, const float (&acc)[16], fl
       blk_coords(e / 16, GM::NB, ebi, ebj);
       const int a = 4 * ebi + (e % 16) / 4, c = 4 * ebj + (e % 4);
       if (a < T && c < T) {
-        b.gram_part[(int64_t)blockIdx.x * TT + a * T + c] = sum;
-        b.gram_part[(int64_t)blockIdx.x * TT + c * T + a] = sum;
+        b.gram_part[(int64_t)lc * TT + a * T + c] = sum;
+        b.gram_part[(int64_t)lc * TT + c * T + a] = sum;
       }
     }
   }
@@ -257,12 +260,12 @@ __device__ __forceinline__ void pass_epilogue(Bufs b, const float (&acc)[16], fl
         s0 += sRed[0][w];
         s1 += sRed[1][w];
       }
-      b.scal_part[2 * blockIdx.x] = s0;
-      b.scal_part[2 * blockIdx.x + 1] = s1;
+      b.scal_part[2 * lc] = s0;
+      b.scal_part[2 * lc + 1] = s1;
     }
   }
 
-  cross_cta_reduce(b, kGram, sScal, sLastp);
+  return cross_cta_reduce(b, kGram, sScal, sLastp, lc, nc);
 }
 
 // ---------------------------------------------------------------------------
@@ -275,29 +278,39 @@ __device__ __forceinline__ void pass_epilogue(Bufs b, const float (&acc)[16], fl
 // stride over tiles; partial Grams and scalars are reduced across CTAs by the
 // last CTA to arrive (two levels, fixed summation order => deterministic).
 // ---------------------------------------------------------------------------
+// dynamic shared memory of pass_body: Wbar^T, V^T and the staged tile
+template <int TB>
+__host__ __device__ constexpr size_t pass_simt_smem() {
+  return sizeof(float) * (2 * (size_t)TB * TB + (size_t)kTile * (TB + 4));
+}
+
+// One pass over the pixels of this CTA (number lc of nc); `dsm` holds
+// pass_simt_smem<TB>() bytes.  Returns true in the CTA that wrote the final
+// reduced sums (when b.finalize).  Control values and eigen data are read
+// around L1 because a persistent caller reuses the CTA across iterations.
 template <int TB, int MODE>
-__global__ void __launch_bounds__(kPassThreads) pass_kernel(Bufs b) {
+__device__ bool pass_body(Bufs b, int lc, int nc, unsigned char* dsm) {
   constexpr bool kGram = (MODE != PM_UPDATE);
   constexpr int ZS = TB + 4;  // staged row stride in floats (16-byte aligned rows)
   using GM = GramMap<TB>;
-  __shared__ __align__(16) float sWT[TB * TB];  // Wbar transposed: sWT[j*TB + t] = Wbar[t][j]
-  __shared__ __align__(16) float sVT[TB * TB];  // V transposed
-  __shared__ __align__(16) float sZ[kTile * ZS];
+  float* sWT = reinterpret_cast<float*>(dsm);   // Wbar transposed: sWT[j*TB + t] = Wbar[t][j]
+  float* sVT = sWT + TB * TB;                   // V transposed
+  float* sZ = sVT + TB * TB;                    // [kTile][ZS]
   __shared__ double sRed[2][kPassThreads / 32];
   __shared__ double sScal[2 * kMaxGroups];
   __shared__ int sLast;
 
   const Ctrl* ctrl = b.ctrl;
-  if (ctrl->done) return;
+  if (__ldcg(&ctrl->done)) return false;
   const int tid = threadIdx.x;
   if (tid == 0) atomicMin(&b.red->t_start, gtimer());
   const int T = b.T;
   const int64_t m = b.m;
   const Job job = *b.job;
-  const int kc = ctrl->k;
+  const int kc = __ldcg(&ctrl->k);
   const bool first = (kc == 0);
-  const float f_mu = ctrl->f_mu, inv_mu = ctrl->f_inv_mu, gamma = ctrl->f_gamma;
-  const float inv_mu_nxt = ctrl->f_inv_mu_nxt;
+  const float f_mu = __ldcg(&ctrl->f_mu), inv_mu = __ldcg(&ctrl->f_inv_mu), gamma = __ldcg(&ctrl->f_gamma);
+  const float inv_mu_nxt = __ldcg(&ctrl->f_inv_mu_nxt);
   const float* Yin = (kc & 1) ? job.Y1 : job.Y0;
   float* Yout = (kc & 1) ? job.Y0 : job.Y1;
 
@@ -305,8 +318,8 @@ __global__ void __launch_bounds__(kPassThreads) pass_kernel(Bufs b) {
     for (int i = tid; i < TB * TB; i += kPassThreads) {
       const int r = i / TB, c = i % TB;
       const bool in = (r < T && c < T);
-      sWT[c * TB + r] = in ? b.eig->Wbar[r * kMaxT + c] : 0.f;
-      sVT[c * TB + r] = in ? b.eig->V32[r * kMaxT + c] : 0.f;
+      sWT[c * TB + r] = in ? __ldcg(&b.eig->Wbar[r * kMaxT + c]) : 0.f;
+      sVT[c * TB + r] = in ? __ldcg(&b.eig->V32[r * kMaxT + c]) : 0.f;
     }
   }
   __syncthreads();
@@ -321,7 +334,7 @@ __global__ void __launch_bounds__(kPassThreads) pass_kernel(Bufs b) {
   float e2 = 0.f, l1 = 0.f;
 
   const int64_t ntiles = (m + kTile - 1) / kTile;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (int64_t tile = lc; tile < ntiles; tile += nc) {
     const int64_t p = tile * kTile + tid;
     const bool valid = p < m;
     float zt[TB];
@@ -385,7 +398,13 @@ __global__ void __launch_bounds__(kPassThreads) pass_kernel(Bufs b) {
     }
   }
 
-  pass_epilogue<TB, kGram>(b, acc, e2, l1, sZ, sRed, sScal, &sLast, gthr, ggrp, gblk);
+  return pass_epilogue<TB, kGram>(b, acc, e2, l1, sZ, sRed, sScal, &sLast, gthr, ggrp, gblk, lc, nc);
+}
+
+template <int TB, int MODE>
+__global__ void __launch_bounds__(kPassThreads) pass_kernel(Bufs b) {
+  extern __shared__ __align__(16) unsigned char pass_dsm[];
+  pass_body<TB, MODE>(b, blockIdx.x, gridDim.x, pass_dsm);
 }
 
 // ---------------------------------------------------------------------------
@@ -416,7 +435,7 @@ __device__ __forceinline__ void refresh_f32(Ctrl* c) {
 // Final sums of a pass that left them as group partials (finalize == 0):
 // red->G, red->e2, red->l1 from the group partials, fixed order.  All threads
 // of the calling CTA take part.
-__device__ void finalize_sums(Bufs b, double* sh) {
+static __device__ void finalize_sums(Bufs b, double* sh) {
   if (b.finalize) return;
   const int T = b.T, TT = T * T;
   const int ng = b.red->ngroups_last;
@@ -437,7 +456,7 @@ __device__ void finalize_sums(Bufs b, double* sh) {
 // EF_INIT (||X|| from the init pass; X == 0 finishes with L = S = 0), and sets
 // the graph's loop condition when the solve ends here.  Returns true when the
 // caller goes on to the eigensolve.
-__device__ bool eig_control(Bufs b, int flags, cudaGraphConditionalHandle h, int use_cond, int* sFlag) {
+static __device__ bool eig_control(Bufs b, int flags, cudaGraphConditionalHandle h, int use_cond, int* sFlag) {
   Ctrl* ctrl = b.ctrl;
   const int tid = threadIdx.x;
   __shared__ double sFin[2 * kMaxGroups];
@@ -726,16 +745,16 @@ __global__ void __launch_bounds__(512) eig_kernel(Bufs b, int flags, cudaGraphCo
 // Final outputs: L = X - S - E with E = (Y_k - Y_{k-1})/mu_k (Eq. 6 rearranged),
 // and the bound-bubble mask: temporal mean of |L| >= theta (Sec. II-F).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) final_kernel(Bufs b) {
+static __device__ void final_body(Bufs b, int lc, int nc) {
   const Ctrl* ctrl = b.ctrl;
   const Job job = *b.job;
   const int T = b.T;
   const int64_t m = b.m;
-  const int kc = ctrl->k;
-  const float inv_mu = ctrl->f_inv_mu;
+  const int kc = __ldcg(&ctrl->k);
+  const float inv_mu = __ldcg(&ctrl->f_inv_mu);
   const float* Yk = (kc & 1) ? job.Y1 : job.Y0;
   const float* Ykm1 = (kc & 1) ? job.Y0 : job.Y1;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t p = (int64_t)lc * blockDim.x + threadIdx.x; p < m; p += (int64_t)nc * blockDim.x) {
     float acc = 0.f;
     for (int t = 0; t < T; ++t) {
       const int64_t i = t * m + p;
@@ -755,8 +774,10 @@ __global__ void __launch_bounds__(256) final_kernel(Bufs b) {
   }
 }
 
+static __global__ void __launch_bounds__(256) final_kernel(Bufs b) { final_body(b, blockIdx.x, gridDim.x); }
+
 // Per-solve reset and pointer hand-off (runs before each graph launch).
-__global__ void begin_kernel(Bufs b, const float* X, float* L, float* S, uint8_t* mask, float theta,
+static __global__ void begin_kernel(Bufs b, const float* X, float* L, float* S, uint8_t* mask, float theta,
                              const __grid_constant__ TmaMaps maps, int use_maps) {
   if (use_maps) {
     // 4 x 128-byte descriptors, copied by 64 threads as 16-byte chunks

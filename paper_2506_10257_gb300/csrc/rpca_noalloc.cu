@@ -99,6 +99,15 @@ void* na_pass_fn(int T) {
   return (void*)pass_kernel<32, PM_GRAM>;
 }
 
+size_t na_pass_smem(int T) {
+  if (T <= 8) return pass_simt_smem<8>();
+  if (T <= 12) return pass_simt_smem<12>();
+  if (T <= 16) return pass_simt_smem<16>();
+  if (T <= 20) return pass_simt_smem<20>();
+  if (T <= 24) return pass_simt_smem<24>();
+  return pass_simt_smem<32>();
+}
+
 rpca_status na_status(cudaError_t e) {
   if (e == cudaSuccess) return RPCA_OK;
   return RPCA_ERR_CUDA;
@@ -146,7 +155,8 @@ extern "C" rpca_status rpca_gram_noalloc(const float* X, int64_t m, int32_t T, c
   void* a_setup[] = {&b, (void*)&X, (void*)&V, &T};
   if (e == cudaSuccess) e = cudaLaunchKernel((void*)na_setup_kernel, dim3(1), dim3(256), a_setup, 0, s);
   void* a_pass[] = {&b};
-  if (e == cudaSuccess) e = cudaLaunchKernel(na_pass_fn(T), dim3((unsigned)grid), dim3(kPassThreads), a_pass, 0, s);
+  if (e == cudaSuccess)
+    e = cudaLaunchKernel(na_pass_fn(T), dim3((unsigned)grid), dim3(kPassThreads), a_pass, na_pass_smem(T), s);
   void* a_store[] = {&b, &G, &T};
   if (e == cudaSuccess) e = cudaLaunchKernel((void*)na_store_kernel, dim3(1), dim3(256), a_store, 0, s);
   return na_status(e);

@@ -220,5 +220,5 @@ __global__ void __launch_bounds__(kPassThreads, 1) pass_tc_kernel(Bufs b) {
   tc_fence_before();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, SH::TMEM_COLS);
-  pass_epilogue<TB, true>(b, acc, e2, 0.f, sZ, sRed, sScal, &sLast, gthr, ggrp, gblk);
+  pass_epilogue<TB, true>(b, acc, e2, 0.f, sZ, sRed, sScal, &sLast, gthr, ggrp, gblk, blockIdx.x, gridDim.x);
 }

@@ -288,5 +288,5 @@ __global__ void __launch_bounds__(kWsThreads, 1) pass_ws_kernel(Bufs b) {
       b.scal_part[2 * blockIdx.x + 1] = 0.0;
     }
   }
-  cross_cta_reduce(b, true, sScal, &sLast);
+  cross_cta_reduce(b, true, sScal, &sLast, blockIdx.x, gridDim.x);
 }

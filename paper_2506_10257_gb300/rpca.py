@@ -27,7 +27,8 @@ MAX_T = 32
 
 EXPORTED = ["rpca_params_default", "rpca_workspace_size", "rpca_plan_create", "rpca_solve", "rpca_solve_host",
             "rpca_plan_result", "rpca_plan_destroy", "rpca_status_str", "rpca_gram", "rpca_eig",
-            "rpca_gram_noalloc", "rpca_plan_timings"]
+            "rpca_gram_noalloc", "rpca_plan_timings", "rpca_batch_create", "rpca_batch_solve",
+            "rpca_batch_tune", "rpca_batch_info", "rpca_batch_window_ctas", "rpca_batch_destroy"]
 
 
 class Params(ctypes.Structure):
@@ -48,6 +49,11 @@ class Result(ctypes.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Window(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("L", ctypes.c_void_p), ("S", ctypes.c_void_p),
+                ("mask", ctypes.c_void_p), ("theta", ctypes.c_float), ("pad_", ctypes.c_int32)]
 
 
 class RpcaError(RuntimeError):
@@ -89,6 +95,13 @@ def load(build_if_missing: bool = True):
     lib.rpca_eig.argtypes = [vp, i32, vp, vp, vp]
     lib.rpca_gram_noalloc.argtypes = [vp, i64, i32, vp, vp, vp]
     lib.rpca_plan_timings.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i32]
+    lib.rpca_batch_create.argtypes = [ctypes.POINTER(Params), i32, ctypes.POINTER(vp)]
+    lib.rpca_batch_solve.argtypes = [vp, ctypes.POINTER(Window), vp, ctypes.POINTER(Result)]
+    lib.rpca_batch_tune.argtypes = [vp, ctypes.POINTER(Window), vp, i32, ctypes.POINTER(ctypes.c_double)]
+    lib.rpca_batch_info.argtypes = [vp, ctypes.POINTER(i32), i32]
+    lib.rpca_batch_window_ctas.argtypes = [vp, ctypes.POINTER(i32), i32]
+    lib.rpca_batch_destroy.argtypes = [vp]
+    lib.rpca_batch_destroy.restype = None
     _lib = lib
     return lib
 
@@ -278,3 +291,96 @@ def gram_noalloc(frames, V=None, G=None, stream=None):
     if st != OK:
         raise RpcaError(st, "rpca_gram_noalloc")
     return G
+
+
+class Batch:
+    """Many windows of uneven (T, m) shapes solved by one persistent launch.
+
+    shapes: list of (m, T); kw: parameters applied to every window, or
+    params: a list of per-window keyword dicts."""
+
+    def __init__(self, shapes, params=None, **kw):
+        _torch()
+        self.lib = load()
+        self.shapes = [(int(m), int(T)) for m, T in shapes]
+        n = len(self.shapes)
+        if n < 1:
+            raise ValueError("a batch needs at least one window")
+        arr = (Params * n)()
+        for i, (m, T) in enumerate(self.shapes):
+            extra = dict(kw)
+            if params is not None:
+                extra.update(params[i])
+            arr[i] = default_params(m, T, **extra)
+        h = ctypes.c_void_p()
+        st = self.lib.rpca_batch_create(arr, n, ctypes.byref(h))
+        if st != OK:
+            raise RpcaError(st, "rpca_batch_create")
+        self.handle = h
+        self.n = n
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.rpca_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _windows(self, frames, Ls, Ss, masks, thetas):
+        torch = _torch()
+        if len(frames) != self.n:
+            raise ValueError(f"expected {self.n} windows, got {len(frames)}")
+        w = (Window * self.n)()
+        for i, F in enumerate(frames):
+            m, T = self.shapes[i]
+            if F.dtype != torch.float32 or not F.is_cuda or not F.is_contiguous() or tuple(F.shape) != (T, m):
+                raise ValueError(f"window {i}: need a contiguous float32 CUDA tensor of shape {(T, m)}")
+            w[i].X = F.data_ptr()
+            w[i].L = Ls[i].data_ptr()
+            w[i].S = Ss[i].data_ptr()
+            w[i].mask = masks[i].data_ptr() if masks is not None and masks[i] is not None else 0
+            w[i].theta = float(thetas[i]) if thetas is not None else 0.0
+        return w
+
+    def solve(self, frames, Ls=None, Ss=None, masks=None, thetas=None, stream=None, wait: bool = True):
+        """Solve every window; returns (Ls, Ss, results) (results None when wait=False)."""
+        torch = _torch()
+        if Ls is None:
+            Ls = [torch.empty_like(F) for F in frames]
+        if Ss is None:
+            Ss = [torch.empty_like(F) for F in frames]
+        w = self._windows(frames, Ls, Ss, masks, thetas)
+        res = (Result * self.n)()
+        st = self.lib.rpca_batch_solve(self.handle, w, _stream_handle(stream), res if wait else None)
+        if st < 0:
+            raise RpcaError(st, "rpca_batch_solve")
+        self._keep = (frames, Ls, Ss, masks)
+        return Ls, Ss, ([r.as_dict() for r in res] if wait else None)
+
+    def tune(self, frames, reps: int = 3, stream=None) -> float:
+        """Autotune the CTA schedule on these windows; returns the best median ms per batch solve."""
+        torch = _torch()
+        Ls = [torch.empty_like(F) for F in frames]
+        Ss = [torch.empty_like(F) for F in frames]
+        w = self._windows(frames, Ls, Ss, None, None)
+        best = ctypes.c_double()
+        st = self.lib.rpca_batch_tune(self.handle, w, _stream_handle(stream), int(reps), ctypes.byref(best))
+        if st != OK:
+            raise RpcaError(st, "rpca_batch_tune")
+        return best.value
+
+    def info(self) -> dict:
+        buf = (ctypes.c_int32 * 6)()
+        st = self.lib.rpca_batch_info(self.handle, buf, 6)
+        if st != OK:
+            raise RpcaError(st, "rpca_batch_info")
+        keys = ["grid", "lanes", "ctas_per_sm", "alpha_milli", "occ_max", "graph"]
+        out = dict(zip(keys, list(buf)))
+        ctas = (ctypes.c_int32 * self.n)()
+        if self.lib.rpca_batch_window_ctas(self.handle, ctas, self.n) == OK:
+            out["window_ctas"] = list(ctas)
+        return out
