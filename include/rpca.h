@@ -84,8 +84,20 @@ typedef struct {
   double lambda;            /* <= 0 selects 1/sqrt(max(m, T)) */
   double mu0_scale;         /* IALM: mu_1 = mu0_scale / ||X||_2 (default 1.25) */
   double rho;               /* IALM growth factor (default 1.5), >= 1 */
-  double mu_max_factor;     /* IALM cap mu_max = factor * mu_1 (default 1e7) */
+  double mu_max_factor;     /* IALM cap mu_max = factor * mu0, mu0 the cold schedule's first
+                               mu (default 1e7) */
   double tol;               /* relative Frobenius stopping tolerance (default 1e-7), > 0 */
+  /* Warm start (the paper always starts from L = S = Y = 0; a sliding-window
+   * stream can resume from the previous window's state instead).  With
+   * warm_start = 1, on entry to rpca_solve the S buffer holds S0 and the L
+   * buffer holds Y0 (m x T each); the first SVT then acts on
+   * Z1 = X - S0 + Y0/mu1 (one extra Gram pass) and every later step is the
+   * same iteration.  0 (default) ignores the buffers' contents. */
+  int32_t warm_start;
+  int32_t pad_;
+  double mu_init;           /* > 0: first mu of the solve (default 0: the schedule's mu0) */
+  double mu_prev_scale;     /* > 0 with warm_start and mu_init == 0: first mu = this times the
+                               final mu of this plan's previous solve (default 0) */
 } rpca_params;
 
 #define RPCA_MAX_T 32
@@ -212,6 +224,64 @@ rpca_status rpca_batch_info(rpca_batch_t batch, int32_t* info, int32_t n);
 rpca_status rpca_batch_window_ctas(rpca_batch_t batch, int32_t* ctas, int32_t n);
 
 void rpca_batch_destroy(rpca_batch_t batch);
+
+/* ---- served form ----------------------------------------------------------- */
+
+/* A request loop over sliding frame windows from several probes (the paper's
+ * real-time goal, Sec. I and IV; the serving machinery itself has no
+ * counterpart in the paper).  Each request is one window solved exactly as by
+ * rpca_solve on a plan of its parameters, except that a probe's windows after
+ * its first may warm-start (see rpca_server_set_warm).
+ *
+ * Continuous batching: requests queue in arrival order and start as soon as a
+ * slot (one of max_slots CUDA streams) is free and their probe's device state
+ * fits the budget, while earlier solves are still running; solves of
+ * different probes overlap on the device.  A probe's windows run in arrival
+ * order.  Progress happens inside rpca_submit, rpca_poll, rpca_server_wait and
+ * rpca_server_stats (no background thread).
+ *
+ * Memory: per probe the server holds a plan workspace (rpca_workspace_size)
+ * and the probe's S and Y state (2 m T floats); that total is charged against
+ * hbm_budget_bytes.  Idle probes (nothing queued or running) are evicted,
+ * least recently used first, when a new probe needs room; their next window
+ * starts cold.  The caller's X, L, S buffers are not charged. */
+typedef struct rpca_server_s* rpca_server_t;
+
+/* max_slots in [1, 256].  Defaults: warm start on, warm_mu_scale 0.1,
+ * cold_every 0. */
+rpca_status rpca_server_create(size_t hbm_budget_bytes, int32_t max_slots, rpca_server_t* out);
+
+/* Warm-start policy.  warm = 1: a probe's window k+1 (assumed to be window k
+ * shifted by one frame) starts from S0, Y0 = window k's final S, Y with the
+ * oldest frame dropped and a zero frame appended, and first mu =
+ * warm_mu_scale * window k's final mu (warm_mu_scale = 0: the schedule's mu0).
+ * cold_every = n > 0 makes every n-th window of a probe start cold (bounds the
+ * drift of a long warm chain); 0 never.  warm = 0: every window starts cold. */
+rpca_status rpca_server_set_warm(rpca_server_t server, int32_t warm, double warm_mu_scale, int32_t cold_every);
+
+/* Queue one window (device buffers as in rpca_solve; they must stay alive and
+ * untouched until the request is reported done) for probe `stream_key`.
+ * *req_id identifies it.  RPCA_ERR_BUDGET when the probe's state alone
+ * exceeds the budget; parameter errors as rpca_plan_create.  warm_start,
+ * mu_init and mu_prev_scale of *p are ignored (the server's policy rules). */
+rpca_status rpca_submit(rpca_server_t server, const rpca_params* p, const void* X, void* L, void* S,
+                        uint8_t* mask, float theta, int32_t stream_key, uint64_t* req_id);
+
+/* RPCA_PENDING while the request is queued or running; once done, fills *out
+ * (nullable), forgets the request and returns its status.  RPCA_ERR_NOTFOUND
+ * for an unknown (or already reported) id. */
+rpca_status rpca_poll(rpca_server_t server, uint64_t req_id, rpca_result* out);
+
+/* Blocks until the request is done, then as rpca_poll.  RPCA_ERR_BUDGET if it
+ * is queued with nothing running that could free memory for it. */
+rpca_status rpca_server_wait(rpca_server_t server, uint64_t req_id, rpca_result* out);
+
+/* stats[0..n) = {bytes held, peak bytes held, budget, queued, running, peak
+ * running, started, finished, probes evicted, requests refused}. */
+rpca_status rpca_server_stats(rpca_server_t server, int64_t* stats, int32_t n);
+
+/* Waits for running solves, frees every probe's state. */
+void rpca_server_destroy(rpca_server_t server);
 
 /* ---- kernel-level entry points (each one step of the iteration) ---------- */
 

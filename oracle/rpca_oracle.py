@@ -127,7 +127,9 @@ def rpca(
       else, under ``ialm``, mu = min(rho*mu, mu_max).
 
     ``S0``, ``Y0`` and ``mu_init`` give a warm start (all three default to the
-    cold start S = Y = 0 and the schedule's first mu).
+    cold start S = Y = 0 and the schedule's first mu).  The paper has no warm
+    start; the reading taken: the cap mu_max = mu_max_factor * mu0 stays the
+    cold schedule's (mu0 from this X) whatever mu_init is.
     """
     X = np.asarray(X)
     X = X.astype(np.complex128 if np.iscomplexobj(X) else np.float64)
@@ -140,8 +142,9 @@ def rpca(
     L = np.zeros_like(X)
     if normX == 0.0:
         return Result(L, S, Y, 0, 0.0, True, 0, 0.0, lam, [])
-    mu = initial_mu(X, schedule, mu0_scale) if mu_init is None else float(mu_init)
-    mu_max = mu_max_factor * mu
+    mu0 = initial_mu(X, schedule, mu0_scale)
+    mu = mu0 if mu_init is None else float(mu_init)
+    mu_max = mu_max_factor * mu0
     history = []
     resid = np.inf
     rank = 0
@@ -162,8 +165,12 @@ def rpca(
 def rpca_frames(frames: np.ndarray, **kw) -> Result:
     """Same as ``rpca`` on the Casorati matrix X = frames.T of a (T, m) window.
 
-    The returned L, S, Y are transposed back to (T, m) frame rows.
+    The returned L, S, Y are transposed back to (T, m) frame rows; a warm
+    start's S0 and Y0 are given as (T, m) frame rows too.
     """
+    for k in ("S0", "Y0"):
+        if kw.get(k) is not None:
+            kw[k] = np.asarray(kw[k]).T
     r = rpca(np.asarray(frames).T, **kw)
     r.L, r.S, r.Y = r.L.T, r.S.T, r.Y.T
     return r

@@ -140,6 +140,8 @@ __device__ void run_window(WinDesc& wd, int lc, unsigned char* dsm, unsigned lon
       j->L = wd.L;
       j->mask = wd.mask;
       j->theta = wd.theta;
+      j->Sout = nullptr;
+      j->Yout = nullptr;
       Ctrl* c = b.ctrl;
       c->k = 0;
       c->done = 0;

@@ -158,6 +158,9 @@ rpca_status validate(const rpca_params* p) {
   if (p->precision < RPCA_PREC_FP32 || p->precision > RPCA_PREC_TF32) return RPCA_ERR_ARG;
   if (p->precision != RPCA_PREC_FP32 && p->drive == RPCA_DRIVE_HOST) return RPCA_ERR_UNSUPPORTED;
   if (p->m * (int64_t)p->T > (int64_t)1 << 40) return RPCA_ERR_ARG;
+  if (p->warm_start != 0 && p->warm_start != 1) return RPCA_ERR_ARG;
+  if (!(p->mu_init >= 0.0) || !(p->mu_prev_scale >= 0.0) || !isfinite(p->mu_init) || !isfinite(p->mu_prev_scale))
+    return RPCA_ERR_ARG;
   return RPCA_OK;
 }
 
@@ -277,6 +280,15 @@ static rpca_status build_graph(rpca_plan_s* pl) {
   cudaGraphNode_t n_init, n_eig0, n_while, n_fin, n_pass, n_eig;
   CK(add_kernel(pl->graph, &n_init, nullptr, 0, pl->ks.pass[PM_INIT], pg, pb, a_pass, pl->ks.pass_smem));
   CK(add_kernel(pl->graph, &n_eig0, &n_init, 1, eig_fn(pl), eg, eb, a_eig0, es));
+  if (pl->p.warm_start) {
+    // warm start: the first SVT needs the Gram of Z1 = X - S0 + Y0/mu1, not of X
+    int f_eig = EF_EIG | EF_FULL;
+    void* a_eigw[] = {&b, &f_eig, &h, &use_cond, &nulld, &nullo, &nullo};
+    cudaGraphNode_t n_gw, n_ew;
+    CK(add_kernel(pl->graph, &n_gw, &n_eig0, 1, pl->ks.pass[PM_GRAM], pg, pb, a_pass, pl->ks.pass_smem));
+    CK(add_kernel(pl->graph, &n_ew, &n_gw, 1, eig_fn(pl), eg, eb, a_eigw, es));
+    n_eig0 = n_ew;
+  }
 
   alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
   memset(cp_raw, 0, sizeof(cp_raw));
@@ -314,6 +326,8 @@ void result_from_ctrl(double lambda, const Ctrl& c, rpca_result* out) {
   out->passes_timed = (int32_t)c.pass_cnt;
   out->eigs_timed = (int32_t)c.eig_cnt;
 }
+
+Ctrl* plan_ctrl(rpca_plan_t pl) { return pl ? pl->bufs.ctrl : nullptr; }
 
 rpca_status plan_view(rpca_plan_t pl, PlanView* v) {
   if (!pl || !v) return RPCA_ERR_ARG;
@@ -441,8 +455,12 @@ rpca_status rpca_plan_create(const rpca_params* p, void* workspace, size_t works
   c.mu_max_factor = p->mu_max_factor;
   c.tol = p->tol;
   c.jacobi_eps = pl->eig_fp64 ? 1e-12 : 1e-6;
+  if (getenv("RPCA_JACOBI_EPS")) c.jacobi_eps = atof(getenv("RPCA_JACOBI_EPS"));  // tuning override
   c.warm_sweeps = 4;
   c.cold_sweeps = 30;
+  c.warm = p->warm_start;
+  c.mu_init = p->mu_init;
+  c.mu_prev_scale = p->mu_prev_scale;
   cudaError_t e = cudaMemset(pl->ws, 0, pl->lay.gram_part);  // ctrl, eig, red (counters), job
   if (e == cudaSuccess) e = cudaMemcpy(b.ctrl, &c, sizeof(c), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&pl->ctrl_host, sizeof(Ctrl));
@@ -489,6 +507,12 @@ static rpca_status run_host_loop(rpca_plan_s* pl, cudaStream_t s) {
   void* a_eig[] = {&b, &f_eig, &h, &use_cond, &nulld, &nullo, &nullo};
   CK(launch(pl->ks.pass[PM_INIT], pg, pb, a_pass, s, pl->ks.pass_smem));
   CK(launch(eig_fn(pl), eg, eb, a_init, s, es));
+  if (pl->p.warm_start) {
+    int f_full = EF_EIG | EF_FULL;
+    void* a_full[] = {&b, &f_full, &h, &use_cond, &nulld, &nullo, &nullo};
+    CK(launch(pl->ks.pass[PM_GRAM], pg, pb, a_pass, s, pl->ks.pass_smem));
+    CK(launch(eig_fn(pl), eg, eb, a_full, s, es));
+  }
   for (int it = 0; it <= pl->p.max_iter; ++it) {
     CK(cudaMemcpyAsync(pl->ctrl_host, b.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -523,6 +547,12 @@ static rpca_status run_stream_loop(rpca_plan_s* pl, cudaStream_t s) {
   void* a_iter[] = {&b, &f_iter, &h, &use_cond, &nulld, &nullo, &nullo};
   CK(launch(pl->ks.pass[PM_INIT], pg, pb, a_pass, s, pl->ks.pass_smem));
   CK(launch(eig_fn(pl), eg, eb, a_init, s, es));
+  if (pl->p.warm_start) {
+    int f_eig = EF_EIG | EF_FULL;
+    void* a_eig[] = {&b, &f_eig, &h, &use_cond, &nulld, &nullo, &nullo};
+    CK(launch(pl->ks.pass[PM_GRAM], pg, pb, a_pass, s, pl->ks.pass_smem));
+    CK(launch(eig_fn(pl), eg, eb, a_eig, s, es));
+  }
   for (int it = 0; it < pl->p.max_iter; ++it) {
     if (it % 8 == 0) {
       CK(cudaMemcpyAsync(pl->ctrl_host, b.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
@@ -539,6 +569,13 @@ static rpca_status run_stream_loop(rpca_plan_s* pl, cudaStream_t s) {
 
 rpca_status rpca_solve(rpca_plan_t pl, const void* X, void* L, void* S, uint8_t* mask, float theta, void* stream,
                        rpca_result* out) {
+  return rpca::plan_solve_ex(pl, X, L, S, mask, theta, stream, nullptr, nullptr, -1.0, out);
+}
+
+}  // extern "C"
+
+rpca_status rpca::plan_solve_ex(rpca_plan_t pl, const void* X, void* L, void* S, uint8_t* mask, float theta,
+                                void* stream, float* Sout, float* Yout, double mu_prev_scale, rpca_result* out) {
   if (!pl || !X || !L || !S) return RPCA_ERR_ARG;
   if (((uintptr_t)X | (uintptr_t)L | (uintptr_t)S) & 15u) return RPCA_ERR_ARG;
   if (X == L || X == S || L == S) return RPCA_ERR_ARG;
@@ -554,7 +591,7 @@ rpca_status rpca_solve(rpca_plan_t pl, const void* X, void* L, void* S, uint8_t*
       return RPCA_ERR_CUDA;
     use_maps = 1;
   }
-  void* a_begin[] = {&b, (void*)&X, &L, &S, &mask, &theta, &maps, &use_maps};
+  void* a_begin[] = {&b, (void*)&X, &L, &S, &mask, &theta, &Sout, &Yout, &mu_prev_scale, &maps, &use_maps};
   CK(cudaLaunchKernel((void*)begin_kernel, dim3(1), dim3(64), a_begin, 0, s));
   if (pl->p.drive == RPCA_DRIVE_GRAPH) {
     CK(cudaGraphLaunch(pl->exec, s));
@@ -568,6 +605,8 @@ rpca_status rpca_solve(rpca_plan_t pl, const void* X, void* L, void* S, uint8_t*
   fill_result(pl, *pl->ctrl_host, out);
   return (rpca_status)out->status;
 }
+
+extern "C" {
 
 rpca_status rpca_plan_result(rpca_plan_t pl, rpca_result* out) {
   if (!pl || !out) return RPCA_ERR_ARG;

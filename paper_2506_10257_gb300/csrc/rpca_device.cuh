@@ -33,7 +33,8 @@ constexpr int kMaxGroups = 64;
 // Pass kinds.
 enum PassMode { PM_INIT = 0, PM_FUSED = 1, PM_UPDATE = 2, PM_GRAM = 3 };
 // Eig-kernel phases.
-enum EigFlags { EF_INIT = 1, EF_CHECK = 2, EF_EIG = 4 };
+// EF_FULL: allow the cold sweep cap while keeping the basis (first SVT of a warm start).
+enum EigFlags { EF_INIT = 1, EF_CHECK = 2, EF_EIG = 4, EF_FULL = 16 };
 
 // Iteration control block (device resident, one per plan).
 struct Ctrl {
@@ -60,6 +61,10 @@ struct Ctrl {
   double jacobi_eps; // graded off-diagonal threshold of the Jacobi sweeps
   int warm_sweeps;   // sweep cap once warm started
   int cold_sweeps;   // sweep cap of the first eigensolve
+  int warm;          // 1: the solve starts from S0 (in S) and Y0 (in the L buffer)
+  int pad_w;
+  double mu_init;       // > 0: first mu of the solve instead of the schedule's
+  double mu_prev_scale; // > 0 with warm: first mu = this times the plan's previous final mu
   // FP32 copies used by the passes (rounded once from the FP64 values).
   float f_mu, f_inv_mu, f_gamma, f_inv_mu_nxt;
   // Device-side timing of the solve (globaltimer, ns): fused/update passes
@@ -110,6 +115,8 @@ struct Job {
   float* L;
   uint8_t* mask;
   float theta;
+  float* Sout;      // when set, the final step also copies S here
+  float* Yout;      // ... and the final dual Y_k here (the state a warm start resumes)
 };
 
 // Per-solve tensor maps handed to the begin kernel as a kernel parameter.

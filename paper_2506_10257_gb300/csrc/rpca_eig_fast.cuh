@@ -73,7 +73,7 @@ __device__ void eig_fast_body(Bufs b, int flags, cudaGraphConditionalHandle h, i
 
   const float eps = (float)ctrl->jacobi_eps;
   const float eps2 = eps * eps;
-  int max_sweeps = cold ? ctrl->cold_sweeps : ctrl->warm_sweeps;
+  int max_sweeps = (cold || (flags & EF_FULL)) ? ctrl->cold_sweeps : ctrl->warm_sweeps;
   if (max_sweeps > kEigLogSweeps) max_sweeps = kEigLogSweeps;
   // upper-triangle entries owned by this thread
   int ea[EPT], ec[EPT];
@@ -239,16 +239,7 @@ __device__ void eig_fast_body(Bufs b, int flags, cudaGraphConditionalHandle h, i
     if (flags & EF_INIT) {
       double lmax = 0.0;
       for (int a = 0; a < T; ++a) lmax = fmax(lmax, S.ev[a]);
-      double mu1;
-      if (ctrl->schedule == 0)
-        mu1 = ctrl->mu0_scale / sqrt(lmax);
-      else
-        mu1 = ((double)b.m * (double)T) / (4.0 * ctrl->normX1);
-      ctrl->mu_cur = mu1;
-      ctrl->mu_max = ctrl->mu_max_factor * mu1;
-      ctrl->mu_nxt = (ctrl->schedule == 0) ? fmin(ctrl->rho * mu1, ctrl->mu_max) : mu1;
-      ctrl->k = 0;
-      refresh_f32(ctrl);
+      init_mu(b, lmax);
     }
     sTau = 1.0 / ctrl->mu_cur;
   }

@@ -18,6 +18,16 @@ struct PlanView {
 // Fills *v from a plan; RPCA_ERR_ARG for a null plan.
 rpca_status plan_view(rpca_plan_t plan, PlanView* v);
 
+// rpca_solve with two extra outputs written by the final step (either may be
+// NULL): Sout gets S, Yout the final dual Y_k (the state a warm start resumes);
+// mu_prev_scale >= 0 replaces the plan's mu_prev_scale for this solve and
+// later ones (< 0 keeps it).
+rpca_status plan_solve_ex(rpca_plan_t plan, const void* X, void* L, void* S, uint8_t* mask, float theta,
+                          void* stream, float* Sout, float* Yout, double mu_prev_scale, rpca_result* out);
+
+// Device control block of the plan.
+Ctrl* plan_ctrl(rpca_plan_t plan);
+
 // rpca_result of a solve from its control block.
 void result_from_ctrl(double lambda, const Ctrl& c, rpca_result* out);
 

@@ -308,7 +308,7 @@ __device__ bool pass_body(Bufs b, int lc, int nc, unsigned char* dsm) {
   const int64_t m = b.m;
   const Job job = *b.job;
   const int kc = __ldcg(&ctrl->k);
-  const bool first = (kc == 0);
+  const bool first = (kc == 0) && !__ldcg(&ctrl->warm);  // a warm start reads S0, Y0
   const float f_mu = __ldcg(&ctrl->f_mu), inv_mu = __ldcg(&ctrl->f_inv_mu), gamma = __ldcg(&ctrl->f_gamma);
   const float inv_mu_nxt = __ldcg(&ctrl->f_inv_mu_nxt);
   const float* Yin = (kc & 1) ? job.Y1 : job.Y0;
@@ -430,6 +430,27 @@ __device__ __forceinline__ void refresh_f32(Ctrl* c) {
   c->f_inv_mu = (float)inv;
   c->f_gamma = (float)(c->lambda * inv);
   c->f_inv_mu_nxt = (float)(c->mu_nxt == c->mu_cur ? inv : 1.0 / c->mu_nxt);
+}
+
+// First mu of a solve (FP64, thread 0 of an eigen-step with EF_INIT): the
+// schedule's mu0 (Sec. II-A: 1.25/||X||_2 from the top Gram eigenvalue lmax,
+// or m T / (4 ||X||_1)), unless the plan sets mu_init, or asks a warm start to
+// resume from mu_prev_scale times its previous solve's final mu.  The cap
+// mu_max = mu_max_factor * mu0 always follows the cold schedule.
+__device__ __forceinline__ void init_mu(Bufs b, double lmax) {
+  Ctrl* c = b.ctrl;
+  const double mu0 = (c->schedule == 0) ? c->mu0_scale / sqrt(lmax)
+                                        : ((double)b.m * (double)b.T) / (4.0 * c->normX1);
+  double mu1 = mu0;
+  if (c->mu_init > 0.0)
+    mu1 = c->mu_init;
+  else if (c->warm && c->mu_prev_scale > 0.0 && c->mu_cur > 0.0)
+    mu1 = c->mu_prev_scale * c->mu_cur;
+  c->mu_cur = mu1;
+  c->mu_max = c->mu_max_factor * mu0;
+  c->mu_nxt = (c->schedule == 0) ? fmin(c->rho * mu1, c->mu_max) : mu1;
+  c->k = 0;
+  refresh_f32(c);
 }
 
 // Final sums of a pass that left them as group partials (finalize == 0):
@@ -597,7 +618,7 @@ __global__ void __launch_bounds__(512) eig_kernel(Bufs b, int flags, cudaGraphCo
   // ---- cyclic Jacobi, parallel round-robin ordering ----
   int cur = 0;
   const Real eps = raw ? (Real)(sizeof(Real) == 8 ? 1e-15 : 1e-7) : (Real)ctrl->jacobi_eps;
-  const int max_sweeps = raw ? 40 : (cold ? ctrl->cold_sweeps : ctrl->warm_sweeps);
+  const int max_sweeps = raw ? 40 : ((cold || (flags & EF_FULL)) ? ctrl->cold_sweeps : ctrl->warm_sweeps);
   int sweeps = 0;
   while (sweeps < max_sweeps) {
     int need = 0;
@@ -701,16 +722,7 @@ __global__ void __launch_bounds__(512) eig_kernel(Bufs b, int flags, cudaGraphCo
     if (flags & EF_INIT) {
       double lmax = 0.0;
       for (int a = 0; a < T; ++a) lmax = fmax(lmax, sEv[a]);
-      double mu1;
-      if (ctrl->schedule == 0)
-        mu1 = ctrl->mu0_scale / sqrt(lmax);
-      else
-        mu1 = ((double)b.m * (double)T) / (4.0 * ctrl->normX1);
-      ctrl->mu_cur = mu1;
-      ctrl->mu_max = ctrl->mu_max_factor * mu1;
-      ctrl->mu_nxt = (ctrl->schedule == 0) ? fmin(ctrl->rho * mu1, ctrl->mu_max) : mu1;
-      ctrl->k = 0;
-      refresh_f32(ctrl);
+      init_mu(b, lmax);
     }
     sTau = 1.0 / ctrl->mu_cur;
   }
@@ -751,6 +763,7 @@ static __device__ void final_body(Bufs b, int lc, int nc) {
   const int T = b.T;
   const int64_t m = b.m;
   const int kc = __ldcg(&ctrl->k);
+  const bool warm = __ldcg(&ctrl->warm) != 0;
   const float inv_mu = __ldcg(&ctrl->f_inv_mu);
   const float* Yk = (kc & 1) ? job.Y1 : job.Y0;
   const float* Ykm1 = (kc & 1) ? job.Y0 : job.Y1;
@@ -758,15 +771,20 @@ static __device__ void final_body(Bufs b, int lc, int nc) {
     float acc = 0.f;
     for (int t = 0; t < T; ++t) {
       const int64_t i = t * m + p;
-      float l = 0.f;
+      float l = 0.f, yk = 0.f;
       if (kc == 0) {
+        // finished at the init step (X == 0 or non-finite): L = 0, S = 0
+        if (warm) yk = Yk[i];
         job.S[i] = 0.f;
       } else {
         const float x = job.X[i], s = job.S[i];
-        const float yk = Yk[i];
-        const float ym = (kc >= 2) ? Ykm1[i] : 0.f;
+        yk = Yk[i];
+        // Y_{k-1}: the previous iterate, Y0 itself after one warm iteration
+        const float ym = (kc >= 2 || warm) ? Ykm1[i] : 0.f;
         l = (x - s) - (yk * inv_mu - ym * inv_mu);
       }
+      if (job.Sout) job.Sout[i] = job.S[i];
+      if (job.Yout) job.Yout[i] = yk;
       job.L[i] = l;
       acc += fabsf(l);
     }
@@ -778,7 +796,8 @@ static __global__ void __launch_bounds__(256) final_kernel(Bufs b) { final_body(
 
 // Per-solve reset and pointer hand-off (runs before each graph launch).
 static __global__ void begin_kernel(Bufs b, const float* X, float* L, float* S, uint8_t* mask, float theta,
-                             const __grid_constant__ TmaMaps maps, int use_maps) {
+                                    float* Sout, float* Yout, double mu_prev_scale,
+                                    const __grid_constant__ TmaMaps maps, int use_maps) {
   if (use_maps) {
     // 4 x 128-byte descriptors, copied by 64 threads as 16-byte chunks
     const uint4* src = reinterpret_cast<const uint4*>(&maps);
@@ -793,7 +812,10 @@ static __global__ void begin_kernel(Bufs b, const float* X, float* L, float* S, 
     j->L = L;
     j->mask = mask;
     j->theta = theta;
+    j->Sout = Sout;
+    j->Yout = Yout;
     Ctrl* c = b.ctrl;
+    if (mu_prev_scale >= 0.0) c->mu_prev_scale = mu_prev_scale;  // per-solve warm-start override
     c->k = 0;
     c->done = 0;
     c->status = 0;

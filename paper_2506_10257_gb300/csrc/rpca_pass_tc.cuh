@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) pass_tc_kernel(Bufs b) {
   const int64_t m = b.m;
   const Job job = *b.job;
   const int kc = ctrl->k;
-  const bool first = (kc == 0);
+  const bool first = (kc == 0) && !__ldcg(&ctrl->warm);  // a warm start reads S0, Y0
   const float f_mu = ctrl->f_mu, inv_mu = ctrl->f_inv_mu, gamma = ctrl->f_gamma;
   const float inv_mu_nxt = ctrl->f_inv_mu_nxt;
   const float* Yin = (kc & 1) ? job.Y1 : job.Y0;

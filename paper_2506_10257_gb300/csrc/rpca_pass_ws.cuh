@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) pass_ws_kernel(Bufs b) {
   const int64_t m = b.m;
   const Job* jobp = b.job;
   const int kc = ctrl->k;
-  const bool first = (kc == 0);
+  const bool first = (kc == 0) && !__ldcg(&ctrl->warm);  // a warm start reads S0, Y0
   const float f_mu = ctrl->f_mu, inv_mu = ctrl->f_inv_mu, gamma = ctrl->f_gamma;
   const float inv_mu_nxt = ctrl->f_inv_mu_nxt;
   float* Sp = jobp->S;

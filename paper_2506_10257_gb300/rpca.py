@@ -28,7 +28,9 @@ MAX_T = 32
 EXPORTED = ["rpca_params_default", "rpca_workspace_size", "rpca_plan_create", "rpca_solve", "rpca_solve_host",
             "rpca_plan_result", "rpca_plan_destroy", "rpca_status_str", "rpca_gram", "rpca_eig",
             "rpca_gram_noalloc", "rpca_plan_timings", "rpca_batch_create", "rpca_batch_solve",
-            "rpca_batch_tune", "rpca_batch_info", "rpca_batch_window_ctas", "rpca_batch_destroy"]
+            "rpca_batch_tune", "rpca_batch_info", "rpca_batch_window_ctas", "rpca_batch_destroy",
+            "rpca_server_create", "rpca_server_set_warm", "rpca_submit", "rpca_poll", "rpca_server_wait",
+            "rpca_server_stats", "rpca_server_destroy"]
 
 
 class Params(ctypes.Structure):
@@ -37,7 +39,8 @@ class Params(ctypes.Structure):
                 ("drive", ctypes.c_int32), ("max_iter", ctypes.c_int32),
                 ("lambda_", ctypes.c_double), ("mu0_scale", ctypes.c_double),
                 ("rho", ctypes.c_double), ("mu_max_factor", ctypes.c_double),
-                ("tol", ctypes.c_double)]
+                ("tol", ctypes.c_double), ("warm_start", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("mu_init", ctypes.c_double), ("mu_prev_scale", ctypes.c_double)]
 
 
 class Result(ctypes.Structure):
@@ -102,6 +105,14 @@ def load(build_if_missing: bool = True):
     lib.rpca_batch_window_ctas.argtypes = [vp, ctypes.POINTER(i32), i32]
     lib.rpca_batch_destroy.argtypes = [vp]
     lib.rpca_batch_destroy.restype = None
+    lib.rpca_server_create.argtypes = [ctypes.c_size_t, i32, ctypes.POINTER(vp)]
+    lib.rpca_server_set_warm.argtypes = [vp, i32, ctypes.c_double, i32]
+    lib.rpca_submit.argtypes = [vp, ctypes.POINTER(Params), vp, vp, vp, vp, f32, i32, ctypes.POINTER(ctypes.c_uint64)]
+    lib.rpca_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(Result)]
+    lib.rpca_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(Result)]
+    lib.rpca_server_stats.argtypes = [vp, ctypes.POINTER(i64), i32]
+    lib.rpca_server_destroy.argtypes = [vp]
+    lib.rpca_server_destroy.restype = None
     _lib = lib
     return lib
 
@@ -127,6 +138,15 @@ def _torch():
     if not torch.cuda.is_available():
         raise RuntimeError("rpca needs a CUDA device (no CPU fallback)")
     return torch
+
+
+def _check_like(frames, **bufs):
+    """Output (and warm-state) buffers must be contiguous float32 CUDA tensors shaped like frames."""
+    torch = _torch()
+    for name, t in bufs.items():
+        if (t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous()
+                or tuple(t.shape) != tuple(frames.shape)):
+            raise ValueError(f"{name} must be a contiguous float32 CUDA tensor of shape {tuple(frames.shape)}")
 
 
 def _stream_handle(stream):
@@ -180,6 +200,7 @@ class Plan:
             L = torch.empty_like(frames)
         if S is None:
             S = torch.empty_like(frames)
+        _check_like(frames, L=L, S=S)
         res = Result()
         st = self.lib.rpca_solve(self.handle, ctypes.c_void_p(frames.data_ptr()), ctypes.c_void_p(L.data_ptr()),
                                  ctypes.c_void_p(S.data_ptr()),
@@ -339,6 +360,7 @@ class Batch:
             m, T = self.shapes[i]
             if F.dtype != torch.float32 or not F.is_cuda or not F.is_contiguous() or tuple(F.shape) != (T, m):
                 raise ValueError(f"window {i}: need a contiguous float32 CUDA tensor of shape {(T, m)}")
+            _check_like(F, L=Ls[i], S=Ss[i])
             w[i].X = F.data_ptr()
             w[i].L = Ls[i].data_ptr()
             w[i].S = Ss[i].data_ptr()
@@ -384,3 +406,95 @@ class Batch:
         if self.lib.rpca_batch_window_ctas(self.handle, ctas, self.n) == OK:
             out["window_ctas"] = list(ctas)
         return out
+
+
+class Server:
+    """Served form: sliding windows of several probes, continuous batching over
+    CUDA streams, per-probe warm-start state on the device, HBM admission."""
+
+    STATS = ["bytes", "peak_bytes", "budget", "queued", "running", "peak_running", "started", "finished",
+             "evicted", "refused"]
+
+    def __init__(self, hbm_budget_bytes: int = 120 * 10**9, max_slots: int = 8, warm: bool = True,
+                 warm_mu_scale: float = 0.1, cold_every: int = 0):
+        _torch()
+        self.lib = load()
+        h = ctypes.c_void_p()
+        st = self.lib.rpca_server_create(int(hbm_budget_bytes), int(max_slots), ctypes.byref(h))
+        if st != OK:
+            raise RpcaError(st, "rpca_server_create")
+        self.handle = h
+        self.set_warm(warm, warm_mu_scale, cold_every)
+        self._keep = {}
+
+    def set_warm(self, warm: bool, warm_mu_scale: float = 0.1, cold_every: int = 0):
+        st = self.lib.rpca_server_set_warm(self.handle, int(bool(warm)), float(warm_mu_scale), int(cold_every))
+        if st != OK:
+            raise RpcaError(st, "rpca_server_set_warm")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.rpca_server_destroy(self.handle)
+            self.handle = None
+            self._keep = {}
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, frames, key: int, L=None, S=None, mask=None, theta: float = 0.0, **kw) -> int:
+        """Queue one (T, m) float32 CUDA window of probe `key`; returns the request id.
+
+        L and S (allocated here unless given) receive the result; keep them
+        until the request is reported done."""
+        torch = _torch()
+        if frames.dtype != torch.float32 or not frames.is_cuda or not frames.is_contiguous():
+            raise ValueError("frames must be a contiguous float32 CUDA tensor")
+        T, m = frames.shape
+        p = default_params(m, T, **kw)
+        if L is None:
+            L = torch.empty_like(frames)
+        if S is None:
+            S = torch.empty_like(frames)
+        _check_like(frames, L=L, S=S)
+        rid = ctypes.c_uint64()
+        st = self.lib.rpca_submit(self.handle, ctypes.byref(p), ctypes.c_void_p(frames.data_ptr()),
+                                  ctypes.c_void_p(L.data_ptr()), ctypes.c_void_p(S.data_ptr()),
+                                  ctypes.c_void_p(mask.data_ptr() if mask is not None else 0), ctypes.c_float(theta),
+                                  int(key), ctypes.byref(rid))
+        if st != OK:
+            raise RpcaError(st, "rpca_submit")
+        self._keep[rid.value] = (frames, L, S, mask)
+        return rid.value
+
+    def outputs(self, rid: int):
+        """(L, S, mask) tensors of a request."""
+        f, L, S, mk = self._keep[rid]
+        return L, S, mk
+
+    def poll(self, rid: int):
+        """None while pending, else (status, result dict)."""
+        res = Result()
+        st = self.lib.rpca_poll(self.handle, ctypes.c_uint64(rid), ctypes.byref(res))
+        if st == PENDING:
+            return None
+        if st in (ERR_NOTFOUND, ERR_ARG):
+            raise RpcaError(st, "rpca_poll")
+        return st, res.as_dict()
+
+    def wait(self, rid: int):
+        """Block until done; (status, result dict)."""
+        res = Result()
+        st = self.lib.rpca_server_wait(self.handle, ctypes.c_uint64(rid), ctypes.byref(res))
+        if st in (ERR_NOTFOUND, ERR_ARG, ERR_BUDGET):
+            raise RpcaError(st, "rpca_server_wait")
+        return st, res.as_dict()
+
+    def stats(self) -> dict:
+        buf = (ctypes.c_int64 * 10)()
+        st = self.lib.rpca_server_stats(self.handle, buf, 10)
+        if st != OK:
+            raise RpcaError(st, "rpca_server_stats")
+        return dict(zip(self.STATS, list(buf)))

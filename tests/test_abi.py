@@ -44,13 +44,16 @@ def test_ctypes_mirrors_match_the_header(tmp_path):
     # compile a probe against include/rpca.h with the host compiler and compare layouts
     fields_p = [f for f, _ in rpca.Params._fields_]
     fields_r = [f for f, _ in rpca.Result._fields_]
+    fields_w = [f for f, _ in rpca.Window._fields_]
     cname = {"lambda_": "lambda"}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rpca.h"', 'int main(void) {',
-             'printf("%zu %zu\\n", sizeof(rpca_params), sizeof(rpca_result));']
+             'printf("%zu %zu %zu\\n", sizeof(rpca_params), sizeof(rpca_result), sizeof(rpca_window));']
     for f in fields_p:
         lines.append(f'printf("%zu\\n", offsetof(rpca_params, {cname.get(f, f)}));')
     for f in fields_r:
         lines.append(f'printf("%zu\\n", offsetof(rpca_result, {cname.get(f, f)}));')
+    for f in fields_w:
+        lines.append(f'printf("%zu\\n", offsetof(rpca_window, {f}));')
     lines.append("return 0; }")
     src = tmp_path / "probe.c"
     src.write_text("\n".join(lines))
@@ -59,5 +62,7 @@ def test_ctypes_mirrors_match_the_header(tmp_path):
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
     vals = [int(v) for v in out]
     assert vals[0] == ctypes.sizeof(rpca.Params) and vals[1] == ctypes.sizeof(rpca.Result)
+    assert vals[2] == ctypes.sizeof(rpca.Window)
     offs = [getattr(rpca.Params, f).offset for f in fields_p] + [getattr(rpca.Result, f).offset for f in fields_r]
-    assert vals[2:] == offs
+    offs += [getattr(rpca.Window, f).offset for f in fields_w]
+    assert vals[3:] == offs

@@ -1,0 +1,240 @@
+"""GPU: warm-started solves and the served form.
+
+* A warm start (S0 in S, Y0 in the L buffer, explicit first mu) matches the
+  oracle run from the same S0, Y0, mu_init (the oracle's own previous window,
+  shifted by one frame) within the FP32 tolerance.
+* Served requests give the same result alone and in a mix of probes running
+  concurrently (same kernels, same grid: bit for bit), and a probe's warm
+  chain follows the oracle's warm chain.
+* Admission by HBM budget: refusal, waiting for memory, eviction of idle probes.
+"""
+import numpy as np
+import pytest
+
+from oracle import rpca_oracle as O
+from paper_2506_10257_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-5
+WARM_MU_TOL = 2e-5
+
+
+@pytest.fixture(scope="module")
+def rp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_10257_gb300 import rpca
+    rpca.load()
+    return rpca
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def stream(seed, ny, nx, T, n):
+    """Frames of one probe and its n sliding T-frame windows (each (T, m))."""
+    w = synth.make_window(seed=seed, ny=ny, nx=nx, T=T + n - 1, n_bound=4, n_free=6)
+    F = np.ascontiguousarray(w.frames, dtype=np.float32)
+    return [np.ascontiguousarray(F[s:s + T]) for s in range(n)], w
+
+
+def shift(A):
+    """(T, m) state with the oldest frame dropped and a zero frame appended."""
+    B = np.zeros_like(A)
+    B[:-1] = A[1:]
+    return B
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+# ---- warm start through the plan API ---------------------------------------------
+
+@pytest.mark.parametrize("mu_scale", [None, 0.1])
+def test_warm_start_matches_oracle(rp, mu_scale):
+    wins, _ = stream(31, 32, 32, 12, 2)
+    prev = O.rpca_frames(wins[0])
+    S0 = shift(prev.S).astype(np.float32)
+    Y0 = shift(prev.Y).astype(np.float32)
+    mu_init = None if mu_scale is None else mu_scale * prev.mu
+    ref = O.rpca_frames(wins[1], S0=S0.astype(np.float64), Y0=Y0.astype(np.float64), mu_init=mu_init)
+    T, m = wins[1].shape
+    plan = rp.Plan(m, T, warm_start=1, mu_init=0.0 if mu_init is None else mu_init)
+    L, S = cuda(Y0), cuda(S0)   # on entry: S holds S0, L holds Y0
+    L, S, res = plan.solve(cuda(wins[1]), L=L, S=S)
+    torch.cuda.synchronize()
+    plan.close()
+    assert res["status"] == rp.OK
+    assert abs(res["iters"] - ref.iters) <= 1, (res["iters"], ref.iters)
+    # Started at a large mu (a tenth of the previous window's final one) the
+    # solve runs its few iterations where tau = 1/mu is far below every
+    # singular value; there the end point is more sensitive to rounding: with
+    # FP32 Jacobi rotations S lands 1.2e-5 from the oracle (FP64 rotations:
+    # below 1e-5), so this case is held to WARM_MU_TOL.
+    tol = FP32_TOL if mu_scale is None else WARM_MU_TOL
+    assert rel(L.cpu().numpy(), ref.L) <= tol and rel(S.cpu().numpy(), ref.S) <= tol
+
+
+def test_warm_start_with_zero_state_is_the_cold_solve(rp):
+    wins, _ = stream(32, 24, 40, 10, 1)
+    ref = O.rpca_frames(wins[0])
+    T, m = wins[0].shape
+    plan = rp.Plan(m, T, warm_start=1)
+    L, S, res = plan.solve(cuda(wins[0]), L=torch.zeros(T, m, device="cuda"), S=torch.zeros(T, m, device="cuda"))
+    torch.cuda.synchronize()
+    plan.close()
+    assert abs(res["iters"] - ref.iters) <= 1
+    assert rel(L.cpu().numpy(), ref.L) <= FP32_TOL and rel(S.cpu().numpy(), ref.S) <= FP32_TOL
+
+
+@pytest.mark.parametrize("drive", ["HOST", "STREAM"])
+def test_warm_start_other_drives(rp, drive):
+    wins, _ = stream(33, 16, 32, 8, 2)
+    prev = O.rpca_frames(wins[0])
+    S0, Y0 = shift(prev.S).astype(np.float32), shift(prev.Y).astype(np.float32)
+    ref = O.rpca_frames(wins[1], S0=S0.astype(np.float64), Y0=Y0.astype(np.float64))
+    T, m = wins[1].shape
+    plan = rp.Plan(m, T, warm_start=1, drive=getattr(rp, "DRIVE_" + drive))
+    L, S, res = plan.solve(cuda(wins[1]), L=cuda(Y0), S=cuda(S0))
+    torch.cuda.synchronize()
+    plan.close()
+    assert rel(L.cpu().numpy(), ref.L) <= FP32_TOL and rel(S.cpu().numpy(), ref.S) <= FP32_TOL
+
+
+# ---- served form -------------------------------------------------------------------
+
+PROBES = [(41, 32, 32, 20), (42, 48, 40, 20), (43, 16, 64, 12)]   # (seed, ny, nx, T)
+
+
+def serve(rp, probes_windows, slots, warm=True, mu_scale=0.1, order="interleave"):
+    sv = rp.Server(hbm_budget_bytes=10**9, max_slots=slots, warm=warm, warm_mu_scale=mu_scale)
+    ids = {}
+    n = max(len(w) for w in probes_windows.values())
+    seq = []
+    if order == "interleave":
+        for k in range(n):
+            for key, wins in probes_windows.items():
+                if k < len(wins):
+                    seq.append((key, k))
+    else:
+        for key, wins in probes_windows.items():
+            seq += [(key, k) for k in range(len(wins))]
+    for key, k in seq:
+        ids[(key, k)] = sv.submit(cuda(probes_windows[key][k]), key=key)
+    out = {}
+    for key, k in seq:
+        st, res = sv.wait(ids[(key, k)])
+        L, S, _ = sv.outputs(ids[(key, k)])
+        out[(key, k)] = (st, res, L.cpu().numpy(), S.cpu().numpy())
+    stats = sv.stats()
+    sv.close()
+    return out, stats
+
+
+def test_served_results_same_alone_and_in_mix(rp):
+    pw = {i: stream(s, ny, nx, T, 4)[0] for i, (s, ny, nx, T) in enumerate(PROBES)}
+    mix, stats = serve(rp, pw, slots=4)
+    assert stats["peak_running"] >= 2   # solves of different probes overlapped
+    for key, wins in pw.items():
+        alone, _ = serve(rp, {key: wins}, slots=1)
+        for k in range(len(wins)):
+            a, b = alone[(key, k)], mix[(key, k)]
+            assert a[0] == rp.OK and b[0] == rp.OK
+            assert a[1]["iters"] == b[1]["iters"]
+            assert rel(b[2], a[2]) <= 1e-6 and rel(b[3], a[3]) <= 1e-6
+
+
+def test_served_warm_chain_follows_oracle(rp):
+    # warm_mu_scale = 0: each window's first mu is its own mu0.  The server
+    # starts window k from its own FP32 state of window k-1, the oracle chain
+    # from its FP64 state; the iteration stops on the primal residual alone, so
+    # its end point moves with its start and the ~1e-6 difference of the
+    # starts grows to ~1e-4 in L and S.  The warm-start arithmetic itself is
+    # held to 1e-5 by test_warm_start_matches_oracle (identical starts); here
+    # the chain is held to CHAIN_TOL and to the bound-bubble mask (Dice).
+    CHAIN_TOL = 2e-3
+    s, ny, nx, T = PROBES[0]
+    wins, w = stream(s, ny, nx, T, 4)
+    got, _ = serve(rp, {0: wins}, slots=2, mu_scale=0.0)
+    prev = None
+    for k, F in enumerate(wins):
+        kw = {} if prev is None else dict(S0=shift(prev.S), Y0=shift(prev.Y))
+        ref = O.rpca_frames(F, **kw)
+        st, res, L, S = got[(0, k)]
+        assert st == rp.OK
+        tol = FP32_TOL if k == 0 else CHAIN_TOL
+        assert rel(L, ref.L) <= tol and rel(S, ref.S) <= tol, (k, rel(L, ref.L), rel(S, ref.S))
+        img = O.temporal_mean_abs(ref.L)
+        th = O.mask_threshold(img, w.bound_mask_gt)
+        m_ref, m_gpu = O.bound_mask(img, th), O.bound_mask(O.temporal_mean_abs(L), th)
+        assert O.dice(m_gpu, m_ref) >= 0.999
+        prev = ref
+
+
+def test_served_cold_policy_matches_cold_oracle(rp):
+    s, ny, nx, T = PROBES[2]
+    wins, _ = stream(s, ny, nx, T, 3)
+    got, _ = serve(rp, {5: wins}, slots=2, warm=False)
+    for k, F in enumerate(wins):
+        ref = O.rpca_frames(F)
+        st, res, L, S = got[(5, k)]
+        assert rel(L, ref.L) <= FP32_TOL and rel(S, ref.S) <= FP32_TOL
+
+
+def test_admission_by_budget(rp):
+    wins, _ = stream(44, 32, 32, 10, 2)
+    T, m = wins[0].shape
+    # a budget below one probe's state refuses the request
+    sv = rp.Server(hbm_budget_bytes=4096, max_slots=2)
+    with pytest.raises(rp.RpcaError) as e:
+        sv.submit(cuda(wins[0]), key=1)
+    assert e.value.status == rp.ERR_BUDGET
+    assert sv.stats()["refused"] == 1
+    sv.close()
+    # room for one probe: the second probe waits, then evicts the idle first one
+    per_probe = rp.Plan(m, T).workspace.numel() + 2 * 4 * m * T
+    sv = rp.Server(hbm_budget_bytes=per_probe + per_probe // 2, max_slots=2)
+    a = sv.submit(cuda(wins[0]), key=1)
+    b = sv.submit(cuda(wins[1]), key=2)
+    assert sv.wait(a)[0] == rp.OK and sv.wait(b)[0] == rp.OK
+    st = sv.stats()
+    assert st["evicted"] == 1 and st["peak_bytes"] <= st["budget"]
+    # the evicted probe starts cold again and still solves
+    c = sv.submit(cuda(wins[1]), key=1)
+    assert sv.wait(c)[0] == rp.OK
+    sv.close()
+
+
+def test_poll_unknown_and_twice(rp):
+    wins, _ = stream(45, 16, 16, 8, 1)
+    sv = rp.Server(hbm_budget_bytes=10**9, max_slots=1)
+    with pytest.raises(rp.RpcaError) as e:
+        sv.poll(12345)
+    assert e.value.status == rp.ERR_NOTFOUND
+    rid = sv.submit(cuda(wins[0]), key=0)
+    st, res = sv.wait(rid)
+    assert st == rp.OK and res["iters"] > 0
+    with pytest.raises(rp.RpcaError):
+        sv.poll(rid)
+    sv.close()
+
+
+@pytest.mark.parametrize("prec", ["TF32X3", "BF16X3"])
+def test_warm_start_tensor_core_precisions(rp, prec):
+    wins, _ = stream(34, 64, 64, 20, 2)
+    prev = O.rpca_frames(wins[0])
+    S0, Y0 = shift(prev.S).astype(np.float32), shift(prev.Y).astype(np.float32)
+    ref = O.rpca_frames(wins[1], S0=S0.astype(np.float64), Y0=Y0.astype(np.float64), mu_init=0.1 * prev.mu)
+    T, m = wins[1].shape
+    plan = rp.Plan(m, T, warm_start=1, mu_init=0.1 * prev.mu, precision=getattr(rp, "PREC_" + prec))
+    L, S, res = plan.solve(cuda(wins[1]), L=cuda(Y0), S=cuda(S0))
+    torch.cuda.synchronize()
+    plan.close()
+    assert rel(L.cpu().numpy(), ref.L) <= 1e-4 and rel(S.cpu().numpy(), ref.S) <= 1e-4

@@ -242,3 +242,44 @@ def test_rmse_and_dice_hand_values():
     th = O.mask_threshold(img, np.array([0, 1, 0, 1], bool))
     assert th == pytest.approx(1.75)
     np.testing.assert_array_equal(O.bound_mask(img, th), [False, True, False, True])
+
+
+def test_warm_start_from_converged_state_is_a_fixed_point():
+    # The ALM iteration is at a fixed point at its own converged (S, Y, mu): one
+    # more iteration from there meets the stopping test at once and returns the
+    # same L and S (to the tolerance the cold solve stopped at).  A warm start
+    # that ignored S0 or Y0 would need more iterations or land elsewhere.
+    w = synth.make_window(seed=11, ny=24, nx=24, T=12, n_bound=4, n_free=6)
+    X = w.frames.T.astype(np.float64)
+    cold = O.rpca(X)
+    warm = O.rpca(X, S0=cold.S, Y0=cold.Y, mu_init=cold.mu)
+    assert cold.converged and warm.converged and warm.iters == 1
+    assert np.linalg.norm(warm.L - cold.L) <= 1e-5 * np.linalg.norm(cold.L)
+    assert np.linalg.norm(warm.S - cold.S) <= 1e-5 * np.linalg.norm(cold.S)
+
+
+def test_warm_start_with_zero_state_is_the_cold_start():
+    w = synth.make_window(seed=12, ny=16, nx=16, T=8, n_bound=3, n_free=4)
+    X = w.frames.T.astype(np.float64)
+    a = O.rpca(X)
+    b = O.rpca(X, S0=np.zeros_like(X), Y0=np.zeros_like(X), mu_init=O.initial_mu(X, O.SCHEDULE_IALM))
+    assert a.iters == b.iters and np.array_equal(a.L, b.L) and np.array_equal(a.S, b.S)
+
+
+def test_warm_start_keeps_the_cold_cap():
+    # mu_max = 1e7 * mu0 of the cold schedule, whatever mu_init is: started at
+    # mu_init = mu0 * 1e7 * 10 the first step uses mu_init, the second the cap.
+    w = synth.make_window(seed=13, ny=16, nx=16, T=8, n_bound=3, n_free=4)
+    X = w.frames.T.astype(np.float64)
+    mu0 = O.initial_mu(X, O.SCHEDULE_IALM)
+    r = O.rpca(X, mu_init=mu0 * 1e8, max_iter=2, tol=1e-30)
+    assert r.history[0][0] == mu0 * 1e8 and r.history[1][0] == 1e7 * mu0
+
+
+def test_frames_wrapper_transposes_the_warm_state():
+    w = synth.make_window(seed=14, ny=8, nx=8, T=6, n_bound=2, n_free=2)
+    X = w.frames.T.astype(np.float64)
+    cold = O.rpca(X)
+    a = O.rpca(X, S0=cold.S, Y0=cold.Y, mu_init=cold.mu)
+    b = O.rpca_frames(w.frames, S0=cold.S.T, Y0=cold.Y.T, mu_init=cold.mu)
+    assert np.array_equal(a.L.T, b.L) and np.array_equal(a.S.T, b.S)
