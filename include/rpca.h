@@ -75,7 +75,8 @@ typedef enum {
 
 typedef struct {
   int64_t m;                /* pixels per frame (rows of X), >= 1 */
-  int32_t T;                /* frames (columns of X), 1 <= T <= RPCA_MAX_T */
+  int32_t T;                /* frames (columns of X), 1 <= T <= RPCA_MAX_T; precisions other
+                               than FP32 need T <= RPCA_MAX_T_NARROW */
   int32_t dtype;            /* rpca_dtype */
   int32_t precision;        /* rpca_precision */
   int32_t mu_schedule;      /* rpca_mu_schedule */
@@ -100,7 +101,10 @@ typedef struct {
                                final mu of this plan's previous solve (default 0) */
 } rpca_params;
 
-#define RPCA_MAX_T 32
+/* Largest frame count.  Windows of T <= 32 frames run one pixel row per
+ * thread; T in 33..224 run the shared-memory tiled path (FP32 only). */
+#define RPCA_MAX_T 224
+#define RPCA_MAX_T_NARROW 32
 
 typedef struct {
   int32_t status;           /* rpca_status of this solve */
@@ -289,14 +293,15 @@ void rpca_server_destroy(rpca_server_t server);
  * real float32) and V a T x T row-major float32 matrix (NULL = identity).
  * G is written as T x T row-major float64 on the device.  This is the
  * contraction that feeds the SVT step of Eq. 4 (SVD of Z through the
- * eigen-decomposition of its Gram).  Synchronous on `stream`. */
+ * eigen-decomposition of its Gram).  T <= RPCA_MAX_T_NARROW.  Synchronous on
+ * `stream`. */
 rpca_status rpca_gram(const float* X, int64_t m, int32_t T, const float* V, double* G,
                       int32_t precision, void* stream);
 
 /* Symmetric eigen-decomposition of a T x T float64 matrix G (row-major,
  * device) by cyclic Jacobi in FP64 on one CTA: on return evals[i] and the
  * columns of evecs (T x T row-major, device) satisfy G evecs = evecs diag(evals),
- * evals in descending order.  Synchronous on `stream`. */
+ * evals in descending order.  T <= RPCA_MAX_T_NARROW.  Synchronous on `stream`. */
 rpca_status rpca_eig(const double* G, int32_t T, double* evals, double* evecs, void* stream);
 
 /* ---- entry point that allocates no device memory ------------------------ */
@@ -315,7 +320,7 @@ rpca_status rpca_eig(const double* G, int32_t T, double* evals, double* evecs, v
  * 512 CTAs, reduction counters, control block) is a fixed array compiled into
  * the library, one copy on every GPU that loads it, held until the process
  * exits.  The caller still provides X, V and G.
- *   - T must be <= RPCA_MAX_T (else RPCA_ERR_UNSUPPORTED); m is not limited
+ *   - T must be <= RPCA_MAX_T_NARROW (else RPCA_ERR_UNSUPPORTED); m is not limited
  *     (the CTAs stride over the pixels).
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call

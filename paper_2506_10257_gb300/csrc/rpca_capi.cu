@@ -103,9 +103,10 @@ bool get_set(int T, KernelSet* out) {
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Layout {
-  size_t ctrl, eig, red, job, gram_part, group_part, scal_part, gscal_part, ybuf, total;
+  size_t ctrl, eig, red, job, gw, ww, vw, evw, rlog, rrnd, gram_part, group_part, scal_part, gscal_part, ybuf, total;
   int grid, ngroups;
-  int ws_grid;   // CTAs of the warp-specialised pass (one per SM, 128-pixel tiles)
+  int ws_grid;     // CTAs of the warp-specialised pass (one per SM, 128-pixel tiles)
+  int wide_grid;   // CTAs of the wide pass (T > kMaxT; one per SM, 32-pixel tiles)
 };
 
 int device_sms() {
@@ -123,7 +124,8 @@ Layout make_layout(int64_t m, int T, int sms) {
   grid = std::min<int64_t>(grid, (int64_t)kGroup * kMaxGroups);
   L.grid = (int)std::max<int64_t>(grid, 1);
   L.ws_grid = (int)std::max<int64_t>(std::min<int64_t>((m + 127) / 128, std::max(sms, 1)), 1);
-  const int maxgrid = std::max(L.grid, L.ws_grid);
+  L.wide_grid = (int)std::max<int64_t>(std::min<int64_t>((m + 31) / 32, std::max(sms, 1)), 1);
+  const int maxgrid = std::max({L.grid, L.ws_grid, T > kMaxT ? L.wide_grid : 1});
   L.ngroups = (maxgrid + kGroup - 1) / kGroup;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -135,6 +137,16 @@ Layout make_layout(int64_t m, int T, int sms) {
   L.eig = take(sizeof(EigState));
   L.red = take(sizeof(RedState));
   L.job = take(sizeof(Job));
+  const size_t tw = T > kMaxT ? (size_t)T * T : 1;   // wide-path Gram, Wbar, V
+  L.gw = take(sizeof(float) * tw);
+  L.ww = take(sizeof(float) * tw);
+  L.vw = take(sizeof(float) * tw);
+  L.evw = take(sizeof(double) * (size_t)T);
+  // rotation log of the wide eigen-step: every round of kWideLogSweeps sweeps
+  const size_t nrounds = T > kMaxT ? (size_t)kWideLogSweeps * (size_t)(T + (T & 1)) : 1;
+  const size_t npairs = T > kMaxT ? (size_t)(T + (T & 1)) / 2 : 1;
+  L.rlog = take(sizeof(float2) * nrounds * npairs);
+  L.rrnd = take(sizeof(int) * nrounds);
   L.gram_part = take(sizeof(float) * (size_t)maxgrid * T * T);
   L.group_part = take(sizeof(float) * (size_t)L.ngroups * T * T);
   L.scal_part = take(sizeof(double) * 2 * (size_t)maxgrid);
@@ -157,6 +169,7 @@ rpca_status validate(const rpca_params* p) {
   if (p->dtype != RPCA_R32) return RPCA_ERR_UNSUPPORTED;
   if (p->precision < RPCA_PREC_FP32 || p->precision > RPCA_PREC_TF32) return RPCA_ERR_ARG;
   if (p->precision != RPCA_PREC_FP32 && p->drive == RPCA_DRIVE_HOST) return RPCA_ERR_UNSUPPORTED;
+  if (p->precision != RPCA_PREC_FP32 && p->T > kMaxT) return RPCA_ERR_UNSUPPORTED;  // wide path is FP32
   if (p->m * (int64_t)p->T > (int64_t)1 << 40) return RPCA_ERR_ARG;
   if (p->warm_start != 0 && p->warm_start != 1) return RPCA_ERR_ARG;
   if (!(p->mu_init >= 0.0) || !(p->mu_prev_scale >= 0.0) || !isfinite(p->mu_init) || !isfinite(p->mu_prev_scale))
@@ -169,6 +182,8 @@ rpca_status validate(const rpca_params* p) {
 struct rpca_plan_s {
   rpca_params p;
   KernelSet ks;
+  bool wide;          // T > kMaxT: shared-memory tiled passes, 1024-thread eigen-step
+  WideKernels wk;
   Layout lay;
   Bufs bufs;
   char* ws;
@@ -233,20 +248,40 @@ static cudaError_t launch(void* fn, dim3 g, dim3 blk, void** args, cudaStream_t 
 // the fast FP32 form.  Both take (Bufs, flags, handle, use_cond, ...); the
 // extra pointer arguments only exist in the smem form and are ignored by the
 // fast one.
-static void* eig_fn(const rpca_plan_s* pl) { return pl->eig_fp64 ? pl->ks.eig64 : pl->ks.eig_fast; }
-static size_t eig_smem(const rpca_plan_s* pl) { return pl->eig_fp64 ? 0 : pl->ks.eig_fast_smem; }
-static dim3 eig_block(const rpca_plan_s* pl) { return dim3(pl->eig_fp64 ? pl->ks.eig_threads : kEigThreads); }
+static void* eig_fn(const rpca_plan_s* pl) {
+  if (pl->wide) return pl->wk.eig;
+  return pl->eig_fp64 ? pl->ks.eig64 : pl->ks.eig_fast;
+}
+static size_t eig_smem(const rpca_plan_s* pl) {
+  if (pl->wide) return pl->wk.eig_smem;
+  return pl->eig_fp64 ? 0 : pl->ks.eig_fast_smem;
+}
+static dim3 eig_block(const rpca_plan_s* pl) {
+  if (pl->wide) return dim3(pl->wk.eig_threads);
+  return dim3(pl->eig_fp64 ? pl->ks.eig_threads : kEigThreads);
+}
+// CUDA-core FP32 passes by mode (narrow: one pixel row per thread; wide: tiles).
+static void* pass_fn(const rpca_plan_s* pl, int mode) { return pl->wide ? pl->wk.pass[mode] : pl->ks.pass[mode]; }
+static size_t pass_smem(const rpca_plan_s* pl) { return pl->wide ? pl->wk.pass_smem : pl->ks.pass_smem; }
+static dim3 pass_grid(const rpca_plan_s* pl) { return dim3(pl->wide ? pl->lay.wide_grid : pl->lay.grid); }
+static dim3 pass_block(const rpca_plan_s* pl) { return dim3(pl->wide ? pl->wk.pass_threads : kPassThreads); }
 // Fused per-iteration pass: CUDA-core FP32 or the tensor-core form of the plan's precision.
 static void* fused_fn(const rpca_plan_s* pl) {
-  if (pl->p.precision == RPCA_PREC_FP32) return pl->ks.pass[PM_FUSED];  // dynamic smem: ks.pass_smem
+  if (pl->p.precision == RPCA_PREC_FP32) return pass_fn(pl, PM_FUSED);
   return pl->use_ws ? pl->ks.pass_ws[pl->p.precision] : pl->ks.pass_tc[pl->p.precision];
 }
 static size_t fused_smem(const rpca_plan_s* pl) {
-  if (pl->p.precision == RPCA_PREC_FP32) return pl->ks.pass_smem;
+  if (pl->p.precision == RPCA_PREC_FP32) return pass_smem(pl);
   return pl->use_ws ? pl->ks.pass_ws_smem[pl->p.precision] : pl->ks.pass_tc_smem[pl->p.precision];
 }
-static dim3 fused_grid(const rpca_plan_s* pl) { return dim3(pl->use_ws ? pl->lay.ws_grid : pl->lay.grid); }
-static dim3 fused_block(const rpca_plan_s* pl) { return dim3(pl->use_ws ? kWsThreads : kPassThreads); }
+static dim3 fused_grid(const rpca_plan_s* pl) {
+  if (pl->p.precision == RPCA_PREC_FP32) return pass_grid(pl);
+  return dim3(pl->use_ws ? pl->lay.ws_grid : pl->lay.grid);
+}
+static dim3 fused_block(const rpca_plan_s* pl) {
+  if (pl->p.precision == RPCA_PREC_FP32) return pass_block(pl);
+  return dim3(pl->use_ws ? kWsThreads : kPassThreads);
+}
 
 static cudaError_t add_kernel(cudaGraph_t g, cudaGraphNode_t* node, const cudaGraphNode_t* deps, size_t ndeps,
                               void* fn, dim3 grid, dim3 blk, void** args, size_t smem = 0) {
@@ -267,7 +302,7 @@ static rpca_status build_graph(rpca_plan_s* pl) {
   cudaGraphConditionalHandle h;
   CK(cudaGraphConditionalHandleCreate(&h, pl->graph, 0, cudaGraphCondAssignDefault));
   Bufs b = pl->bufs;
-  const dim3 pg(pl->lay.grid), pb(kPassThreads), eg(1), eb = eig_block(pl);
+  const dim3 pg = pass_grid(pl), pb = pass_block(pl), eg(1), eb = eig_block(pl);
   const size_t es = eig_smem(pl);
   const double* nulld = nullptr;
   double* nullo = nullptr;
@@ -278,14 +313,14 @@ static rpca_status build_graph(rpca_plan_s* pl) {
   void* a_eig0[] = {&b, &f_init, &h, &use_cond, &nulld, &nullo, &nullo};
   void* a_eig1[] = {&b, &f_iter, &h, &use_cond, &nulld, &nullo, &nullo};
   cudaGraphNode_t n_init, n_eig0, n_while, n_fin, n_pass, n_eig;
-  CK(add_kernel(pl->graph, &n_init, nullptr, 0, pl->ks.pass[PM_INIT], pg, pb, a_pass, pl->ks.pass_smem));
+  CK(add_kernel(pl->graph, &n_init, nullptr, 0, pass_fn(pl, PM_INIT), pg, pb, a_pass, pass_smem(pl)));
   CK(add_kernel(pl->graph, &n_eig0, &n_init, 1, eig_fn(pl), eg, eb, a_eig0, es));
   if (pl->p.warm_start) {
     // warm start: the first SVT needs the Gram of Z1 = X - S0 + Y0/mu1, not of X
     int f_eig = EF_EIG | EF_FULL;
     void* a_eigw[] = {&b, &f_eig, &h, &use_cond, &nulld, &nullo, &nullo};
     cudaGraphNode_t n_gw, n_ew;
-    CK(add_kernel(pl->graph, &n_gw, &n_eig0, 1, pl->ks.pass[PM_GRAM], pg, pb, a_pass, pl->ks.pass_smem));
+    CK(add_kernel(pl->graph, &n_gw, &n_eig0, 1, pass_fn(pl, PM_GRAM), pg, pb, a_pass, pass_smem(pl)));
     CK(add_kernel(pl->graph, &n_ew, &n_gw, 1, eig_fn(pl), eg, eb, a_eigw, es));
     n_eig0 = n_ew;
   }
@@ -385,11 +420,19 @@ rpca_status rpca_plan_create(const rpca_params* p, void* workspace, size_t works
   if (sms <= 0) return RPCA_ERR_CUDA;
   rpca_plan_s* pl = new rpca_plan_s();
   pl->p = *p;
-  if (!get_set(p->T, &pl->ks)) {
-    delete pl;
-    return RPCA_ERR_UNSUPPORTED;
+  pl->wide = p->T > kMaxT;
+  if (pl->wide) {
+    if (!wide_kernels(p->T, &pl->wk)) {
+      delete pl;
+      return RPCA_ERR_UNSUPPORTED;
+    }
+  } else {
+    if (!get_set(p->T, &pl->ks)) {
+      delete pl;
+      return RPCA_ERR_UNSUPPORTED;
+    }
+    set_tc(p->T, &pl->ks);
   }
-  set_tc(p->T, &pl->ks);
   pl->use_ws = (p->precision != RPCA_PREC_FP32) && (p->m % 4 == 0) && tma_encoder() != nullptr &&
                !(getenv("RPCA_NO_WS") && atoi(getenv("RPCA_NO_WS")) != 0);
   if (p->precision != RPCA_PREC_FP32) {
@@ -404,7 +447,7 @@ rpca_status rpca_plan_create(const rpca_params* p, void* workspace, size_t works
     }
   }
   pl->lay = make_layout(p->m, p->T, sms);
-  if (pl->ks.eig_fast_smem > 48 * 1024) {
+  if (!pl->wide && pl->ks.eig_fast_smem > 48 * 1024) {
     cudaError_t ea = cudaFuncSetAttribute(pl->ks.eig_fast, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)pl->ks.eig_fast_smem);
     if (ea != cudaSuccess) {
@@ -437,6 +480,12 @@ rpca_status rpca_plan_create(const rpca_params* p, void* workspace, size_t works
   b.group_part = (float*)(pl->ws + pl->lay.group_part);
   b.scal_part = (double*)(pl->ws + pl->lay.scal_part);
   b.gscal_part = (double*)(pl->ws + pl->lay.gscal_part);
+  b.Gw = (float*)(pl->ws + pl->lay.gw);
+  b.Ww = (float*)(pl->ws + pl->lay.ww);
+  b.Vw = (float*)(pl->ws + pl->lay.vw);
+  b.evw = (double*)(pl->ws + pl->lay.evw);
+  b.rot_log = (float2*)(pl->ws + pl->lay.rlog);
+  b.rot_rnd = (int*)(pl->ws + pl->lay.rrnd);
   b.m = p->m;
   b.T = p->T;
   b.grid = pl->lay.grid;
@@ -494,7 +543,7 @@ rpca_status rpca_plan_create(const rpca_params* p, void* workspace, size_t works
 // host after every iteration (one host synchronisation per iteration).
 static rpca_status run_host_loop(rpca_plan_s* pl, cudaStream_t s) {
   Bufs b = pl->bufs;
-  const dim3 pg(pl->lay.grid), pb(kPassThreads), eg(1), eb = eig_block(pl);
+  const dim3 pg = pass_grid(pl), pb = pass_block(pl), eg(1), eb = eig_block(pl);
   const size_t es = eig_smem(pl);
   cudaGraphConditionalHandle h = 0;
   const double* nulld = nullptr;
@@ -505,24 +554,24 @@ static rpca_status run_host_loop(rpca_plan_s* pl, cudaStream_t s) {
   void* a_init[] = {&b, &f_init, &h, &use_cond, &nulld, &nullo, &nullo};
   void* a_check[] = {&b, &f_check, &h, &use_cond, &nulld, &nullo, &nullo};
   void* a_eig[] = {&b, &f_eig, &h, &use_cond, &nulld, &nullo, &nullo};
-  CK(launch(pl->ks.pass[PM_INIT], pg, pb, a_pass, s, pl->ks.pass_smem));
+  CK(launch(pass_fn(pl, PM_INIT), pg, pb, a_pass, s, pass_smem(pl)));
   CK(launch(eig_fn(pl), eg, eb, a_init, s, es));
   if (pl->p.warm_start) {
     int f_full = EF_EIG | EF_FULL;
     void* a_full[] = {&b, &f_full, &h, &use_cond, &nulld, &nullo, &nullo};
-    CK(launch(pl->ks.pass[PM_GRAM], pg, pb, a_pass, s, pl->ks.pass_smem));
+    CK(launch(pass_fn(pl, PM_GRAM), pg, pb, a_pass, s, pass_smem(pl)));
     CK(launch(eig_fn(pl), eg, eb, a_full, s, es));
   }
   for (int it = 0; it <= pl->p.max_iter; ++it) {
     CK(cudaMemcpyAsync(pl->ctrl_host, b.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (pl->ctrl_host->done) break;
-    CK(launch(pl->ks.pass[PM_UPDATE], pg, pb, a_pass, s, pl->ks.pass_smem));
+    CK(launch(pass_fn(pl, PM_UPDATE), pg, pb, a_pass, s, pass_smem(pl)));
     CK(launch(eig_fn(pl), eg, eb, a_check, s, es));
     CK(cudaMemcpyAsync(pl->ctrl_host, b.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (pl->ctrl_host->done) break;
-    CK(launch(pl->ks.pass[PM_GRAM], pg, pb, a_pass, s, pl->ks.pass_smem));
+    CK(launch(pass_fn(pl, PM_GRAM), pg, pb, a_pass, s, pass_smem(pl)));
     CK(launch(eig_fn(pl), eg, eb, a_eig, s, es));
   }
   const int fgrid = (int)std::min<int64_t>((pl->p.m + 255) / 256, 4096);
@@ -535,7 +584,7 @@ static rpca_status run_host_loop(rpca_plan_s* pl, cudaStream_t s) {
 // at once.
 static rpca_status run_stream_loop(rpca_plan_s* pl, cudaStream_t s) {
   Bufs b = pl->bufs;
-  const dim3 pg(pl->lay.grid), pb(kPassThreads), eg(1), eb = eig_block(pl);
+  const dim3 pg = pass_grid(pl), pb = pass_block(pl), eg(1), eb = eig_block(pl);
   const size_t es = eig_smem(pl);
   cudaGraphConditionalHandle h = 0;
   const double* nulld = nullptr;
@@ -545,12 +594,12 @@ static rpca_status run_stream_loop(rpca_plan_s* pl, cudaStream_t s) {
   void* a_pass[] = {&b};
   void* a_init[] = {&b, &f_init, &h, &use_cond, &nulld, &nullo, &nullo};
   void* a_iter[] = {&b, &f_iter, &h, &use_cond, &nulld, &nullo, &nullo};
-  CK(launch(pl->ks.pass[PM_INIT], pg, pb, a_pass, s, pl->ks.pass_smem));
+  CK(launch(pass_fn(pl, PM_INIT), pg, pb, a_pass, s, pass_smem(pl)));
   CK(launch(eig_fn(pl), eg, eb, a_init, s, es));
   if (pl->p.warm_start) {
     int f_eig = EF_EIG | EF_FULL;
     void* a_eig[] = {&b, &f_eig, &h, &use_cond, &nulld, &nullo, &nullo};
-    CK(launch(pl->ks.pass[PM_GRAM], pg, pb, a_pass, s, pl->ks.pass_smem));
+    CK(launch(pass_fn(pl, PM_GRAM), pg, pb, a_pass, s, pass_smem(pl)));
     CK(launch(eig_fn(pl), eg, eb, a_eig, s, es));
   }
   for (int it = 0; it < pl->p.max_iter; ++it) {
@@ -688,7 +737,7 @@ const char* rpca_status_str(int32_t s) {
 rpca_status rpca_gram(const float* X, int64_t m, int32_t T, const float* V, double* G, int32_t precision,
                       void* stream) {
   if (!X || !G || m < 1 || T < 1) return RPCA_ERR_ARG;
-  if (T > RPCA_MAX_T) return RPCA_ERR_UNSUPPORTED;
+  if (T > kMaxT) return RPCA_ERR_UNSUPPORTED;
   if (precision != RPCA_PREC_FP32) return RPCA_ERR_UNSUPPORTED;
   rpca_params p;
   rpca_params_default(&p, m, T);
@@ -741,7 +790,7 @@ rpca_status rpca_gram(const float* X, int64_t m, int32_t T, const float* V, doub
 
 rpca_status rpca_eig(const double* G, int32_t T, double* evals, double* evecs, void* stream) {
   if (!G || !evals || !evecs || T < 1) return RPCA_ERR_ARG;
-  if (T > RPCA_MAX_T) return RPCA_ERR_UNSUPPORTED;
+  if (T > kMaxT) return RPCA_ERR_UNSUPPORTED;
   rpca_params p;
   rpca_params_default(&p, 1, T);
   p.drive = RPCA_DRIVE_HOST;

@@ -24,7 +24,9 @@
 
 namespace rpca {
 
-constexpr int kMaxT = 32;            // largest frame count of this build
+constexpr int kMaxT = 32;            // largest frame count of the register-resident passes
+constexpr int kMaxTW = 224;          // largest frame count of the wide (shared-memory tiled) path
+constexpr int kWideLogSweeps = 30;   // Jacobi sweeps one wide eigen-step may take (and log)
 constexpr int kPassThreads = 256;    // one pixel per thread per tile
 constexpr int kTile = kPassThreads;  // pixels per CTA tile
 constexpr int kGroup = 16;           // CTAs per first-level reduction group
@@ -139,6 +141,14 @@ struct Bufs {
   int ngroups;
   int finalize;        // 1: the pass itself sums the group partials into red->G, e2, l1;
                        // 0: the next eigen-step does (saves a serial reduction level)
+  // T > kMaxT ("wide" windows): the reduced Gram, Wbar and V live in these
+  // T x T row-major arrays of the workspace instead of red->G and EigState.
+  float* Gw;
+  float* Ww;
+  float* Vw;
+  double* evw;
+  float2* rot_log;    // wide eigen-step: (c, s) of every pair of every executed round
+  int* rot_rnd;       // ... and the round number of each
 };
 
 }  // namespace rpca

@@ -15,6 +15,21 @@ struct PlanView {
   float* y1;          // second dual buffer (workspace)
 };
 
+// Kernels of the wide path (kMaxT < T <= kMaxTW), defined in rpca_wide.cu.
+struct WideKernels {
+  void* pass[4];        // per PassMode
+  size_t pass_smem;
+  int pass_threads;
+  int tile;             // pixels per tile
+  void* eig;            // (Bufs, flags, handle, use_cond)
+  size_t eig_smem;
+  int eig_threads;
+};
+
+// Fills *out for T (false when T is not a wide frame count or a kernel
+// attribute cannot be set).
+bool wide_kernels(int T, WideKernels* out);
+
 // Fills *v from a plan; RPCA_ERR_ARG for a null plan.
 rpca_status plan_view(rpca_plan_t plan, PlanView* v);
 

@@ -85,9 +85,30 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
 // fixed order (Kahan), calling out(e, sum) for every entry; each thread takes
 // entries tid, tid + blockDim, ... and issues its loads in batches of 16 so
 // that their L2 latencies overlap.
-template <typename Out>
+template <int W = 1, typename Out>
 __device__ __forceinline__ void sum_rows(const float* src, int r0, int r1, int TT, Out out) {
-  for (int e = threadIdx.x; e < TT; e += blockDim.x) {
+  // W = 4: four entries per step (T x T Grams of wide windows), so that 64
+  // loads are in flight per thread
+  int e = threadIdx.x;
+  for (; W == 4 && e + 3 * (int)blockDim.x < TT; e += 4 * blockDim.x) {
+    float s[4] = {0.f, 0.f, 0.f, 0.f}, comp[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int rb = r0; rb < r1; rb += 16) {
+      float v[4][16];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+          v[q][u] = (rb + u < r1) ? __ldcg(&src[(int64_t)(rb + u) * TT + e + q * blockDim.x]) : 0.f;
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+          if (rb + u < r1) kahan_add(s[q], comp[q], v[q][u]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) out(e + q * blockDim.x, s[q]);
+  }
+  for (; e < TT; e += blockDim.x) {
     float s = 0.f, comp = 0.f;
     for (int rb = r0; rb < r1; rb += 16) {
       float v[16];
@@ -137,6 +158,7 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 // groups, in fixed order, into red->G, red->e2 and red->l1 (only when
 // b.finalize; otherwise the next eigen-step does).  Called by all threads of
 // every CTA; returns true in the CTA that wrote the final sums.
+template <int W = 1>
 static __device__ __noinline__ bool cross_cta_reduce(Bufs b, bool kGram, double* sScal, int* sLastp, int lc, int nc) {
   const int tid = threadIdx.x;
   const int T = b.T;
@@ -158,7 +180,7 @@ static __device__ __noinline__ bool cross_cta_reduce(Bufs b, bool kGram, double*
   __threadfence();
   if (kGram) {
     float* gp = b.group_part + (int64_t)grp * TT;
-    sum_rows(b.gram_part, c0, c1, TT, [&](int e, float v) { gp[e] = v; });
+    sum_rows<W>(b.gram_part, c0, c1, TT, [&](int e, float v) { gp[e] = v; });
   }
   sum_scalars(b.scal_part, c0, c1, sScal, [&](double s0, double s1) {
     b.gscal_part[2 * grp] = s0;
@@ -187,8 +209,13 @@ static __device__ __noinline__ bool cross_cta_reduce(Bufs b, bool kGram, double*
   if (!sLast) return false;
   __threadfence();
   if (kGram) {
-    float* G = b.red->G;
-    sum_rows(b.group_part, 0, ngroups, TT, [&](int e, float v) { G[(e / T) * kMaxT + e % T] = v; });
+    if (T > kMaxT) {
+      float* G = b.Gw;
+      sum_rows<W>(b.group_part, 0, ngroups, TT, [&](int e, float v) { G[e] = v; });
+    } else {
+      float* G = b.red->G;
+      sum_rows(b.group_part, 0, ngroups, TT, [&](int e, float v) { G[(e / T) * kMaxT + e % T] = v; });
+    }
   }
   sum_scalars(b.gscal_part, 0, ngroups, sScal, [&](double s0, double s1) {
     b.red->e2 = s0;
@@ -461,8 +488,13 @@ static __device__ void finalize_sums(Bufs b, double* sh) {
   const int T = b.T, TT = T * T;
   const int ng = b.red->ngroups_last;
   if (b.red->gram_last) {
-    float* G = b.red->G;
-    sum_rows(b.group_part, 0, ng, TT, [&](int e, float v) { G[(e / T) * kMaxT + e % T] = v; });
+    if (T > kMaxT) {
+      float* G = b.Gw;
+      sum_rows<4>(b.group_part, 0, ng, TT, [&](int e, float v) { G[e] = v; });
+    } else {
+      float* G = b.red->G;
+      sum_rows(b.group_part, 0, ng, TT, [&](int e, float v) { G[(e / T) * kMaxT + e % T] = v; });
+    }
   }
   sum_scalars(b.gscal_part, 0, ng, sh, [&](double s0, double s1) {
     b.red->e2 = s0;

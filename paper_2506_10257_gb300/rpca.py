@@ -23,7 +23,8 @@ R32, C64 = 0, 1
 PREC_FP32, PREC_TF32X3, PREC_BF16X3, PREC_TF32 = 0, 1, 2, 3
 MU_IALM, MU_FIXED_L1 = 0, 1
 DRIVE_GRAPH, DRIVE_HOST, DRIVE_STREAM = 0, 1, 2
-MAX_T = 32
+MAX_T = 224
+MAX_T_NARROW = 32
 
 EXPORTED = ["rpca_params_default", "rpca_workspace_size", "rpca_plan_create", "rpca_solve", "rpca_solve_host",
             "rpca_plan_result", "rpca_plan_destroy", "rpca_status_str", "rpca_gram", "rpca_eig",

@@ -169,7 +169,7 @@ def test_nonfinite_input_reports_error(rp):
 
 def test_invalid_arguments(rp):
     with pytest.raises(rp.RpcaError) as ei:
-        rp.Plan(100, 64)
+        rp.Plan(100, rp.MAX_T + 1)
     assert ei.value.status == rp.ERR_UNSUPPORTED
     with pytest.raises(rp.RpcaError):
         rp.Plan(100, 8, tol=0.0)
