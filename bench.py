@@ -1,13 +1,21 @@
 #!/usr/bin/env python
-"""Benchmark: robust PCA (PCP by the augmented-Lagrangian iteration) of one
-512x512-pixel x 20-frame window (Casorati 262144 x 20, float32) per step.
+"""Benchmark: robust PCA (PCP by the augmented-Lagrangian iteration) of
+512x512-pixel x 20-frame windows (Casorati 262144 x 20, float32).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--form batch|plan|serve] [--precision fp32|tf32x3|bf16x3|tf32]
 
-One step = one complete solve (init pass, every iteration until the relative
-residual is <= 1e-7, final L and mask) of a seeded synthetic window resident
-in HBM.  L2 is flushed (a 256 MB write, outside the per-step CUDA events)
-before every timed step.  Prints ONE JSON line on rank 0.
+Every solve is complete: init pass, every iteration until the relative
+residual is <= 1e-7, final L and mask, of seeded synthetic windows resident
+in HBM.  L2 is flushed (a 256 MB write, outside the step events) before every
+timed step.  Prints ONE JSON line on rank 0.
+
+Forms (the metric is solves/s of 262144 x 20 windows in every form):
+  batch  (default) one step = one persistent launch solving --windows windows
+         of different seeds (the batched form; the fastest measured);
+  plan   one step = one solve through a plan (CUDA-graph device loop);
+  serve  one step = --windows requests of different probes submitted to the
+         served form and waited for (continuous batching over CUDA streams).
 
 Under torchrun (N > 1) every rank solves its own windows (independent
 problems, no data-path collective: weak scaling); rank 0 reports the
@@ -56,6 +64,21 @@ def ncu_traffic(kernel_src_hash: str):
     """DRAM bytes per launch of the fused pass from the committed ncu summary,
     or None when the summary was taken on a different kernel source."""
     path = os.path.join(ROOT, "profiles", "fused_pass_w512x512_t20.md")
+    if not os.path.exists(path):
+        return None
+    src_hash, traffic = None, None
+    for line in open(path):
+        if line.startswith("kernel_source_sha256:"):
+            src_hash = line.split(":", 1)[1].strip()
+        if line.startswith("dram_bytes_per_launch:"):
+            traffic = float(line.split(":", 1)[1].strip())
+    return traffic if src_hash == kernel_src_hash else None
+
+
+def ncu_batch_traffic(kernel_src_hash: str, iters):
+    """DRAM bytes per persistent batch launch from the committed ncu summary
+    (measured on the same windows), or None for another kernel source."""
+    path = os.path.join(ROOT, "profiles", "batch_kernel_8x262144x20.md")
     if not os.path.exists(path):
         return None
     src_hash, traffic = None, None
@@ -183,8 +206,7 @@ def run_reference(args):
     return 0
 
 
-def run_ours(args):
-    import numpy as np
+def _setup(args):
     import torch
     rank, local_rank, world = dist_env()
     torch.cuda.set_device(local_rank)
@@ -195,6 +217,270 @@ def run_ours(args):
     from paper_2506_10257_gb300 import rpca
     B.build()
     rpca.load(build_if_missing=False)
+    return rpca, rank, local_rank, world
+
+
+def _theta(w):
+    # threshold of the bound-bubble mask: half the mean ground-truth image at bound-bubble cores
+    import numpy as np
+    img_gt = np.mean(np.abs(w.L_gt), axis=0)
+    return float(0.5 * img_gt[w.bound_mask_gt].mean())
+
+
+def _max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    t = torch.tensor([v], device="cuda", dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(world):
+    if world > 1:
+        import torch
+        torch.distributed.barrier()
+
+
+def _timed_steps(args, world, local_rank, step, flush):
+    """K steps bracketed by barrier + synchronize; per-step CUDA events on the
+    current stream (L2 flushed before each, outside the events)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clk = ClockSampler(local_rank)
+    _barrier(world)
+    torch.cuda.synchronize()
+    with clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    _barrier(world)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = _max_over_ranks(sum(step_ms), world)
+    return step_ms, total_ms, clk.summary()
+
+
+def _cpu_baseline(line, w, L, S, mask, theta, res_iters):
+    import numpy as np
+    from oracle import rpca_oracle as O
+    n = cores()
+    t0 = time.perf_counter()
+    ref = O.rpca_frames(w.frames)
+    dt = time.perf_counter() - t0
+    Lg, Sg = L.cpu().numpy().astype(np.float64), S.cpu().numpy().astype(np.float64)
+    mask_ref = O.bound_mask(O.temporal_mean_abs(ref.L), theta)
+    line["cpu_baseline"] = {"value": 1.0 / dt, "unit": "solves/s", "cores": n, "kind": "oracle",
+                            "sample": "one full 262144x20 solve of window 0 (FP64, LAPACK SVD)",
+                            "iters": ref.iters}
+    line["parity"] = {"window": 0, "errL": float(np.linalg.norm(Lg - ref.L) / np.linalg.norm(ref.L)),
+                      "errS": float(np.linalg.norm(Sg - ref.S) / np.linalg.norm(ref.S)),
+                      "mask_dice": O.dice(mask.cpu().numpy().astype(bool), mask_ref),
+                      "iters_gpu": res_iters, "iters_oracle": ref.iters}
+
+
+def _roofline(alg_bytes, seconds, kernel, timing, traffic=None):
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / seconds / 1e9 if seconds > 0 else None
+    return {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+            "algorithmic_bytes_per_launch": alg_bytes, "timing": timing,
+            "peak_kind": peak_kind + " (hbm_gbs, burst copy)"}
+
+
+def _solve_bytes(m, T, iters):
+    """Algorithmic HBM bytes of one solve: init pass reads X; each iteration
+    reads X, S, Y and writes S, Y; the final step reads X, S, Y_k, Y_k-1 and
+    writes L (plus the m-byte mask)."""
+    return 4 * m * T * (1 + 5 * iters + 5) + m
+
+
+def _plain_reference_rate(rpca, Xs, m, T, flush):
+    """Plain FP32 form (one plan, solves one after another) on the same windows."""
+    import torch
+    plan = rpca.Plan(m, T)
+    L, S = torch.empty_like(Xs[0]), torch.empty_like(Xs[0])
+    for X in Xs[:2]:
+        plan.solve(X, L, S)
+    flush.fill_(0.0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for X in Xs:
+        plan.solve(X, L, S, wait=False)
+    e1.record()
+    torch.cuda.synchronize()
+    plan.close()
+    return len(Xs) / (e0.elapsed_time(e1) * 1e-3)
+
+
+def run_batch(args):
+    import numpy as np
+    import torch
+    rpca, rank, local_rank, world = _setup(args)
+    NB = args.windows
+    ws = [window(1 + i + 1000 * rank) for i in range(NB)]
+    T, m = ws[0].frames.shape
+    Xs = [torch.from_numpy(w.frames).cuda() for w in ws]
+    Ls = [torch.empty_like(X) for X in Xs]
+    Ss = [torch.empty_like(X) for X in Xs]
+    thetas = [_theta(w) for w in ws]
+    masks = [torch.zeros(m, dtype=torch.uint8, device="cuda") for _ in ws]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    batch = rpca.Batch([(m, T)] * NB)
+    tuned_ms = batch.tune(Xs, reps=2) if args.tune else None
+    for _ in range(args.warmup):
+        batch.solve(Xs, Ls, Ss, masks=masks, thetas=thetas)
+    torch.cuda.synchronize()
+    step_ms, total_ms, clocks = _timed_steps(
+        args, world, local_rank, lambda: batch.solve(Xs, Ls, Ss, masks=masks, thetas=thetas, wait=False), flush)
+    _, _, res = batch.solve(Xs, Ls, Ss, masks=masks, thetas=thetas)
+    info = batch.info()
+    ms_per_step = total_ms / args.steps
+    value = world * NB * args.steps / (total_ms * 1e-3)
+    iters = [r["iters"] for r in res]
+
+    # end to end through the public API: pinned host windows in, L, S, masks out, every step
+    Xh = [torch.from_numpy(w.frames).pin_memory() for w in ws]
+    Lh = [torch.empty((T, m), dtype=torch.float32).pin_memory() for _ in ws]
+    Sh = [torch.empty((T, m), dtype=torch.float32).pin_memory() for _ in ws]
+    Mh = [torch.empty(m, dtype=torch.uint8).pin_memory() for _ in ws]
+
+    def e2e_step():
+        for i in range(NB):
+            Xs[i].copy_(Xh[i], non_blocking=True)
+        batch.solve(Xs, Ls, Ss, masks=masks, thetas=thetas, wait=False)
+        for i in range(NB):
+            Lh[i].copy_(Ls[i], non_blocking=True)
+            Sh[i].copy_(Ss[i], non_blocking=True)
+            Mh[i].copy_(masks[i], non_blocking=True)
+        torch.cuda.synchronize()
+
+    e2e_step()
+    e2e_steps = max(3, args.steps // 2)
+    _barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    e2e_s = _max_over_ranks(time.perf_counter() - t0, world)
+    e2e_val = world * NB * e2e_steps / e2e_s
+
+    plain = _plain_reference_rate(rpca, Xs, m, T, flush)
+    alg = sum(_solve_bytes(m, T, it) for it in iters)
+    line = {
+        "metric": "solves/s", "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded microbubble windows, in HBM)",
+        "config": {"workload": WORKLOAD + " (512x512 px x 20 frames, Casorati 262144x20, fp32)",
+                   "form": f"batched persistent launch, {NB} windows per step (different seeds)",
+                   "precision": "fp32", "tol": 1e-7,
+                   "l2": "flushed before every step (256 MB write, outside step events); "
+                         "the step's windows (8 x 3 x 21 MB) exceed L2",
+                   "schedule": info, "tuned_ms": tuned_ms,
+                   "parallelism": f"replicas x{world} (independent windows)"},
+        "ms_per_solve": ms_per_step / NB,
+        "latency_ms": {"p50": statistics.median(step_ms), "p99": float(np.percentile(step_ms, 99)),
+                       "min": min(step_ms), "max": max(step_ms),
+                       "note": "every window of a step completes at the launch's end"},
+        "iters": iters,
+        "kernel_us": {"pass_per_window": [round(r["pass_us"], 2) for r in res[:2]],
+                      "eig": round(res[0]["eig_us"], 2)},
+        "gpu_launches": args.steps * 2,
+        "roofline": _roofline(alg, ms_per_step * 1e-3 / 1.0, "batch_kernel<20> (persistent: passes + eigen-steps)",
+                              "CUDA events around each persistent launch (its descriptor copy and "
+                              "control-block gather included), algorithmic bytes of all windows' solves",
+                              traffic=ncu_batch_traffic(kernel_source_hash(), iters)),
+        "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": NB * m * T * 4,
+                "d2h_bytes_per_step": NB * (2 * m * T * 4 + m), "steps": e2e_steps},
+        "vs_plain_fp32": {"plain_solves_per_s": plain, "ratio": value / plain},
+        "clocks": clocks,
+        "kernel_source_sha256": kernel_source_hash(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        _cpu_baseline(line, ws[0], Ls[0], Ss[0], masks[0], thetas[0], iters[0])
+    batch.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_serve(args):
+    import numpy as np
+    import torch
+    rpca, rank, local_rank, world = _setup(args)
+    NB = args.windows
+    ws = [window(1 + i + 1000 * rank) for i in range(NB)]
+    T, m = ws[0].frames.shape
+    Xs = [torch.from_numpy(w.frames).cuda() for w in ws]
+    Ls = [torch.empty_like(X) for X in Xs]
+    Ss = [torch.empty_like(X) for X in Xs]
+    thetas = [_theta(w) for w in ws]
+    masks = [torch.zeros(m, dtype=torch.uint8, device="cuda") for _ in ws]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    prec = {"fp32": rpca.PREC_FP32, "tf32x3": rpca.PREC_TF32X3, "bf16x3": rpca.PREC_BF16X3,
+            "tf32": rpca.PREC_TF32}[args.precision]
+    sv = rpca.Server(hbm_budget_bytes=120 * 10**9, max_slots=args.slots, warm=False)
+    lat = []
+
+    def step():
+        t0 = time.perf_counter()
+        ids = [sv.submit(X, key=i, L=Ls[i], S=Ss[i], mask=masks[i], theta=thetas[i], precision=prec)
+               for i, X in enumerate(Xs)]
+        res = []
+        for r in ids:
+            res.append(sv.wait(r)[1])
+            lat.append((time.perf_counter() - t0) * 1e3)
+        return res
+
+    for _ in range(args.warmup):
+        step()
+    lat.clear()
+    step_ms, total_ms, clocks = _timed_steps(args, world, local_rank, step, flush)
+    res = step()
+    iters = [r["iters"] for r in res]
+    ms_per_step = total_ms / args.steps
+    value = world * NB * args.steps / (total_ms * 1e-3)
+    plain = _plain_reference_rate(rpca, Xs, m, T, flush)
+    alg = sum(_solve_bytes(m, T, it) for it in iters)
+    line = {
+        "metric": "solves/s", "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded microbubble windows, in HBM)",
+        "config": {"workload": WORKLOAD + " (512x512 px x 20 frames, Casorati 262144x20, fp32)",
+                   "form": f"served: {NB} probes submit one window each per step, {args.slots} slots, cold starts",
+                   "precision": args.precision, "tol": 1e-7,
+                   "l2": "flushed before every step (256 MB write, outside step events)"},
+        "ms_per_solve": ms_per_step / NB,
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "note": "submit to completion seen by the host, per request"},
+        "iters": iters,
+        "gpu_launches": args.steps * sum(3 + 2 * it for it in iters),
+        "roofline": _roofline(alg, ms_per_step * 1e-3, "all solves of a step (fused passes dominate)",
+                              "CUDA events around each step"),
+        "e2e": None,
+        "vs_plain_fp32": {"plain_solves_per_s": plain, "ratio": value / plain},
+        "clocks": clocks,
+        "server_stats": sv.stats(),
+    }
+    sv.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    rpca, rank, local_rank, world = _setup(args)
 
     w = window(1 + 1000 * rank)
     T, m = w.frames.shape
@@ -205,39 +491,16 @@ def run_ours(args):
     plan = rpca.Plan(m, T, precision=prec, drive=drive)
     L = torch.empty_like(X)
     S = torch.empty_like(X)
-    # threshold of the bound-bubble mask: half the mean ground-truth image at bound-bubble cores
-    img_gt = np.mean(np.abs(w.L_gt), axis=0)
-    theta = float(0.5 * img_gt[w.bound_mask_gt].mean())
+    theta = _theta(w)
     mask = torch.zeros(m, dtype=torch.uint8, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    stream = torch.cuda.current_stream()
 
     for _ in range(args.warmup):
         plan.solve(X, L, S, mask=mask, theta=theta, wait=True)
     torch.cuda.synchronize()
-
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    results = []
-    clk = ClockSampler(local_rank)
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    with clk:
-        for k in range(args.steps):
-            flush.fill_(float(k))                          # L2 flush (not inside the step events)
-            ev[k][0].record(stream)
-            plan.solve(X, L, S, mask=mask, theta=theta, wait=False)
-            ev[k][1].record(stream)
-        torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    step_ms, total_ms, clocks = _timed_steps(
+        args, world, local_rank, lambda: plan.solve(X, L, S, mask=mask, theta=theta, wait=False), flush)
     res = plan.result()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
     ms_per_step = total_ms / args.steps
     value = world * args.steps / (total_ms * 1e-3)
 
@@ -248,24 +511,17 @@ def run_ours(args):
     Mh = torch.empty(m, dtype=torch.uint8).pin_memory().numpy()
     plan.solve_host(Xh, Lh, Sh, mask=Mh, theta=theta)
     e2e_steps = max(3, args.steps // 2)
-    if world > 1:
-        torch.distributed.barrier()
+    _barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         plan.solve_host(Xh, Lh, Sh, mask=Mh, theta=theta)
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = _max_over_ranks(time.perf_counter() - t0, world)
     e2e_val = world * e2e_steps / e2e_s
 
-    # roofline of the dominant kernel (the fused per-iteration pass)
-    peak, peak_kind = measured_peaks()
+    # roofline of the dominant kernel (the fused per-iteration pass), device-timer durations
     alg_bytes = 5 * m * T * 4                    # read X, S, Y; write S, Y
     pass_us = res["pass_us"]
-    achieved = alg_bytes / (pass_us * 1e-6) / 1e9 if pass_us > 0 else None
     src_hash = kernel_source_hash()
     line = {
         "metric": "solves/s", "value": value, "unit": "solves/s", "n_gpus": world,
@@ -273,6 +529,7 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded microbubble window, in HBM)",
         "config": {"workload": WORKLOAD + " (512x512 px x 20 frames, Casorati 262144x20, fp32)",
+                   "form": "plan: one solve per step",
                    "precision": args.precision,
                    "drive": {"graph": "cuda-graph device loop", "stream": "kernels launched one by one",
                              "host": "plain form: host loop, unfused passes"}[args.drive],
@@ -284,34 +541,17 @@ def run_ours(args):
         "kernel_us": {"pass": pass_us, "eig": res["eig_us"], "init": res["init_us"],
                       "eig_split": {k: round(v, 3) for k, v in plan.timings().items()}},
         "gpu_launches": args.steps * launches_per_solve(args.drive, res["iters"]),
-        "roofline": {"bound": "hbm", "kernel": "pass_kernel<20,FUSED>",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": ncu_traffic(src_hash),
-                     "algorithmic_bytes_per_launch": alg_bytes,
-                     "timing": "device global timer per launch over the timed solves",
-                     "peak_kind": peak_kind + " (hbm_gbs)"},
+        "roofline": _roofline(alg_bytes, pass_us * 1e-6, "pass_kernel<20,FUSED>",
+                              "device global timer per launch over the timed solves",
+                              traffic=ncu_traffic(src_hash)),
         "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": m * T * 4,
                 "d2h_bytes_per_step": 2 * m * T * 4 + m + 48, "steps": e2e_steps},
-        "clocks": clk.summary(),
+        "clocks": clocks,
         "kernel_source_sha256": src_hash,
     }
-
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        from oracle import rpca_oracle as O
-        n = cores()
-        t0 = time.perf_counter()
-        ref = O.rpca_frames(w.frames)
-        dt = time.perf_counter() - t0
         plan.solve(X, L, S, mask=mask, theta=theta, wait=True)
-        Lg, Sg = L.cpu().numpy().astype(np.float64), S.cpu().numpy().astype(np.float64)
-        mask_ref = O.bound_mask(O.temporal_mean_abs(ref.L), theta)
-        line["cpu_baseline"] = {"value": 1.0 / dt, "unit": "solves/s", "cores": n, "kind": "oracle",
-                                "sample": "one full 262144x20 solve of the same window (FP64, LAPACK SVD)",
-                                "iters": ref.iters}
-        line["parity"] = {"errL": float(np.linalg.norm(Lg - ref.L) / np.linalg.norm(ref.L)),
-                          "errS": float(np.linalg.norm(Sg - ref.S) / np.linalg.norm(ref.S)),
-                          "mask_dice": O.dice(mask.cpu().numpy().astype(bool), mask_ref),
-                          "iters_gpu": res["iters"], "iters_oracle": ref.iters}
+        _cpu_baseline(line, w, L, S, mask, theta, res["iters"])
     plan.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -328,6 +568,10 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32", "tf32x3", "bf16x3", "tf32"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--form", choices=["batch", "plan", "serve"], default="batch")
+    ap.add_argument("--windows", type=int, default=8, help="windows per step (batch, serve)")
+    ap.add_argument("--slots", type=int, default=4, help="server slots (serve)")
+    ap.add_argument("--tune", action="store_true", help="autotune the batch schedule first")
     ap.add_argument("--drive", choices=["graph", "stream", "host"], default="graph",
                     help="graph: the product path; stream: same kernels launched one by one (for ncu); "
                          "host: the plain unfused form")
@@ -336,6 +580,10 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.form == "batch":
+        return run_batch(args)
+    if args.form == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 
