@@ -76,18 +76,23 @@ def ncu_traffic(kernel_src_hash: str):
 
 
 def ncu_batch_traffic(kernel_src_hash: str, iters):
-    """DRAM bytes per persistent batch launch from the committed ncu summary
-    (measured on the same windows), or None for another kernel source."""
-    path = os.path.join(ROOT, "profiles", "batch_kernel_8x262144x20.md")
+    """DRAM bytes of one persistent batch launch, from the committed ncu
+    capture of the same kernel on 4 windows of this workload: its bytes per
+    window solve (32 iterations) scaled to these windows by their iteration
+    counts (traffic grows with the iterations run).  None for another kernel
+    source."""
+    path = os.path.join(ROOT, "profiles", "batch_kernel_4x262144x20.md")
     if not os.path.exists(path):
         return None
-    src_hash, traffic = None, None
+    src_hash, per_window = None, None
     for line in open(path):
         if line.startswith("kernel_source_sha256:"):
             src_hash = line.split(":", 1)[1].strip()
-        if line.startswith("dram_bytes_per_launch:"):
-            traffic = float(line.split(":", 1)[1].strip())
-    return traffic if src_hash == kernel_src_hash else None
+        if line.startswith("dram_bytes_per_window_solve:"):
+            per_window = float(line.split(":", 1)[1].strip())
+    if src_hash != kernel_src_hash or per_window is None:
+        return None
+    return sum(per_window * (1 + 5 * it + 5) / (1 + 5 * 32 + 5) for it in iters)
 
 
 def kernel_source_hash() -> str:
