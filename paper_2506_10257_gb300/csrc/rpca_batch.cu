@@ -316,6 +316,7 @@ rpca_status rpca_batch_create(const rpca_params* params, int32_t n, rpca_batch_t
     if (params[i].precision != RPCA_PREC_FP32) return RPCA_ERR_UNSUPPORTED;
     if (params[i].T > kMaxT) return RPCA_ERR_UNSUPPORTED;
     if (params[i].warm_start) return RPCA_ERR_UNSUPPORTED;  // windows of a batch start cold
+    if (params[i].dtype != RPCA_R32) return RPCA_ERR_UNSUPPORTED;
   }
   rpca_batch_s* b = new rpca_batch_s();
   b->n = n;

@@ -117,7 +117,7 @@ int device_sms() {
 }
 
 // Grid: two 256-thread CTAs per SM (register bound), never more than the tiles.
-Layout make_layout(int64_t m, int T, int sms) {
+Layout make_layout(int64_t m, int T, int sms, bool wide) {
   Layout L;
   const int64_t ntiles = (m + kTile - 1) / kTile;
   int64_t grid = std::min<int64_t>(ntiles, (int64_t)std::max(sms, 1) * 2);
@@ -125,7 +125,7 @@ Layout make_layout(int64_t m, int T, int sms) {
   L.grid = (int)std::max<int64_t>(grid, 1);
   L.ws_grid = (int)std::max<int64_t>(std::min<int64_t>((m + 127) / 128, std::max(sms, 1)), 1);
   L.wide_grid = (int)std::max<int64_t>(std::min<int64_t>((m + 31) / 32, std::max(sms, 1)), 1);
-  const int maxgrid = std::max({L.grid, L.ws_grid, T > kMaxT ? L.wide_grid : 1});
+  const int maxgrid = std::max({L.grid, L.ws_grid, wide ? L.wide_grid : 1});
   L.ngroups = (maxgrid + kGroup - 1) / kGroup;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -137,14 +137,14 @@ Layout make_layout(int64_t m, int T, int sms) {
   L.eig = take(sizeof(EigState));
   L.red = take(sizeof(RedState));
   L.job = take(sizeof(Job));
-  const size_t tw = T > kMaxT ? (size_t)T * T : 1;   // wide-path Gram, Wbar, V
+  const size_t tw = wide ? (size_t)T * T : 1;   // wide-path Gram, Wbar, V
   L.gw = take(sizeof(float) * tw);
   L.ww = take(sizeof(float) * tw);
   L.vw = take(sizeof(float) * tw);
   L.evw = take(sizeof(double) * (size_t)T);
   // rotation log of the wide eigen-step: every round of kWideLogSweeps sweeps
-  const size_t nrounds = T > kMaxT ? (size_t)kWideLogSweeps * (size_t)(T + (T & 1)) : 1;
-  const size_t npairs = T > kMaxT ? (size_t)(T + (T & 1)) / 2 : 1;
+  const size_t nrounds = wide ? (size_t)kWideLogSweeps * (size_t)(T + (T & 1)) : 1;
+  const size_t npairs = wide ? (size_t)(T + (T & 1)) / 2 : 1;
   L.rlog = take(sizeof(float2) * nrounds * npairs);
   L.rrnd = take(sizeof(int) * nrounds);
   L.gram_part = take(sizeof(float) * (size_t)maxgrid * T * T);
@@ -156,6 +156,12 @@ Layout make_layout(int64_t m, int T, int sms) {
   return L;
 }
 
+// Real columns of the window's matrix: complex windows run as their
+// interleaved real embedding with 2 x T columns.
+int real_cols(const rpca_params* p) { return p->dtype == RPCA_C64 ? 2 * p->T : p->T; }
+// Complex windows and windows of more than kMaxT frames run the tiled path.
+bool uses_wide(const rpca_params* p) { return p->dtype == RPCA_C64 || p->T > kMaxT; }
+
 rpca_status validate(const rpca_params* p) {
   if (!p) return RPCA_ERR_ARG;
   if (p->m < 1 || p->T < 1) return RPCA_ERR_ARG;
@@ -166,7 +172,8 @@ rpca_status validate(const rpca_params* p) {
     return RPCA_ERR_ARG;
   if (p->drive != RPCA_DRIVE_GRAPH && p->drive != RPCA_DRIVE_HOST && p->drive != RPCA_DRIVE_STREAM)
     return RPCA_ERR_ARG;
-  if (p->dtype != RPCA_R32) return RPCA_ERR_UNSUPPORTED;
+  if (p->dtype != RPCA_R32 && p->dtype != RPCA_C64) return RPCA_ERR_ARG;
+  if (p->dtype == RPCA_C64 && (2 * p->T > kMaxTW || p->precision != RPCA_PREC_FP32)) return RPCA_ERR_UNSUPPORTED;
   if (p->precision < RPCA_PREC_FP32 || p->precision > RPCA_PREC_TF32) return RPCA_ERR_ARG;
   if (p->precision != RPCA_PREC_FP32 && p->drive == RPCA_DRIVE_HOST) return RPCA_ERR_UNSUPPORTED;
   if (p->precision != RPCA_PREC_FP32 && p->T > kMaxT) return RPCA_ERR_UNSUPPORTED;  // wide path is FP32
@@ -345,11 +352,11 @@ static rpca_status build_graph(rpca_plan_s* pl) {
 
 namespace rpca {
 
-void result_from_ctrl(double lambda, const Ctrl& c, rpca_result* out) {
+void result_from_ctrl(double lambda, const Ctrl& c, rpca_result* out, int cplx) {
   memset(out, 0, sizeof(*out));
   out->status = c.status;
   out->iters = c.k;
-  out->rank = c.rank;
+  out->rank = cplx ? c.rank / 2 : c.rank;
   out->sweeps = c.total_sweeps;
   out->resid = c.resid;
   out->mu = c.mu_cur;
@@ -368,7 +375,8 @@ rpca_status plan_view(rpca_plan_t pl, PlanView* v) {
   if (!pl || !v) return RPCA_ERR_ARG;
   v->bufs = pl->bufs;
   v->m = pl->p.m;
-  v->T = pl->p.T;
+  v->T = real_cols(&pl->p);
+  v->cplx = pl->p.dtype == RPCA_C64;
   v->max_grid = std::max(pl->lay.grid, pl->lay.ws_grid);
   v->lambda = pl->lambda;
   v->y1 = (float*)(pl->ws + pl->lay.ybuf);
@@ -378,7 +386,7 @@ rpca_status plan_view(rpca_plan_t pl, PlanView* v) {
 }  // namespace rpca
 
 static void fill_result(const rpca_plan_s* pl, const Ctrl& c, rpca_result* out) {
-  result_from_ctrl(pl->lambda, c, out);
+  result_from_ctrl(pl->lambda, c, out, pl->p.dtype == RPCA_C64);
 }
 
 extern "C" {
@@ -407,7 +415,7 @@ rpca_status rpca_workspace_size(const rpca_params* p, size_t* bytes) {
   if (!bytes) return RPCA_ERR_ARG;
   const int sms = device_sms();
   if (sms <= 0) return RPCA_ERR_CUDA;
-  *bytes = make_layout(p->m, p->T, sms).total;
+  *bytes = make_layout(p->m, real_cols(p), sms, uses_wide(p)).total;
   return RPCA_OK;
 }
 
@@ -420,9 +428,11 @@ rpca_status rpca_plan_create(const rpca_params* p, void* workspace, size_t works
   if (sms <= 0) return RPCA_ERR_CUDA;
   rpca_plan_s* pl = new rpca_plan_s();
   pl->p = *p;
-  pl->wide = p->T > kMaxT;
+  const bool cplx = p->dtype == RPCA_C64;
+  const int Tr = real_cols(p);
+  pl->wide = uses_wide(p);
   if (pl->wide) {
-    if (!wide_kernels(p->T, &pl->wk)) {
+    if (!wide_kernels(Tr, cplx, &pl->wk)) {
       delete pl;
       return RPCA_ERR_UNSUPPORTED;
     }
@@ -446,7 +456,7 @@ rpca_status rpca_plan_create(const rpca_params* p, void* workspace, size_t works
       return cuda_status(ea);
     }
   }
-  pl->lay = make_layout(p->m, p->T, sms);
+  pl->lay = make_layout(p->m, Tr, sms, pl->wide);
   if (!pl->wide && pl->ks.eig_fast_smem > 48 * 1024) {
     cudaError_t ea = cudaFuncSetAttribute(pl->ks.eig_fast, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)pl->ks.eig_fast_smem);
@@ -487,7 +497,9 @@ rpca_status rpca_plan_create(const rpca_params* p, void* workspace, size_t works
   b.rot_log = (float2*)(pl->ws + pl->lay.rlog);
   b.rot_rnd = (int*)(pl->ws + pl->lay.rrnd);
   b.m = p->m;
-  b.T = p->T;
+  b.T = Tr;
+  b.cplx = cplx ? 1 : 0;
+  b.wide = pl->wide ? 1 : 0;
   b.grid = pl->lay.grid;
   b.ngroups = pl->lay.ngroups;
   b.finalize = 0;
@@ -667,7 +679,7 @@ rpca_status rpca_plan_result(rpca_plan_t pl, rpca_result* out) {
 rpca_status rpca_solve_host(rpca_plan_t pl, const void* X_host, void* L_host, void* S_host, uint8_t* mask_host,
                             float theta, void* stream, rpca_result* out) {
   if (!pl || !X_host || !L_host || !S_host) return RPCA_ERR_ARG;
-  const size_t bytes = sizeof(float) * (size_t)pl->p.m * pl->p.T;
+  const size_t bytes = sizeof(float) * (size_t)pl->p.m * real_cols(&pl->p);
   if (!pl->stage_x) {
     CK(cudaMalloc((void**)&pl->stage_x, bytes));
     CK(cudaMalloc((void**)&pl->stage_l, bytes));

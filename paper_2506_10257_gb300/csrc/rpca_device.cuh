@@ -139,6 +139,8 @@ struct Bufs {
   int T;
   int grid;
   int ngroups;
+  int cplx;            // complex window: T = 2 x frames, columns (2t, 2t + 1) = (Re, Im) of frame t
+  int wide;            // tiled path: the reduced Gram goes to Gw (T x T), else to red->G (kMaxT stride)
   int finalize;        // 1: the pass itself sums the group partials into red->G, e2, l1;
                        // 0: the next eigen-step does (saves a serial reduction level)
   // T > kMaxT ("wide" windows): the reduced Gram, Wbar and V live in these

@@ -13,6 +13,7 @@ struct PlanView {
   int max_grid;       // CTAs whose partials fit in the plan's workspace
   double lambda;      // resolved lambda
   float* y1;          // second dual buffer (workspace)
+  int cplx;           // complex window (T = 2 x frames)
 };
 
 // Kernels of the wide path (kMaxT < T <= kMaxTW), defined in rpca_wide.cu.
@@ -26,9 +27,9 @@ struct WideKernels {
   int eig_threads;
 };
 
-// Fills *out for T (false when T is not a wide frame count or a kernel
-// attribute cannot be set).
-bool wide_kernels(int T, WideKernels* out);
+// Fills *out for T real columns (complex windows: T = 2 x frames, cplx set);
+// false when T is not a wide column count or a kernel attribute cannot be set.
+bool wide_kernels(int T, bool cplx, WideKernels* out);
 
 // Fills *v from a plan; RPCA_ERR_ARG for a null plan.
 rpca_status plan_view(rpca_plan_t plan, PlanView* v);
@@ -43,7 +44,8 @@ rpca_status plan_solve_ex(rpca_plan_t plan, const void* X, void* L, void* S, uin
 // Device control block of the plan.
 Ctrl* plan_ctrl(rpca_plan_t plan);
 
-// rpca_result of a solve from its control block.
-void result_from_ctrl(double lambda, const Ctrl& c, rpca_result* out);
+// rpca_result of a solve from its control block (cplx: the rank counts each
+// complex singular value once, not twice as the real embedding does).
+void result_from_ctrl(double lambda, const Ctrl& c, rpca_result* out, int cplx = 0);
 
 }  // namespace rpca

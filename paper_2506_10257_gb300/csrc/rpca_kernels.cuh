@@ -209,7 +209,7 @@ static __device__ __noinline__ bool cross_cta_reduce(Bufs b, bool kGram, double*
   if (!sLast) return false;
   __threadfence();
   if (kGram) {
-    if (T > kMaxT) {
+    if (b.wide) {
       float* G = b.Gw;
       sum_rows<W>(b.group_part, 0, ngroups, TT, [&](int e, float v) { G[e] = v; });
     } else {
@@ -466,8 +466,9 @@ __device__ __forceinline__ void refresh_f32(Ctrl* c) {
 // mu_max = mu_max_factor * mu0 always follows the cold schedule.
 __device__ __forceinline__ void init_mu(Bufs b, double lmax) {
   Ctrl* c = b.ctrl;
+  const double frames = b.cplx ? 0.5 * (double)b.T : (double)b.T;  // n1 n2 counts complex entries once
   const double mu0 = (c->schedule == 0) ? c->mu0_scale / sqrt(lmax)
-                                        : ((double)b.m * (double)b.T) / (4.0 * c->normX1);
+                                        : ((double)b.m * frames) / (4.0 * c->normX1);
   double mu1 = mu0;
   if (c->mu_init > 0.0)
     mu1 = c->mu_init;
@@ -488,7 +489,7 @@ static __device__ void finalize_sums(Bufs b, double* sh) {
   const int T = b.T, TT = T * T;
   const int ng = b.red->ngroups_last;
   if (b.red->gram_last) {
-    if (T > kMaxT) {
+    if (b.wide) {
       float* G = b.Gw;
       sum_rows<4>(b.group_part, 0, ng, TT, [&](int e, float v) { G[e] = v; });
     } else {
@@ -799,6 +800,40 @@ static __device__ void final_body(Bufs b, int lc, int nc) {
   const float inv_mu = __ldcg(&ctrl->f_inv_mu);
   const float* Yk = (kc & 1) ? job.Y1 : job.Y0;
   const float* Ykm1 = (kc & 1) ? job.Y0 : job.Y1;
+  if (b.cplx) {
+    // complex window: (Re, Im) pairs, frame-major; the mask uses |L|
+    const int F = T / 2;
+    const float2* X2 = reinterpret_cast<const float2*>(job.X);
+    float2* S2 = reinterpret_cast<float2*>(job.S);
+    float2* L2 = reinterpret_cast<float2*>(job.L);
+    const float2* Yk2 = reinterpret_cast<const float2*>(Yk);
+    const float2* Ym2 = reinterpret_cast<const float2*>(Ykm1);
+    float2* So2 = reinterpret_cast<float2*>(job.Sout);
+    float2* Yo2 = reinterpret_cast<float2*>(job.Yout);
+    for (int64_t p = (int64_t)lc * blockDim.x + threadIdx.x; p < m; p += (int64_t)nc * blockDim.x) {
+      float acc = 0.f;
+      for (int t = 0; t < F; ++t) {
+        const int64_t i = t * m + p;
+        float2 l = make_float2(0.f, 0.f), yk = make_float2(0.f, 0.f);
+        if (kc == 0) {
+          if (warm) yk = Yk2[i];
+          S2[i] = make_float2(0.f, 0.f);
+        } else {
+          const float2 x = X2[i], s = S2[i];
+          yk = Yk2[i];
+          const float2 ym = (kc >= 2 || warm) ? Ym2[i] : make_float2(0.f, 0.f);
+          l.x = (x.x - s.x) - (yk.x * inv_mu - ym.x * inv_mu);
+          l.y = (x.y - s.y) - (yk.y * inv_mu - ym.y * inv_mu);
+        }
+        if (So2) So2[i] = S2[i];
+        if (Yo2) Yo2[i] = yk;
+        L2[i] = l;
+        acc += sqrtf(fmaf(l.x, l.x, l.y * l.y));
+      }
+      if (job.mask) job.mask[p] = (acc / (float)F >= job.theta) ? 1 : 0;
+    }
+    return;
+  }
   for (int64_t p = (int64_t)lc * blockDim.x + threadIdx.x; p < m; p += (int64_t)nc * blockDim.x) {
     float acc = 0.f;
     for (int t = 0; t < T; ++t) {

@@ -113,7 +113,7 @@ namespace {
 size_t probe_bytes(const rpca_params& p) {
   size_t ws = 0;
   if (rpca_workspace_size(&p, &ws) != RPCA_OK) return 0;
-  return ws + 2 * sizeof(float) * (size_t)p.m * (size_t)p.T;
+  return ws + 2 * sizeof(float) * (size_t)p.m * (size_t)p.T * (p.dtype == RPCA_C64 ? 2 : 1);
 }
 
 void free_probe(rpca_server_s* sv, Probe* pr) {
@@ -164,7 +164,7 @@ rpca_status ensure_probe(rpca_server_s* sv, Request* rq, Probe** out) {
   q.mu_init = 0.0;
   q.mu_prev_scale = 0.0;
   if (q.drive == RPCA_DRIVE_HOST) q.drive = RPCA_DRIVE_GRAPH;
-  const size_t mT = sizeof(float) * (size_t)q.m * (size_t)q.T;
+  const size_t mT = sizeof(float) * (size_t)q.m * (size_t)q.T * (q.dtype == RPCA_C64 ? 2 : 1);
   rpca_status st = rpca_plan_create(&q, nullptr, 0, &pr->plan);
   if (st == RPCA_OK) st = cuda_st(cudaMalloc((void**)&pr->S_state, mT));
   if (st == RPCA_OK) st = cuda_st(cudaMalloc((void**)&pr->Y_state, mT));
@@ -186,8 +186,8 @@ rpca_status ensure_probe(rpca_server_s* sv, Request* rq, Probe** out) {
 rpca_status start(rpca_server_s* sv, Request* rq, Probe* pr, int slot) {
   Slot& sl = sv->slots[slot];
   cudaStream_t s = sl.stream;
-  const int64_t m = rq->p.m;
   const int T = rq->p.T;
+  const int64_t m = rq->p.m * (rq->p.dtype == RPCA_C64 ? 2 : 1);  // floats per frame
   const size_t frame = sizeof(float) * (size_t)m;
   const bool warm = sv->warm && pr->have_prev && !(sv->cold_every > 0 && pr->windows % sv->cold_every == 0);
   cudaError_t e = cudaSuccess;
@@ -230,7 +230,7 @@ void finish(rpca_server_s* sv, Slot& sl, rpca_status err) {
   rpca::PlanView v;
   rpca::plan_view(pr->plan, &v);
   if (err == RPCA_OK) {
-    rpca::result_from_ctrl(v.lambda, *sl.ctrl_host, &rq->res);
+    rpca::result_from_ctrl(v.lambda, *sl.ctrl_host, &rq->res, v.cplx);
   } else {
     memset(&rq->res, 0, sizeof(rq->res));
     rq->res.status = err;

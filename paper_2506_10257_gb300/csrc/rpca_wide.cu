@@ -90,17 +90,24 @@ __device__ __forceinline__ void tile_times(float (&acc)[CW], float* sM, const fl
   }
 }
 
-template <int CW, int MODE>
+// CPLX: complex windows as their interleaved real embedding (column 2t = Re,
+// 2t + 1 = Im of frame t; T = 2 x frames).  The Hermitian Gram Z^H Z is the
+// real Gram of the 2m rows a = [Re z, Im z] and b = a P = [-Im z, Re z] (the
+// row of i z) per pixel, so the pass adds both rows of every pixel to the
+// Gram; the shrink of Eq. 5 acts on the magnitude of each complex entry.
+template <int CW, int MODE, bool CPLX>
 __global__ void __launch_bounds__(kWideThreads, 1) pass_wide_kernel(Bufs b) {
   using WS = WideShape<CW>;
   constexpr int TP = WS::TP;
+  constexpr int UP = CPLX ? TP : WS::UP;       // U row stride (complex: 64 rows over the S, Y tiles)
+  constexpr int NROWS = CPLX ? 2 * kWP : kWP;  // Gram rows per tile
   constexpr bool kGram = (MODE != PM_UPDATE);
   extern __shared__ __align__(16) float wide_smem[];
   float* sX = wide_smem;               // [TP][kWP]
   float* sS = sX + TP * kWP;           // [TP][kWP]
   float* sY = sS + TP * kWP;           // [TP][kWP]
   float* sM = sY + TP * kWP;           // [kWKC][TP]
-  float* sU = sS;                      // [kWP][UP], over the S and Y tiles once they are used
+  float* sU = sS;                      // [NROWS][UP], over the S and Y tiles once they are used
   __shared__ double sRed[2][kWideThreads / 32];
   __shared__ double sScal[2 * kMaxGroups];
   __shared__ int sLast;
@@ -139,24 +146,49 @@ __global__ void __launch_bounds__(kWideThreads, 1) pass_wide_kernel(Bufs b) {
     const bool valid = p < m;
     __syncthreads();  // the previous tile's U is consumed
     // ---- 1. stage the tile (frame-major) ----
-    for (int t = w; t < TP; t += 8) {
-      const bool in = valid && t < T;
-      const float x = in ? job.X[(int64_t)t * m + p] : 0.f;
-      sX[t * kWP + lane] = x;
-      if (MODE == PM_INIT) {
-        e2 = fmaf(x, x, e2);
-        l1 += fabsf(x);
-      } else {
-        sS[t * kWP + lane] = (in && !first) ? job.S[(int64_t)t * m + p] : 0.f;
-        sY[t * kWP + lane] = (in && !first) ? Yin[(int64_t)t * m + p] : 0.f;
+    if constexpr (CPLX) {
+      const float2* X2 = reinterpret_cast<const float2*>(job.X);
+      const float2* S2 = reinterpret_cast<const float2*>(job.S);
+      const float2* Y2 = reinterpret_cast<const float2*>(Yin);
+      for (int f = w; f < TP / 2; f += 8) {
+        const bool in = valid && 2 * f < T;
+        const float2 x = in ? X2[(int64_t)f * m + p] : make_float2(0.f, 0.f);
+        sX[(2 * f) * kWP + lane] = x.x;
+        sX[(2 * f + 1) * kWP + lane] = x.y;
+        if (MODE == PM_INIT) {
+          const float a2 = fmaf(x.x, x.x, x.y * x.y);
+          e2 += a2;
+          l1 += sqrtf(a2);
+        } else {
+          const float2 sv = (in && !first) ? S2[(int64_t)f * m + p] : make_float2(0.f, 0.f);
+          const float2 yv = (in && !first) ? Y2[(int64_t)f * m + p] : make_float2(0.f, 0.f);
+          sS[(2 * f) * kWP + lane] = sv.x;
+          sS[(2 * f + 1) * kWP + lane] = sv.y;
+          sY[(2 * f) * kWP + lane] = yv.x;
+          sY[(2 * f + 1) * kWP + lane] = yv.y;
+        }
+      }
+    } else {
+      for (int t = w; t < TP; t += 8) {
+        const bool in = valid && t < T;
+        const float x = in ? job.X[(int64_t)t * m + p] : 0.f;
+        sX[t * kWP + lane] = x;
+        if (MODE == PM_INIT) {
+          e2 = fmaf(x, x, e2);
+          l1 += fabsf(x);
+        } else {
+          sS[t * kWP + lane] = (in && !first) ? job.S[(int64_t)t * m + p] : 0.f;
+          sY[t * kWP + lane] = (in && !first) ? Yin[(int64_t)t * m + p] : 0.f;
+        }
       }
     }
     __syncthreads();
     if (MODE == PM_INIT) {
-      // U = X (standard basis), pixel-major
+      // U = X (standard basis), pixel-major; complex: also the rows of i X
       for (int i = tid; i < TP * kWP; i += kWideThreads) {
         const int t = i / kWP, pp = i % kWP;
-        sU[pp * WS::UP + t] = sX[t * kWP + pp];
+        sU[pp * UP + t] = sX[t * kWP + pp];
+        if (CPLX) sU[(kWP + pp) * UP + t] = (t & 1) ? sX[(t - 1) * kWP + pp] : -sX[(t + 1) * kWP + pp];
       }
     } else {
       if (MODE != PM_GRAM) {
@@ -167,23 +199,51 @@ __global__ void __launch_bounds__(kWideThreads, 1) pass_wide_kernel(Bufs b) {
         });
         __syncthreads();  // every warp has read the whole tile before Z' overwrites X
         // ---- 3. Eq. 5-6 for (lane's pixel, warp's frames) ----
+        if constexpr (CPLX) {
+          float2* S2 = reinterpret_cast<float2*>(job.S);
+          float2* Yo2 = reinterpret_cast<float2*>(Yout);
 #pragma unroll
-        for (int j = 0; j < CW; ++j) {
-          const int t = w * CW + j;
-          if (t < T) {
-            const float x = sX[t * kWP + lane], s = sS[t * kWP + lane], y = sY[t * kWP + lane];
-            const float r = s + q[j];
-            const float c = fminf(fmaxf(r, -gamma), gamma);
-            const float sn = r - c;
-            const float yn = f_mu * c;
-            const float e = c - y * inv_mu;
-            e2 = fmaf(e, e, e2);
-            if (valid) {
-              job.S[(int64_t)t * m + p] = sn;
-              Yout[(int64_t)t * m + p] = yn;
+          for (int j = 0; j < CW; j += 2) {
+            const int t = w * CW + j;   // even: (Re, Im) of frame t / 2
+            if (t < T) {
+              const float xr = sX[t * kWP + lane], xi = sX[(t + 1) * kWP + lane];
+              const float sr = sS[t * kWP + lane], si = sS[(t + 1) * kWP + lane];
+              const float yr = sY[t * kWP + lane], yi = sY[(t + 1) * kWP + lane];
+              const float rr = sr + q[j], ri = si + q[j + 1];
+              const float mag = sqrtf(fmaf(rr, rr, ri * ri));
+              const float f = (mag > gamma) ? gamma / mag : 1.f;   // clip to the disc of radius gamma
+              const float cr = rr * f, ci = ri * f;
+              const float snr = rr - cr, sni = ri - ci;           // Eq. 5 (magnitude shrink)
+              const float ynr = f_mu * cr, yni = f_mu * ci;       // Eq. 6
+              const float er = cr - yr * inv_mu, ei = ci - yi * inv_mu;
+              e2 = fmaf(er, er, fmaf(ei, ei, e2));
+              if (valid) {
+                S2[(int64_t)(t >> 1) * m + p] = make_float2(snr, sni);
+                Yo2[(int64_t)(t >> 1) * m + p] = make_float2(ynr, yni);
+              }
+              sX[t * kWP + lane] = valid ? form_z(xr, snr, ynr, inv_mu_nxt) : 0.f;
+              sX[(t + 1) * kWP + lane] = valid ? form_z(xi, sni, yni, inv_mu_nxt) : 0.f;
             }
-            // Z' of the next iteration replaces X in the tile (only this thread reads it)
-            sX[t * kWP + lane] = valid ? form_z(x, sn, yn, inv_mu_nxt) : 0.f;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < CW; ++j) {
+            const int t = w * CW + j;
+            if (t < T) {
+              const float x = sX[t * kWP + lane], s = sS[t * kWP + lane], y = sY[t * kWP + lane];
+              const float r = s + q[j];
+              const float c = fminf(fmaxf(r, -gamma), gamma);
+              const float sn = r - c;
+              const float yn = f_mu * c;
+              const float e = c - y * inv_mu;
+              e2 = fmaf(e, e, e2);
+              if (valid) {
+                job.S[(int64_t)t * m + p] = sn;
+                Yout[(int64_t)t * m + p] = yn;
+              }
+              // Z' of the next iteration replaces X in the tile (only this thread reads it)
+              sX[t * kWP + lane] = valid ? form_z(x, sn, yn, inv_mu_nxt) : 0.f;
+            }
           }
         }
       } else {
@@ -196,9 +256,19 @@ __global__ void __launch_bounds__(kWideThreads, 1) pass_wide_kernel(Bufs b) {
         float u[CW];
         tile_times<CW>(u, sM, b.Vw, T, w, [&](int t) { return sX[t * kWP + lane]; });
         __syncthreads();  // every warp is done reading S, Y (aliased by U)
-        float4* dst = reinterpret_cast<float4*>(&sU[lane * WS::UP + w * CW]);
+        float4* dst = reinterpret_cast<float4*>(&sU[lane * UP + w * CW]);
 #pragma unroll
         for (int j4 = 0; j4 < CW / 4; ++j4) dst[j4] = make_float4(u[4 * j4], u[4 * j4 + 1], u[4 * j4 + 2], u[4 * j4 + 3]);
+        if constexpr (CPLX) {
+          // rows of i Z': (-Im, Re) per frame, in the same basis
+          tile_times<CW>(u, sM, b.Vw, T, w, [&](int t) {
+            return (t & 1) ? sX[(t - 1) * kWP + lane] : -sX[(t + 1) * kWP + lane];
+          });
+          float4* dstb = reinterpret_cast<float4*>(&sU[(kWP + lane) * UP + w * CW]);
+#pragma unroll
+          for (int j4 = 0; j4 < CW / 4; ++j4)
+            dstb[j4] = make_float4(u[4 * j4], u[4 * j4 + 1], u[4 * j4 + 2], u[4 * j4 + 3]);
+        }
       }
     }
     if (kGram) {
@@ -208,9 +278,9 @@ __global__ void __launch_bounds__(kWideThreads, 1) pass_wide_kernel(Bufs b) {
       for (int uu = 0; uu < WS::BPT; ++uu) {
         if (gbi[uu] < 0) continue;
         const int bi = gbi[uu], bj = gbj[uu];
-        for (int pp = 0; pp < kWP; ++pp) {
-          const float4 a = *reinterpret_cast<const float4*>(&sU[pp * WS::UP + 4 * bi]);
-          const float4 c = *reinterpret_cast<const float4*>(&sU[pp * WS::UP + 4 * bj]);
+        for (int pp = 0; pp < NROWS; ++pp) {
+          const float4 a = *reinterpret_cast<const float4*>(&sU[pp * UP + 4 * bi]);
+          const float4 c = *reinterpret_cast<const float4*>(&sU[pp * UP + 4 * bj]);
           const float av[4] = {a.x, a.y, a.z, a.w};
           const float cv[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
@@ -627,13 +697,13 @@ __global__ void __launch_bounds__(kEigWThreads, 1) eig_wide_kernel(Bufs b, int f
   }
 }
 
-template <int CW>
+template <int CW, bool CPLX>
 WideKernels make_wide() {
   WideKernels k;
-  k.pass[PM_INIT] = (void*)pass_wide_kernel<CW, PM_INIT>;
-  k.pass[PM_FUSED] = (void*)pass_wide_kernel<CW, PM_FUSED>;
-  k.pass[PM_UPDATE] = (void*)pass_wide_kernel<CW, PM_UPDATE>;
-  k.pass[PM_GRAM] = (void*)pass_wide_kernel<CW, PM_GRAM>;
+  k.pass[PM_INIT] = (void*)pass_wide_kernel<CW, PM_INIT, CPLX>;
+  k.pass[PM_FUSED] = (void*)pass_wide_kernel<CW, PM_FUSED, CPLX>;
+  k.pass[PM_UPDATE] = (void*)pass_wide_kernel<CW, PM_UPDATE, CPLX>;
+  k.pass[PM_GRAM] = (void*)pass_wide_kernel<CW, PM_GRAM, CPLX>;
   k.pass_smem = WideShape<CW>::smem;
   k.pass_threads = kWideThreads;
   k.tile = kWP;
@@ -642,17 +712,25 @@ WideKernels make_wide() {
   return k;
 }
 
-bool wide_kernels(int T, WideKernels* out) {
-  if (T <= kMaxT || T > kMaxTW) return false;
-  const int TP = (T + 31) / 32 * 32;
+template <bool CPLX>
+WideKernels pick_wide(int TP) {
   switch (TP) {
-    case 64: *out = make_wide<8>(); break;
-    case 96: *out = make_wide<12>(); break;
-    case 128: *out = make_wide<16>(); break;
-    case 160: *out = make_wide<20>(); break;
-    case 192: *out = make_wide<24>(); break;
-    default: *out = make_wide<28>(); break;
+    case 32: return make_wide<4, CPLX>();
+    case 64: return make_wide<8, CPLX>();
+    case 96: return make_wide<12, CPLX>();
+    case 128: return make_wide<16, CPLX>();
+    case 160: return make_wide<20, CPLX>();
+    case 192: return make_wide<24, CPLX>();
+    default: return make_wide<28, CPLX>();
   }
+}
+
+bool wide_kernels(int T, bool cplx, WideKernels* out) {
+  if (T > kMaxTW || T < 1) return false;
+  if (!cplx && T <= kMaxT) return false;
+  if (cplx && (T & 1)) return false;
+  const int TP = (T + 31) / 32 * 32;
+  *out = cplx ? pick_wide<true>(TP) : pick_wide<false>(TP);
   const int Te = T + (T & 1);
   out->eig_smem = sizeof(float) * ((size_t)Te * (Te + 1) + (size_t)kVRows * T);
   if (cudaFuncSetAttribute(out->eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->eig_smem) != cudaSuccess)

@@ -142,12 +142,12 @@ def _torch():
 
 
 def _check_like(frames, **bufs):
-    """Output (and warm-state) buffers must be contiguous float32 CUDA tensors shaped like frames."""
-    torch = _torch()
+    """Output (and warm-state) buffers must be contiguous CUDA tensors of the frames' dtype and shape."""
+    _torch()
     for name, t in bufs.items():
-        if (t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous()
+        if (t.dtype != frames.dtype or not t.is_cuda or not t.is_contiguous()
                 or tuple(t.shape) != tuple(frames.shape)):
-            raise ValueError(f"{name} must be a contiguous float32 CUDA tensor of shape {tuple(frames.shape)}")
+            raise ValueError(f"{name} must be a contiguous {frames.dtype} CUDA tensor of shape {tuple(frames.shape)}")
 
 
 def _stream_handle(stream):
@@ -193,8 +193,9 @@ class Plan:
         Returns (L, S, result) where result is a dict (None when wait=False).
         """
         torch = _torch()
-        if frames.dtype != torch.float32 or not frames.is_cuda or not frames.is_contiguous():
-            raise ValueError("frames must be a contiguous float32 CUDA tensor")
+        want = torch.complex64 if self.params.dtype == C64 else torch.float32
+        if frames.dtype != want or not frames.is_cuda or not frames.is_contiguous():
+            raise ValueError(f"frames must be a contiguous {want} CUDA tensor")
         if tuple(frames.shape) != (self.T, self.m):
             raise ValueError(f"frames shape {tuple(frames.shape)} != {(self.T, self.m)}")
         if L is None:
@@ -218,7 +219,7 @@ class Plan:
         The C library copies it to the device, solves, and copies L, S (and the
         mask) back into the given host buffers.  Returns (L, S, result)."""
         import numpy as np
-        F = np.ascontiguousarray(np.asarray(frames), dtype=np.float32)
+        F = np.ascontiguousarray(np.asarray(frames), dtype=np.complex64 if self.params.dtype == C64 else np.float32)
         if F.shape != (self.T, self.m):
             raise ValueError(f"frames shape {F.shape} != {(self.T, self.m)}")
         if L is None:
@@ -257,6 +258,8 @@ def solve(frames, **kw):
     T, m = frames.shape
     mask = kw.pop("mask", None)
     theta = kw.pop("theta", 0.0)
+    if str(frames.dtype) == "torch.complex64":
+        kw.setdefault("dtype", C64)
     plan = Plan(m, T, **kw)
     try:
         return plan.solve(frames, mask=mask, theta=theta)
@@ -451,9 +454,11 @@ class Server:
         L and S (allocated here unless given) receive the result; keep them
         until the request is reported done."""
         torch = _torch()
-        if frames.dtype != torch.float32 or not frames.is_cuda or not frames.is_contiguous():
-            raise ValueError("frames must be a contiguous float32 CUDA tensor")
+        if frames.dtype not in (torch.float32, torch.complex64) or not frames.is_cuda or not frames.is_contiguous():
+            raise ValueError("frames must be a contiguous float32 or complex64 CUDA tensor")
         T, m = frames.shape
+        if frames.dtype == torch.complex64:
+            kw = dict(kw, dtype=C64)
         p = default_params(m, T, **kw)
         if L is None:
             L = torch.empty_like(frames)
