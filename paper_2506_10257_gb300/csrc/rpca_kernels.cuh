@@ -428,8 +428,15 @@ __device__ bool pass_body(Bufs b, int lc, int nc, unsigned char* dsm) {
   return pass_epilogue<TB, kGram>(b, acc, e2, l1, sZ, sRed, sScal, &sLast, gthr, ggrp, gblk, lc, nc);
 }
 
+// Two CTAs per SM (128 registers a thread) hide more HBM latency than one CTA
+// with all 255; at 32 frames the cap would spill, so that bucket keeps one.
+template <int TB>
+__host__ __device__ constexpr int pass_min_blocks() {
+  return TB <= 24 ? 2 : 1;
+}
+
 template <int TB, int MODE>
-__global__ void __launch_bounds__(kPassThreads) pass_kernel(Bufs b) {
+__global__ void __launch_bounds__(kPassThreads, pass_min_blocks<TB>()) pass_kernel(Bufs b) {
   extern __shared__ __align__(16) unsigned char pass_dsm[];
   pass_body<TB, MODE>(b, blockIdx.x, gridDim.x, pass_dsm);
 }
