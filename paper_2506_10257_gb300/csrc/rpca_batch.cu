@@ -25,9 +25,13 @@
 
 #include "rpca_kernels.cuh"
 #include "rpca_internal.h"
+#include "rpca_wide.cuh"
 
 namespace rpca {
 #include "rpca_batch.cuh"
+
+// The wide / complex batch kernel (rpca_batch_wide.cu).
+void* batch_wide_kernel_fn(bool cplx);
 }  // namespace rpca
 
 using namespace rpca;
@@ -61,6 +65,9 @@ struct KernelInfo {
   size_t smem;
 };
 
+// Columns per warp of the tiled pass for T real columns.
+int wide_cw(int Tr) { return (Tr + 31) / 32 * 32 / 8; }
+
 KernelInfo batch_kernel_for(int tbmax) {
   if (tbmax <= 16) return {(void*)batch_kernel<16>, batch_smem<16>()};
   if (tbmax <= 20) return {(void*)batch_kernel<20>, batch_smem<20>()};
@@ -81,6 +88,8 @@ struct rpca_batch_s {
   std::vector<rpca_plan_t> plans;
   std::vector<PlanView> views;
   KernelInfo kern{};
+  bool wide = false;           // every window runs the tiled bodies
+  int vrows = 16;              // wide eigen-steps: rows of V staged per step
   int sms = 0;
   int occ_max = 0;       // resident batch CTAs per SM the kernel allows
   BatchConfig cfg{};
@@ -177,7 +186,7 @@ void make_schedule(rpca_batch_s* b, const BatchConfig& cfg) {
     for (int w : lw[l]) {
       b->win_slot[w] = (int)b->slot_win.size();
       b->slot_win.push_back(w);
-      const int64_t tiles = (b->p[w].m + kTile - 1) / kTile;
+      const int64_t tiles = (b->p[w].m + b->views[w].tile - 1) / b->views[w].tile;
       b->win_ncta[w] = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)nc[l], tiles, b->views[w].max_grid}));
     }
     d.w1 = (int)b->slot_win.size();
@@ -257,6 +266,7 @@ void write_static_desc(rpca_batch_s* b) {
   d->nwin = b->n;
   d->nlanes = b->nlanes;
   d->spin_limit = b->spin_limit;
+  d->vrows = b->vrows;
   for (int l = 0; l < b->nlanes; ++l) d->lane[l] = b->lanes[l];
   for (int slot = 0; slot < b->n; ++slot) {
     const int w = b->slot_win[slot];
@@ -266,7 +276,7 @@ void write_static_desc(rpca_batch_s* b) {
     wd.b.finalize = 1;
     wd.b.grid = b->win_ncta[w];
     wd.b.ngroups = (b->win_ncta[w] + kGroup - 1) / kGroup;
-    wd.TB = bucket_tb(b->p[w].T);
+    wd.TB = b->wide ? wide_cw(b->views[w].T) : bucket_tb(b->p[w].T);
   }
 }
 
@@ -312,11 +322,12 @@ rpca_status rpca_batch_create(const rpca_params* params, int32_t n, rpca_batch_t
   if (!params || !out || n < 1) return RPCA_ERR_ARG;
   *out = nullptr;
   if (n > kMaxBatch) return RPCA_ERR_UNSUPPORTED;
+  bool wide = false;
   for (int i = 0; i < n; ++i) {
     if (params[i].precision != RPCA_PREC_FP32) return RPCA_ERR_UNSUPPORTED;
-    if (params[i].T > kMaxT) return RPCA_ERR_UNSUPPORTED;
-    if (params[i].warm_start) return RPCA_ERR_UNSUPPORTED;  // windows of a batch start cold
-    if (params[i].dtype != RPCA_R32) return RPCA_ERR_UNSUPPORTED;
+    if (params[i].warm_start) return RPCA_ERR_UNSUPPORTED;        // windows of a batch start cold
+    if (params[i].dtype != params[0].dtype) return RPCA_ERR_UNSUPPORTED;  // one element type per batch
+    if (params[i].T > kMaxT || params[i].dtype == RPCA_C64) wide = true;
   }
   rpca_batch_s* b = new rpca_batch_s();
   b->n = n;
@@ -330,9 +341,41 @@ rpca_status rpca_batch_create(const rpca_params* params, int32_t n, rpca_batch_t
     delete b;
     return e != cudaSuccess ? cuda_st(e) : RPCA_ERR_UNSUPPORTED;
   }
-  int tbmax = 8;
-  for (int i = 0; i < n; ++i) tbmax = std::max(tbmax, bucket_tb(params[i].T));
-  b->kern = batch_kernel_for(tbmax);
+  b->wide = wide;
+  if (!wide) {
+    int tbmax = 8;
+    for (int i = 0; i < n; ++i) tbmax = std::max(tbmax, bucket_tb(params[i].T));
+    b->kern = batch_kernel_for(tbmax);
+  } else {
+    // shared memory: the largest tiled pass or eigen-step of the batch, with
+    // as many staged V rows (<= 16) as the SM leaves room for
+    const bool cplx = params[0].dtype == RPCA_C64;
+    b->kern.fn = batch_wide_kernel_fn(cplx);
+    cudaFuncAttributes fa;
+    int optin = 0;
+    e = cudaFuncGetAttributes(&fa, b->kern.fn);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) {
+      delete b;
+      return cuda_st(e);
+    }
+    const size_t room = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+    size_t need = 0;
+    for (int vr = 16; vr >= 1; --vr) {
+      need = 0;
+      for (int i = 0; i < n; ++i) {
+        const int Tr = params[i].dtype == RPCA_C64 ? 2 * params[i].T : params[i].T;
+        need = std::max({need, wide_pass_smem_bytes(wide_cw(Tr)), eig_wide_smem(Tr, vr)});
+      }
+      b->vrows = vr;
+      if (need <= room) break;
+    }
+    if (need > room) {
+      delete b;
+      return RPCA_ERR_UNSUPPORTED;
+    }
+    b->kern.smem = need;
+  }
   e = cudaFuncSetAttribute(b->kern.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->kern.smem);
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->occ_max, b->kern.fn, kBatchThreads, b->kern.smem);
@@ -345,7 +388,7 @@ rpca_status rpca_batch_create(const rpca_params* params, int32_t n, rpca_batch_t
     rpca_params q = params[i];
     q.drive = RPCA_DRIVE_STREAM;  // the batch drives the kernels itself
     rpca_plan_t pl = nullptr;
-    st = rpca_plan_create(&q, nullptr, 0, &pl);
+    st = plan_create_ex(&q, wide, &pl);
     if (st == RPCA_OK) {
       b->plans.push_back(pl);
       PlanView v;
@@ -411,7 +454,7 @@ rpca_status rpca_batch_solve(rpca_batch_t b, const rpca_window* win, void* strea
   b->pending = false;
   int worst = RPCA_OK;
   for (int i = 0; i < b->n; ++i) {
-    result_from_ctrl(b->views[i].lambda, b->h_ctrl[b->win_slot[i]], &out[i]);
+    result_from_ctrl(b->views[i].lambda, b->h_ctrl[b->win_slot[i]], &out[i], b->views[i].cplx);
     if (out[i].status < 0) worst = out[i].status;
     else if (worst == RPCA_OK && out[i].status != RPCA_OK) worst = out[i].status;
   }

@@ -41,7 +41,7 @@ struct BatchDesc {
   int nlanes;
   unsigned long long spin_limit;   // polls of a publication wait before it gives up
   unsigned int stop;               // set once any wait ran out: every later wait gives up at once
-  unsigned int pad_;
+  int vrows;                       // wide eigen-steps: rows of V staged per step
   LaneDesc lane[kMaxLanes];
   WinDesc w[kMaxBatch];
 };
@@ -124,8 +124,19 @@ __device__ __forceinline__ void window_fail(Bufs b) {
   __syncthreads();
 }
 
+// Steps of one window kind: the narrow (register-resident) pass and eigen-step
+// for T <= kMaxT frames, or the tiled ones (wide or complex windows).
 template <int TB>
-__device__ void run_window(WinDesc& wd, int lc, unsigned char* dsm, unsigned long long limit, unsigned int* stop) {
+struct NarrowBody {
+  static __device__ bool pass(Bufs b, bool init, int lc, int nc, unsigned char* dsm) {
+    return init ? pass_body<TB, PM_INIT>(b, lc, nc, dsm) : pass_body<TB, PM_FUSED>(b, lc, nc, dsm);
+  }
+  static __device__ void eig(Bufs b, int flags, unsigned char* dsm, int) { eig_fast_body<TB>(b, flags, 0, 0, dsm); }
+};
+
+template <class Body>
+__device__ void run_window(WinDesc& wd, int lc, unsigned char* dsm, unsigned long long limit, unsigned int* stop,
+                           int vrows) {
   const Bufs b = wd.b;
   const int nc = b.grid;
   if (lc >= nc) return;  // the window uses fewer CTAs than its lane has
@@ -172,10 +183,10 @@ __device__ void run_window(WinDesc& wd, int lc, unsigned char* dsm, unsigned lon
   int flags = EF_INIT | EF_EIG;
   const int max_iter = __ldcg(&b.ctrl->max_iter);
   for (int it = 0; it <= max_iter + 1; ++it) {
-    const bool fin = (it == 0) ? pass_body<TB, PM_INIT>(b, lc, nc, dsm) : pass_body<TB, PM_FUSED>(b, lc, nc, dsm);
+    const bool fin = Body::pass(b, it == 0, lc, nc, dsm);
     if (fin) {
       __syncthreads();
-      eig_fast_body<TB>(b, flags, 0, 0, dsm);
+      Body::eig(b, flags, dsm, vrows);
       gen_publish(gen);
     }
     if (!gen_wait(gen, 2u + (unsigned)it, limit, stop)) {
@@ -204,12 +215,12 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchDesc* bd) 
   for (int w = ld.w0; w < ld.w1; ++w) {
     WinDesc& wd = bd->w[w];
     switch (wd.TB) {
-      case 8: run_window<8>(wd, lc, batch_dsm, limit, &bd->stop); break;
-      case 12: if constexpr (TBMAX >= 12) run_window<12>(wd, lc, batch_dsm, limit, &bd->stop); break;
-      case 16: if constexpr (TBMAX >= 16) run_window<16>(wd, lc, batch_dsm, limit, &bd->stop); break;
-      case 20: if constexpr (TBMAX >= 20) run_window<20>(wd, lc, batch_dsm, limit, &bd->stop); break;
-      case 24: if constexpr (TBMAX >= 24) run_window<24>(wd, lc, batch_dsm, limit, &bd->stop); break;
-      case 32: if constexpr (TBMAX >= 32) run_window<32>(wd, lc, batch_dsm, limit, &bd->stop); break;
+      case 8: run_window<NarrowBody<8>>(wd, lc, batch_dsm, limit, &bd->stop, 0); break;
+      case 12: if constexpr (TBMAX >= 12) run_window<NarrowBody<12>>(wd, lc, batch_dsm, limit, &bd->stop, 0); break;
+      case 16: if constexpr (TBMAX >= 16) run_window<NarrowBody<16>>(wd, lc, batch_dsm, limit, &bd->stop, 0); break;
+      case 20: if constexpr (TBMAX >= 20) run_window<NarrowBody<20>>(wd, lc, batch_dsm, limit, &bd->stop, 0); break;
+      case 24: if constexpr (TBMAX >= 24) run_window<NarrowBody<24>>(wd, lc, batch_dsm, limit, &bd->stop, 0); break;
+      case 32: if constexpr (TBMAX >= 32) run_window<NarrowBody<32>>(wd, lc, batch_dsm, limit, &bd->stop, 0); break;
       default: break;
     }
     __syncthreads();

@@ -377,7 +377,9 @@ rpca_status plan_view(rpca_plan_t pl, PlanView* v) {
   v->m = pl->p.m;
   v->T = real_cols(&pl->p);
   v->cplx = pl->p.dtype == RPCA_C64;
-  v->max_grid = std::max(pl->lay.grid, pl->lay.ws_grid);
+  v->max_grid = std::max({pl->lay.grid, pl->lay.ws_grid, pl->wide ? pl->lay.wide_grid : 1});
+  v->tile = pl->wide ? pl->wk.tile : kTile;
+  v->wide = pl->wide ? 1 : 0;
   v->lambda = pl->lambda;
   v->y1 = (float*)(pl->ws + pl->lay.ybuf);
   return RPCA_OK;
@@ -419,7 +421,21 @@ rpca_status rpca_workspace_size(const rpca_params* p, size_t* bytes) {
   return RPCA_OK;
 }
 
+static rpca_status plan_create_impl(const rpca_params* p, void* workspace, size_t workspace_bytes, bool force_wide,
+                                    rpca_plan_t* out);
+
 rpca_status rpca_plan_create(const rpca_params* p, void* workspace, size_t workspace_bytes, rpca_plan_t* out) {
+  return plan_create_impl(p, workspace, workspace_bytes, false, out);
+}
+
+}  // extern "C"
+
+rpca_status rpca::plan_create_ex(const rpca_params* p, bool force_wide, rpca_plan_t* out) {
+  return plan_create_impl(p, nullptr, 0, force_wide, out);
+}
+
+static rpca_status plan_create_impl(const rpca_params* p, void* workspace, size_t workspace_bytes, bool force_wide,
+                                    rpca_plan_t* out) {
   rpca_status st = validate(p);
   if (st != RPCA_OK) return st;
   if (!out) return RPCA_ERR_ARG;
@@ -430,9 +446,9 @@ rpca_status rpca_plan_create(const rpca_params* p, void* workspace, size_t works
   pl->p = *p;
   const bool cplx = p->dtype == RPCA_C64;
   const int Tr = real_cols(p);
-  pl->wide = uses_wide(p);
+  pl->wide = uses_wide(p) || force_wide;
   if (pl->wide) {
-    if (!wide_kernels(Tr, cplx, &pl->wk)) {
+    if (!wide_kernels(Tr, cplx, pl->wide && !uses_wide(p), &pl->wk)) {
       delete pl;
       return RPCA_ERR_UNSUPPORTED;
     }
@@ -550,6 +566,7 @@ rpca_status rpca_plan_create(const rpca_params* p, void* workspace, size_t works
   return RPCA_OK;
 }
 
+extern "C" {
 
 // The plain form: separate Gram and update passes, residual read back by the
 // host after every iteration (one host synchronisation per iteration).

@@ -11,6 +11,8 @@ struct PlanView {
   int64_t m;
   int T;
   int max_grid;       // CTAs whose partials fit in the plan's workspace
+  int tile;           // pixels per tile of the plan's passes
+  int wide;           // the plan runs the tiled path
   double lambda;      // resolved lambda
   float* y1;          // second dual buffer (workspace)
   int cplx;           // complex window (T = 2 x frames)
@@ -28,8 +30,14 @@ struct WideKernels {
 };
 
 // Fills *out for T real columns (complex windows: T = 2 x frames, cplx set);
-// false when T is not a wide column count or a kernel attribute cannot be set.
-bool wide_kernels(int T, bool cplx, WideKernels* out);
+// false when T is not a wide column count (real T <= kMaxT unless force) or a
+// kernel attribute cannot be set.
+bool wide_kernels(int T, bool cplx, bool force, WideKernels* out);
+
+// rpca_plan_create with the tiled path forced for any frame count (the
+// batched form runs every window of a batch that holds a wide or complex
+// window through the tiled bodies).
+rpca_status plan_create_ex(const rpca_params* p, bool force_wide, rpca_plan_t* out);
 
 // Fills *v from a plan; RPCA_ERR_ARG for a null plan.
 rpca_status plan_view(rpca_plan_t plan, PlanView* v);

@@ -1,701 +1,10 @@
-// rpca_wide.cu -- the iteration for windows of many frames (kMaxT < T <= kMaxTW).
-//
-// Same algebra as the register-resident path (see rpca_device.cuh): per
-// iteration one fused pass over the pixels (Eq. 4-6 through the Gram of Z, the
-// residual of Sec. II-A, and the rotated Gram of the next Z) and one
-// eigen-step on one CTA.  With T up to 224 a pixel row no longer fits in one
-// thread's registers, so the pass works on tiles of 32 pixels x TP frames
-// (TP = T rounded up to a multiple of 32) staged in shared memory:
-//   1. X, S, Y of the tile -> shared memory, frame-major [t][p] (coalesced);
-//   2. Q = Z Wbar (Z = X - S + Y/mu formed on the fly), Wbar streamed through
-//      shared memory 32 rows at a time; lane = pixel, warp = 1/8 of the
-//      columns, so every Wbar read is a warp-wide broadcast;
-//   3. the Eq. 5-6 update of the lane's pixel for the warp's frames, S' and
-//      Y' written straight to HBM (coalesced), Z' kept in shared memory;
-//   4. U = Z' V (the next Gram's basis), written pixel-major;
-//   5. the partial Gram U^T U accumulated in registers across the CTA's tiles
-//      (4 x 4 blocks of the upper triangle spread over the CTA's threads).
-// The CTA partials go through the same two-level reduction as the narrow path.
-//
-// The eigen-step (one CTA of 1024 threads) runs cyclic Jacobi with FP32
-// rotations on the rotated Gram held in shared memory: each round of the
-// round-robin order rotates T/2 disjoint pairs; every 2 x 2 block of pairs is
-// then updated in place by one thread (the four entries of a block depend
-// only on each other), and the rotations are applied to the columns of V
-// (kept in the workspace) in the same phase.  The decisions (sigma, tau, the
-// rank and the first mu) are FP64, and Wbar = V diag(g) V^T is formed with V
-// staged in shared memory.
+// rpca_wide.cu -- host side of the wide / complex path: kernel tables.
 #include <cuda_runtime.h>
-#include <math.h>
 
-#include "rpca_kernels.cuh"
 #include "rpca_internal.h"
+#include "rpca_wide.cuh"
 
 namespace rpca {
-
-constexpr int kWP = 32;           // pixels per tile (one per lane)
-constexpr int kWKC = 32;          // rows of Wbar / V staged per step
-constexpr int kWideThreads = 256;
-constexpr int kEigWThreads = 1024;
-constexpr int kEigWBlocks = 7;    // 2 x 2 pair blocks per eigen-step thread
-constexpr int kVRows = 16;        // rows of V staged per step of V <- V + V D
-static_assert((kMaxTW / 2) * (kMaxTW / 2 + 1) / 2 <= kEigWBlocks * kEigWThreads, "pair blocks per thread");
-
-template <int CW>
-struct WideShape {
-  static constexpr int TP = 8 * CW;               // padded frames (8 warps x CW columns)
-  static constexpr int UP = TP + 4;               // row stride of the pixel-major U
-  static constexpr int NB = TP / 4;               // 4-frame blocks
-  static constexpr int NBLK = NB * (NB + 1) / 2;  // upper-triangle 4 x 4 blocks of the Gram
-  static constexpr int BPT = (NBLK + kWideThreads - 1) / kWideThreads;  // blocks per thread
-  static constexpr size_t smem = sizeof(float) * (3 * (size_t)TP * kWP + (size_t)kWKC * TP);
-  static_assert(CW % 4 == 0, "columns per warp must be a multiple of 4");
-  static_assert((size_t)kWP * UP <= 2 * (size_t)TP * kWP, "U must fit in the S and Y tiles");
-};
-
-// Stages rows [k0, k0 + kWKC) of a T x T row-major matrix into sM[kWKC][TP]
-// (zero outside T x T).
-template <int TP>
-__device__ __forceinline__ void stage_rows(float* sM, const float* M, int k0, int T) {
-  for (int i = threadIdx.x; i < kWKC * TP; i += kWideThreads) {
-    const int r = i / TP, c = i % TP;
-    const int k = k0 + r;
-    sM[i] = (k < T && c < T) ? __ldcg(&M[(size_t)k * T + c]) : 0.f;
-  }
-}
-
-// acc[j] = sum_t z(t) * M[t][w*CW + j], z(t) from zfun(t), M streamed from global.
-template <int CW, typename ZF>
-__device__ __forceinline__ void tile_times(float (&acc)[CW], float* sM, const float* M, int T, int w, ZF zfun) {
-  constexpr int TP = WideShape<CW>::TP;
-#pragma unroll
-  for (int j = 0; j < CW; ++j) acc[j] = 0.f;
-  for (int k0 = 0; k0 < T; k0 += kWKC) {
-    __syncthreads();
-    stage_rows<TP>(sM, M, k0, T);
-    __syncthreads();
-    const int kn = min(kWKC, T - k0);
-    for (int kk = 0; kk < kn; ++kk) {
-      const float z = zfun(k0 + kk);
-      const float4* row = reinterpret_cast<const float4*>(&sM[kk * TP + w * CW]);
-#pragma unroll
-      for (int j4 = 0; j4 < CW / 4; ++j4) {
-        const float4 v = row[j4];
-        acc[4 * j4] = fmaf(z, v.x, acc[4 * j4]);
-        acc[4 * j4 + 1] = fmaf(z, v.y, acc[4 * j4 + 1]);
-        acc[4 * j4 + 2] = fmaf(z, v.z, acc[4 * j4 + 2]);
-        acc[4 * j4 + 3] = fmaf(z, v.w, acc[4 * j4 + 3]);
-      }
-    }
-  }
-}
-
-// CPLX: complex windows as their interleaved real embedding (column 2t = Re,
-// 2t + 1 = Im of frame t; T = 2 x frames).  The Hermitian Gram Z^H Z is the
-// real Gram of the 2m rows a = [Re z, Im z] and b = a P = [-Im z, Re z] (the
-// row of i z) per pixel, so the pass adds both rows of every pixel to the
-// Gram; the shrink of Eq. 5 acts on the magnitude of each complex entry.
-template <int CW, int MODE, bool CPLX>
-__global__ void __launch_bounds__(kWideThreads, 1) pass_wide_kernel(Bufs b) {
-  using WS = WideShape<CW>;
-  constexpr int TP = WS::TP;
-  constexpr int UP = CPLX ? TP : WS::UP;       // U row stride (complex: 64 rows over the S, Y tiles)
-  constexpr int NROWS = CPLX ? 2 * kWP : kWP;  // Gram rows per tile
-  constexpr bool kGram = (MODE != PM_UPDATE);
-  extern __shared__ __align__(16) float wide_smem[];
-  float* sX = wide_smem;               // [TP][kWP]
-  float* sS = sX + TP * kWP;           // [TP][kWP]
-  float* sY = sS + TP * kWP;           // [TP][kWP]
-  float* sM = sY + TP * kWP;           // [kWKC][TP]
-  float* sU = sS;                      // [NROWS][UP], over the S and Y tiles once they are used
-  __shared__ double sRed[2][kWideThreads / 32];
-  __shared__ double sScal[2 * kMaxGroups];
-  __shared__ int sLast;
-
-  const Ctrl* ctrl = b.ctrl;
-  if (__ldcg(&ctrl->done)) return;
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  if (tid == 0) atomicMin(&b.red->t_start, gtimer());
-  const int T = b.T;
-  const int64_t m = b.m;
-  const int lc = blockIdx.x, nc = gridDim.x;
-  const Job job = *b.job;
-  const int kc = __ldcg(&ctrl->k);
-  const bool first = (kc == 0) && !__ldcg(&ctrl->warm);
-  const float f_mu = __ldcg(&ctrl->f_mu), inv_mu = __ldcg(&ctrl->f_inv_mu), gamma = __ldcg(&ctrl->f_gamma);
-  const float inv_mu_nxt = __ldcg(&ctrl->f_inv_mu_nxt);
-  const float* Yin = (kc & 1) ? job.Y1 : job.Y0;
-  float* Yout = (kc & 1) ? job.Y0 : job.Y1;
-
-  // Gram blocks owned by this thread
-  int gbi[WS::BPT], gbj[WS::BPT];
-  float gacc[WS::BPT][16];
-#pragma unroll
-  for (int u = 0; u < WS::BPT; ++u) {
-    const int blk = tid + u * kWideThreads;
-    gbi[u] = gbj[u] = -1;
-    if (blk < WS::NBLK) blk_coords(blk, WS::NB, gbi[u], gbj[u]);
-#pragma unroll
-    for (int i = 0; i < 16; ++i) gacc[u][i] = 0.f;
-  }
-  float e2 = 0.f, l1 = 0.f;
-
-  const int64_t ntiles = (m + kWP - 1) / kWP;
-  for (int64_t tile = lc; tile < ntiles; tile += nc) {
-    const int64_t p = tile * kWP + lane;
-    const bool valid = p < m;
-    __syncthreads();  // the previous tile's U is consumed
-    // ---- 1. stage the tile (frame-major) ----
-    if constexpr (CPLX) {
-      const float2* X2 = reinterpret_cast<const float2*>(job.X);
-      const float2* S2 = reinterpret_cast<const float2*>(job.S);
-      const float2* Y2 = reinterpret_cast<const float2*>(Yin);
-      for (int f = w; f < TP / 2; f += 8) {
-        const bool in = valid && 2 * f < T;
-        const float2 x = in ? X2[(int64_t)f * m + p] : make_float2(0.f, 0.f);
-        sX[(2 * f) * kWP + lane] = x.x;
-        sX[(2 * f + 1) * kWP + lane] = x.y;
-        if (MODE == PM_INIT) {
-          const float a2 = fmaf(x.x, x.x, x.y * x.y);
-          e2 += a2;
-          l1 += sqrtf(a2);
-        } else {
-          const float2 sv = (in && !first) ? S2[(int64_t)f * m + p] : make_float2(0.f, 0.f);
-          const float2 yv = (in && !first) ? Y2[(int64_t)f * m + p] : make_float2(0.f, 0.f);
-          sS[(2 * f) * kWP + lane] = sv.x;
-          sS[(2 * f + 1) * kWP + lane] = sv.y;
-          sY[(2 * f) * kWP + lane] = yv.x;
-          sY[(2 * f + 1) * kWP + lane] = yv.y;
-        }
-      }
-    } else {
-      for (int t = w; t < TP; t += 8) {
-        const bool in = valid && t < T;
-        const float x = in ? job.X[(int64_t)t * m + p] : 0.f;
-        sX[t * kWP + lane] = x;
-        if (MODE == PM_INIT) {
-          e2 = fmaf(x, x, e2);
-          l1 += fabsf(x);
-        } else {
-          sS[t * kWP + lane] = (in && !first) ? job.S[(int64_t)t * m + p] : 0.f;
-          sY[t * kWP + lane] = (in && !first) ? Yin[(int64_t)t * m + p] : 0.f;
-        }
-      }
-    }
-    __syncthreads();
-    if (MODE == PM_INIT) {
-      // U = X (standard basis), pixel-major; complex: also the rows of i X
-      for (int i = tid; i < TP * kWP; i += kWideThreads) {
-        const int t = i / kWP, pp = i % kWP;
-        sU[pp * UP + t] = sX[t * kWP + pp];
-        if (CPLX) sU[(kWP + pp) * UP + t] = (t & 1) ? sX[(t - 1) * kWP + pp] : -sX[(t + 1) * kWP + pp];
-      }
-    } else {
-      if (MODE != PM_GRAM) {
-        // ---- 2. Q = Z Wbar ----
-        float q[CW];
-        tile_times<CW>(q, sM, b.Ww, T, w, [&](int t) {
-          return form_z(sX[t * kWP + lane], sS[t * kWP + lane], sY[t * kWP + lane], inv_mu);
-        });
-        __syncthreads();  // every warp has read the whole tile before Z' overwrites X
-        // ---- 3. Eq. 5-6 for (lane's pixel, warp's frames) ----
-        if constexpr (CPLX) {
-          float2* S2 = reinterpret_cast<float2*>(job.S);
-          float2* Yo2 = reinterpret_cast<float2*>(Yout);
-#pragma unroll
-          for (int j = 0; j < CW; j += 2) {
-            const int t = w * CW + j;   // even: (Re, Im) of frame t / 2
-            if (t < T) {
-              const float xr = sX[t * kWP + lane], xi = sX[(t + 1) * kWP + lane];
-              const float sr = sS[t * kWP + lane], si = sS[(t + 1) * kWP + lane];
-              const float yr = sY[t * kWP + lane], yi = sY[(t + 1) * kWP + lane];
-              const float rr = sr + q[j], ri = si + q[j + 1];
-              const float mag = sqrtf(fmaf(rr, rr, ri * ri));
-              const float f = (mag > gamma) ? gamma / mag : 1.f;   // clip to the disc of radius gamma
-              const float cr = rr * f, ci = ri * f;
-              const float snr = rr - cr, sni = ri - ci;           // Eq. 5 (magnitude shrink)
-              const float ynr = f_mu * cr, yni = f_mu * ci;       // Eq. 6
-              const float er = cr - yr * inv_mu, ei = ci - yi * inv_mu;
-              e2 = fmaf(er, er, fmaf(ei, ei, e2));
-              if (valid) {
-                S2[(int64_t)(t >> 1) * m + p] = make_float2(snr, sni);
-                Yo2[(int64_t)(t >> 1) * m + p] = make_float2(ynr, yni);
-              }
-              sX[t * kWP + lane] = valid ? form_z(xr, snr, ynr, inv_mu_nxt) : 0.f;
-              sX[(t + 1) * kWP + lane] = valid ? form_z(xi, sni, yni, inv_mu_nxt) : 0.f;
-            }
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < CW; ++j) {
-            const int t = w * CW + j;
-            if (t < T) {
-              const float x = sX[t * kWP + lane], s = sS[t * kWP + lane], y = sY[t * kWP + lane];
-              const float r = s + q[j];
-              const float c = fminf(fmaxf(r, -gamma), gamma);
-              const float sn = r - c;
-              const float yn = f_mu * c;
-              const float e = c - y * inv_mu;
-              e2 = fmaf(e, e, e2);
-              if (valid) {
-                job.S[(int64_t)t * m + p] = sn;
-                Yout[(int64_t)t * m + p] = yn;
-              }
-              // Z' of the next iteration replaces X in the tile (only this thread reads it)
-              sX[t * kWP + lane] = valid ? form_z(x, sn, yn, inv_mu_nxt) : 0.f;
-            }
-          }
-        }
-      } else {
-        // Z of the current iterate in place of X
-        for (int t = w; t < T; t += 8)
-          sX[t * kWP + lane] = form_z(sX[t * kWP + lane], sS[t * kWP + lane], sY[t * kWP + lane], inv_mu);
-      }
-      if (kGram) {
-        // ---- 4. U = Z' V, pixel-major over the dead S, Y tiles ----
-        float u[CW];
-        tile_times<CW>(u, sM, b.Vw, T, w, [&](int t) { return sX[t * kWP + lane]; });
-        __syncthreads();  // every warp is done reading S, Y (aliased by U)
-        float4* dst = reinterpret_cast<float4*>(&sU[lane * UP + w * CW]);
-#pragma unroll
-        for (int j4 = 0; j4 < CW / 4; ++j4) dst[j4] = make_float4(u[4 * j4], u[4 * j4 + 1], u[4 * j4 + 2], u[4 * j4 + 3]);
-        if constexpr (CPLX) {
-          // rows of i Z': (-Im, Re) per frame, in the same basis
-          tile_times<CW>(u, sM, b.Vw, T, w, [&](int t) {
-            return (t & 1) ? sX[(t - 1) * kWP + lane] : -sX[(t + 1) * kWP + lane];
-          });
-          float4* dstb = reinterpret_cast<float4*>(&sU[(kWP + lane) * UP + w * CW]);
-#pragma unroll
-          for (int j4 = 0; j4 < CW / 4; ++j4)
-            dstb[j4] = make_float4(u[4 * j4], u[4 * j4 + 1], u[4 * j4 + 2], u[4 * j4 + 3]);
-        }
-      }
-    }
-    if (kGram) {
-      __syncthreads();
-      // ---- 5. partial Gram U^T U (upper 4 x 4 blocks) ----
-#pragma unroll
-      for (int uu = 0; uu < WS::BPT; ++uu) {
-        if (gbi[uu] < 0) continue;
-        const int bi = gbi[uu], bj = gbj[uu];
-        for (int pp = 0; pp < NROWS; ++pp) {
-          const float4 a = *reinterpret_cast<const float4*>(&sU[pp * UP + 4 * bi]);
-          const float4 c = *reinterpret_cast<const float4*>(&sU[pp * UP + 4 * bj]);
-          const float av[4] = {a.x, a.y, a.z, a.w};
-          const float cv[4] = {c.x, c.y, c.z, c.w};
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) gacc[uu][i * 4 + j] = fmaf(av[i], cv[j], gacc[uu][i * 4 + j]);
-        }
-      }
-    }
-  }
-
-  // ---- CTA partials ----
-  const int TT = T * T;
-  if (kGram) {
-#pragma unroll
-    for (int uu = 0; uu < WS::BPT; ++uu) {
-      if (gbi[uu] < 0) continue;
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int a = 4 * gbi[uu] + i / 4, c = 4 * gbj[uu] + i % 4;
-        if (a < T && c < T && a <= c) {
-          b.gram_part[(int64_t)lc * TT + a * T + c] = gacc[uu][i];
-          b.gram_part[(int64_t)lc * TT + c * T + a] = gacc[uu][i];
-        }
-      }
-    }
-  }
-  {
-    const double v0 = warp_sum_d((double)e2), v1 = warp_sum_d((double)l1);
-    if (lane == 0) {
-      sRed[0][w] = v0;
-      sRed[1][w] = v1;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      double s0 = 0, s1 = 0;
-      for (int i = 0; i < kWideThreads / 32; ++i) {
-        s0 += sRed[0][i];
-        s1 += sRed[1][i];
-      }
-      b.scal_part[2 * lc] = s0;
-      b.scal_part[2 * lc + 1] = s1;
-    }
-  }
-  cross_cta_reduce<4>(b, kGram, sScal, &sLast, lc, nc);
-}
-
-// ---------------------------------------------------------------------------
-// Eigen-step for wide windows (one CTA, kEigWThreads threads).
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kEigWThreads, 1) eig_wide_kernel(Bufs b, int flags, cudaGraphConditionalHandle h,
-                                                                   int use_cond) {
-  extern __shared__ __align__(16) float eigw_smem[];
-  __shared__ float sC[kMaxTW / 2], sSn[kMaxTW / 2];
-  __shared__ int sP[kMaxTW / 2], sQ[kMaxTW / 2];
-  __shared__ float sDp[kMaxTW / 2], sDq[kMaxTW / 2];
-  __shared__ double sEv[kMaxTW];
-  __shared__ float sG[kMaxTW];
-  __shared__ float2 sCS[2][kMaxTW / 2];
-  __shared__ int2 sPQ[2][kMaxTW / 2];
-  __shared__ int sFlag;
-  __shared__ double sTau;
-
-  Ctrl* ctrl = b.ctrl;
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const int T = b.T;
-  const int Te = T + (T & 1);   // even size (a zero row/column pads odd T)
-  const int K = Te / 2;
-  const int LD = Te + 1;
-  float* G = eigw_smem;          // [Te][LD]
-  const unsigned long long t0 = gtimer();
-  if (!eig_control(b, flags, h, use_cond, &sFlag)) return;
-  const bool cold = (flags & EF_INIT) != 0;
-
-  for (int i = tid; i < Te * LD; i += nthr) {
-    const int r = i / LD, c = i % LD;
-    G[i] = (r < T && c < T) ? b.Gw[r * T + c] : 0.f;
-  }
-  if (cold)
-    for (int i = tid; i < T * T; i += nthr) b.Vw[i] = (i / T == i % T) ? 1.f : 0.f;
-  __syncthreads();  // (global writes of the block are visible to its later reads)
-  const unsigned long long t1 = gtimer();
-
-  const float eps = (float)ctrl->jacobi_eps;
-  const float eps2 = eps * eps;
-  int max_sweeps = (cold || (flags & EF_FULL)) ? ctrl->cold_sweeps : ctrl->warm_sweeps;
-  if (max_sweeps > kWideLogSweeps) max_sweeps = kWideLogSweeps;
-  const int nblk = K * (K + 1) / 2;
-  // the 2 x 2 pair blocks (A <= C) this thread updates, fixed for every round
-  int blkA[kEigWBlocks], blkC[kEigWBlocks];
-#pragma unroll
-  for (int u = 0; u < kEigWBlocks; ++u) {
-    const int bidx = tid + u * kEigWThreads;
-    blkA[u] = blkC[u] = -1;
-    if (bidx < nblk) blk_coords(bidx, K, blkA[u], blkC[u]);
-  }
-  int sweeps = 0, rounds_run = 0;
-  // Rotations are logged (round number, K (c, s) pairs) to the workspace and
-  // applied to V after the sweeps, with V staged in shared memory.
-  float2* log_cs = b.rot_log;
-  int* log_rnd = b.rot_rnd;
-  while (sweeps < max_sweeps) {
-    int need = 0;
-    for (int i = tid; i < Te * Te; i += nthr) {
-      const int a = i / Te, c = i % Te;
-      if (a < c) {
-        const float apq = G[a * LD + c];
-        if (apq != 0.f && apq * apq > eps2 * fabsf(G[a * LD + a] * G[c * LD + c])) need = 1;
-      }
-    }
-    if (!__syncthreads_or(need)) break;
-    for (int rnd = 0; rnd < Te - 1; ++rnd) {
-      // ---- phase A: the round's rotations (GVL sym.schur2, FP32) ----
-      int act = 0;
-      if (tid < K) {
-        int pa, pb;
-        rr_pair(rnd, tid, Te, pa, pb);
-        const int p = min(pa, pb), q = max(pa, pb);
-        const float app = G[p * LD + p], aqq = G[q * LD + q], apq = G[p * LD + q];
-        float c = 1.f, s = 0.f, dp = app, dq = aqq;
-        if (apq != 0.f && apq * apq > eps2 * fabsf(app * aqq)) {
-          act = 1;
-          const float dd = aqq - app;
-          const float r2 = fmaf(dd, dd, 4.f * apq * apq);
-          const float den = fabsf(dd) + sqrtf(r2);
-          const float t = copysignf(1.f, dd) * (2.f * apq) * __fdividef(1.f, den);
-          c = rsqrtf(fmaf(t, t, 1.f));
-          s = t * c;
-          dp = app - t * apq;
-          dq = aqq + t * apq;
-        }
-        sP[tid] = p;
-        sQ[tid] = q;
-        sC[tid] = c;
-        sSn[tid] = s;
-        sDp[tid] = dp;
-        sDq[tid] = dq;
-      }
-      if (!__syncthreads_or(act)) continue;
-      if (tid < K) log_cs[(size_t)rounds_run * K + tid] = make_float2(sC[tid], sSn[tid]);
-      if (tid == 0) log_rnd[rounds_run] = rnd;
-      ++rounds_run;
-      // ---- phase B: G <- J^T G J by 2 x 2 pair blocks, in place ----
-#pragma unroll
-      for (int u = 0; u < kEigWBlocks; ++u) {
-        const int A = blkA[u], C = blkC[u];
-        if (A < 0) continue;
-        const float sA = sSn[A];
-        if (A == C) {
-          if (sA != 0.f) {
-            const int pA = sP[A], qA = sQ[A];
-            G[pA * LD + pA] = sDp[A];
-            G[qA * LD + qA] = sDq[A];
-            G[pA * LD + qA] = 0.f;
-            G[qA * LD + pA] = 0.f;
-          }
-          continue;
-        }
-        const float sC_ = sSn[C];
-        if (sA == 0.f && sC_ == 0.f) continue;  // neither pair rotated: block unchanged
-        const int pA = sP[A], qA = sQ[A], pC = sP[C], qC = sQ[C];
-        const float cA = sC[A], cC = sC[C];
-        const float g00 = G[pA * LD + pC], g01 = G[pA * LD + qC];
-        const float g10 = G[qA * LD + pC], g11 = G[qA * LD + qC];
-        // columns of J for the pair: p -> (c, -s), q -> (s, c)
-        const float h00 = cC * g00 - sC_ * g01, h01 = sC_ * g00 + cC * g01;  // G J (rows pA)
-        const float h10 = cC * g10 - sC_ * g11, h11 = sC_ * g10 + cC * g11;  // G J (rows qA)
-        const float n00 = cA * h00 - sA * h10, n01 = cA * h01 - sA * h11;    // J^T (G J)
-        const float n10 = sA * h00 + cA * h10, n11 = sA * h01 + cA * h11;
-        G[pA * LD + pC] = n00;
-        G[pC * LD + pA] = n00;
-        G[pA * LD + qC] = n01;
-        G[qC * LD + pA] = n01;
-        G[qA * LD + pC] = n10;
-        G[pC * LD + qA] = n10;
-        G[qA * LD + qC] = n11;
-        G[qC * LD + qA] = n11;
-      }
-      __syncthreads();
-    }
-    ++sweeps;
-  }
-  const unsigned long long t2 = gtimer();
-  if (tid < T) sEv[tid] = (double)G[tid * LD + tid];
-  __syncthreads();
-
-  // ---- Q = J_1 J_2 ... from the logged rounds, kept as D = Q - I (over the
-  //      consumed G): near the identity D is small, so its rounding errors
-  //      are relative to small entries; then V <- V + V D ----
-  float* D = G;  // [T][LD]
-  for (int i = tid; i < T * LD; i += nthr) D[i] = 0.f;
-  if (rounds_run > 0) {
-    if (tid < K) {
-      sCS[0][tid] = __ldcg(&log_cs[tid]);
-      int pa, pb;
-      rr_pair(__ldcg(&log_rnd[0]), tid, Te, pa, pb);
-      sPQ[0][tid] = make_int2(min(pa, pb), max(pa, pb));
-    }
-  }
-  __syncthreads();
-  for (int lr = 0; lr < rounds_run; ++lr) {
-    const int cb = lr & 1;
-    // the next round's rotations and pairs, fetched while this one is applied
-    if (lr + 1 < rounds_run && tid < K) {
-      sCS[cb ^ 1][tid] = __ldcg(&log_cs[(size_t)(lr + 1) * K + tid]);
-      int pa, pb;
-      rr_pair(__ldcg(&log_rnd[lr + 1]), tid, Te, pa, pb);
-      sPQ[cb ^ 1][tid] = make_int2(min(pa, pb), max(pa, pb));
-    }
-    // warp w takes rows w, w + 32, ...; lane l takes pairs l, l + 32, ...
-    for (int r = tid >> 5; r < T; r += kEigWThreads / 32)
-      for (int k = tid & 31; k < K; k += 32) {
-      const float2 cs = sCS[cb][k];
-      if (cs.y == 0.f) continue;
-      const int2 pq = sPQ[cb][k];
-      if (pq.y >= T) continue;
-      // Q' = Q J  <=>  D' = D J + (J - I), with c - 1 = -s^2 / (1 + c)
-      const float c = cs.x, sn = cs.y, cm1 = -sn * sn / (1.f + c);
-      float* dr = &D[r * LD];
-      const float dp = dr[pq.x], dq = dr[pq.y];
-      float np = fmaf(c, dp, -sn * dq), nq = fmaf(sn, dp, c * dq);
-      if (r == pq.x) {
-        np += cm1;
-        nq += sn;
-      } else if (r == pq.y) {
-        np -= sn;
-        nq += cm1;
-      }
-      dr[pq.x] = np;
-      dr[pq.y] = nq;
-      }
-    __syncthreads();
-  }
-  // V <- V + V D, kVRows rows of V at a time staged after D
-  float* sVo = eigw_smem + (size_t)Te * LD;  // [kVRows][T]
-  for (int r0 = 0; r0 < T; r0 += kVRows) {
-    const int nr = min(kVRows, T - r0);
-    for (int i = tid; i < nr * T; i += nthr) sVo[i] = __ldcg(&b.Vw[(size_t)r0 * T + i]);
-    __syncthreads();
-    const int ncg = (T + 3) / 4;
-    for (int item = tid; item < nr * ncg; item += nthr) {
-      const int rr = item / ncg, c0 = 4 * (item % ncg);
-      float acc[4] = {0.f, 0.f, 0.f, 0.f};
-      int cc[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) cc[k] = min(c0 + k, T - 1);
-      for (int j = 0; j < T; ++j) {
-        const float v = sVo[rr * T + j];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) acc[k] = fmaf(v, D[j * LD + cc[k]], acc[k]);
-      }
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if (c0 + k < T) b.Vw[(size_t)(r0 + rr) * T + c0 + k] = sVo[rr * T + c0 + k] + acc[k];
-    }
-    __syncthreads();
-  }
-  // V (new) staged over D for the orthonormalisation and Wbar
-  float* sV = G;  // [T][T + 1]
-  const int LV = T + 1;
-  for (int i = tid; i < T * T; i += nthr) sV[(i / T) * LV + i % T] = __ldcg(&b.Vw[i]);
-  __syncthreads();
-
-  // ---- FP64 decisions ----
-  if (tid == 0) {
-    if (flags & EF_INIT) {
-      double lmax = 0.0;
-      for (int a = 0; a < T; ++a) lmax = fmax(lmax, sEv[a]);
-      init_mu(b, lmax);
-    }
-    sTau = 1.0 / ctrl->mu_cur;
-  }
-  __syncthreads();
-  int keep = 0;
-  if (tid < T) {
-    const double sig = sqrt(fmax(sEv[tid], 0.0));
-    keep = sig > sTau;
-    sG[tid] = keep ? (float)(sTau / sig) : 1.f;
-  }
-  const int rank = __syncthreads_count(keep);
-  // ---- re-orthonormalise V (one Newton-Schulz step, V <- V (3 I - V^T V) / 2),
-  //      then Wbar = V diag(g) V^T; V is staged over G ----
-  const int NB4 = (T + 3) / 4;
-  const int nb2 = NB4 * (NB4 + 1) / 2;
-  const unsigned long long t3 = gtimer();
-  // A = V^T V into the (consumed) Gram array, and its largest deviation from I
-  float dev = 0.f;
-  for (int bidx = tid; bidx < nb2; bidx += nthr) {
-    int bi, bj;
-    blk_coords(bidx, NB4, bi, bj);
-    float acc[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) acc[i] = 0.f;
-    int ca[4], cc[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      ca[i] = min(4 * bi + i, T - 1);
-      cc[i] = min(4 * bj + i, T - 1);
-    }
-    for (int r = 0; r < T; ++r) {
-      float va[4], vc[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        va[i] = sV[r * LV + ca[i]];
-        vc[i] = sV[r * LV + cc[i]];
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) acc[i * 4 + k] = fmaf(va[i], vc[k], acc[i * 4 + k]);
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int a = 4 * bi + i, c = 4 * bj + k;
-        if (a < T && c < T) {
-          b.Gw[a * T + c] = acc[i * 4 + k];
-          b.Gw[c * T + a] = acc[i * 4 + k];
-          dev = fmaxf(dev, fabsf(acc[i * 4 + k] - (a == c ? 1.f : 0.f)));
-        }
-      }
-  }
-  // skip the correction once V is orthonormal to FP32 rounding
-  const int correct = __syncthreads_or(dev > 4e-7f);
-  if (correct) {
-    // V_new = 1.5 V - 0.5 V A  (rows of V from shared memory, A from the workspace)
-    const int nbf = NB4 * NB4;
-    for (int bidx = tid; bidx < nbf; bidx += nthr) {
-      const int bi = bidx / NB4, bj = bidx % NB4;
-      float acc[16];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) acc[i] = 0.f;
-      int ra[4], cc[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        ra[i] = min(4 * bi + i, T - 1);
-        cc[i] = min(4 * bj + i, T - 1);
-      }
-      for (int j = 0; j < T; ++j) {
-        float va[4], ac[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          va[i] = sV[ra[i] * LV + j];
-          ac[i] = __ldcg(&b.Gw[j * T + cc[i]]);
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int k = 0; k < 4; ++k) acc[i * 4 + k] = fmaf(va[i], ac[k], acc[i * 4 + k]);
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int r = 4 * bi + i, c = 4 * bj + k;
-          if (r < T && c < T) b.Vw[r * T + c] = 1.5f * sV[r * LV + c] - 0.5f * acc[i * 4 + k];
-        }
-    }
-    __syncthreads();
-    for (int i = tid; i < T * T; i += nthr) sV[(i / T) * LV + i % T] = __ldcg(&b.Vw[i]);
-    __syncthreads();
-  }
-  for (int bidx = tid; bidx < nb2; bidx += nthr) {
-    int bi, bj;
-    blk_coords(bidx, NB4, bi, bj);
-    float acc[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) acc[i] = 0.f;
-    int ra[4], rc[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      ra[i] = min(4 * bi + i, T - 1);
-      rc[i] = min(4 * bj + i, T - 1);
-    }
-    for (int j = 0; j < T; ++j) {
-      const float gj = sG[j];
-      float va[4], vc[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        va[i] = sV[ra[i] * LV + j] * gj;
-        vc[i] = sV[rc[i] * LV + j];
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) acc[i * 4 + k] = fmaf(va[i], vc[k], acc[i * 4 + k]);
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int a = 4 * bi + i, c = 4 * bj + k;
-        if (a < T && c < T) {
-          b.Ww[a * T + c] = acc[i * 4 + k];
-          b.Ww[c * T + a] = acc[i * 4 + k];
-        }
-      }
-  }
-  if (tid < T) b.evw[tid] = sEv[tid];
-  if (tid == 0) {
-    ctrl->rank = rank;
-    ctrl->sweeps = sweeps;
-    ctrl->total_sweeps += sweeps;
-    const unsigned long long t4 = gtimer();
-    ctrl->eig_ns += t4 - t0;
-    ctrl->eig_cnt += 1;
-    ctrl->eig_phase_ns[0] += t1 - t0;
-    ctrl->eig_phase_ns[1] += t2 - t1;
-    ctrl->eig_phase_ns[2] += t3 - t2;
-    ctrl->eig_phase_ns[3] += t4 - t3;
-    ctrl->eig_rounds += rounds_run;
-    set_cond(h, use_cond, 1u);
-  }
-}
 
 template <int CW, bool CPLX>
 WideKernels make_wide() {
@@ -725,14 +34,13 @@ WideKernels pick_wide(int TP) {
   }
 }
 
-bool wide_kernels(int T, bool cplx, WideKernels* out) {
+bool wide_kernels(int T, bool cplx, bool force, WideKernels* out) {
   if (T > kMaxTW || T < 1) return false;
-  if (!cplx && T <= kMaxT) return false;
+  if (!cplx && T <= kMaxT && !force) return false;
   if (cplx && (T & 1)) return false;
   const int TP = (T + 31) / 32 * 32;
   *out = cplx ? pick_wide<true>(TP) : pick_wide<false>(TP);
-  const int Te = T + (T & 1);
-  out->eig_smem = sizeof(float) * ((size_t)Te * (Te + 1) + (size_t)kVRows * T);
+  out->eig_smem = eig_wide_smem(T, kVRows);
   if (cudaFuncSetAttribute(out->eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->eig_smem) != cudaSuccess)
     return false;
   for (int i = 0; i < 4; ++i)

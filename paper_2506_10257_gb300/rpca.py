@@ -362,8 +362,9 @@ class Batch:
         w = (Window * self.n)()
         for i, F in enumerate(frames):
             m, T = self.shapes[i]
-            if F.dtype != torch.float32 or not F.is_cuda or not F.is_contiguous() or tuple(F.shape) != (T, m):
-                raise ValueError(f"window {i}: need a contiguous float32 CUDA tensor of shape {(T, m)}")
+            if (F.dtype not in (torch.float32, torch.complex64) or not F.is_cuda or not F.is_contiguous()
+                    or tuple(F.shape) != (T, m)):
+                raise ValueError(f"window {i}: need a contiguous float32 or complex64 CUDA tensor of shape {(T, m)}")
             _check_like(F, L=Ls[i], S=Ss[i])
             w[i].X = F.data_ptr()
             w[i].L = Ls[i].data_ptr()

@@ -141,3 +141,50 @@ def test_batch_rejects_unsupported(rp):
         rp.Batch([(4096, 20)], precision=rp.PREC_BF16X3)
     with pytest.raises(ValueError):
         rp.Batch([])
+
+
+def oracle_same_iters(frames, iters, **kw):
+    """The oracle's iterate with the GPU's iteration count (rerun when the FP32
+    and FP64 residuals cross tol one iteration apart)."""
+    ref = O.rpca_frames(frames, **kw)
+    assert abs(iters - ref.iters) <= 1, (iters, ref.iters)
+    if iters != ref.iters:
+        ref = O.rpca_frames(frames, **dict(kw, max_iter=iters, tol=1e-30))
+    return ref
+
+
+def test_batch_with_wide_windows(rp):
+    # a window of more than 32 frames sends every window of the batch through
+    # the tiled bodies (narrow ones included)
+    wins = windows([(32, 32, 12), (24, 40, 50), (32, 32, 20), (16, 32, 100), (20, 17, 33)], seed0=600)
+    got, info = run_batch(rp, wins)
+    for w, g in zip(wins, got):
+        assert g["res"]["status"] == rp.OK, g["res"]
+        ref = oracle_same_iters(w.frames, g["res"]["iters"])
+        eL, eS = rel(g["L"], ref.L), rel(g["S"], ref.S)
+        assert eL <= FP32_TOL and eS <= FP32_TOL, (eL, eS, w.m, w.T)
+
+
+def test_batch_of_complex_windows(rp):
+    shapes = [(16, 16, 8), (32, 32, 20), (24, 24, 13)]
+    wins = [synth.make_window(seed=700 + i, ny=ny, nx=nx, T=T, n_bound=4, n_free=6, complex_iq=True)
+            for i, (ny, nx, T) in enumerate(shapes)]
+    b = rp.Batch([(w.m, w.T) for w in wins], dtype=rp.C64)
+    X = [torch.from_numpy(np.ascontiguousarray(w.frames, dtype=np.complex64)).cuda() for w in wins]
+    Ls, Ss, res = b.solve(X)
+    torch.cuda.synchronize()
+    b.close()
+    for w, L, S, r in zip(wins, Ls, Ss, res):
+        assert r["status"] == rp.OK
+        ref = oracle_same_iters(w.frames, r["iters"])
+        assert r["rank"] == ref.rank
+        Lg = L.cpu().numpy().astype(np.complex128)
+        Sg = S.cpu().numpy().astype(np.complex128)
+        eL = np.linalg.norm(Lg - ref.L) / np.linalg.norm(ref.L)
+        eS = np.linalg.norm(Sg - ref.S) / np.linalg.norm(ref.S)
+        assert eL <= FP32_TOL and eS <= FP32_TOL, (eL, eS)
+
+
+def test_batch_rejects_mixed_element_types(rp):
+    with pytest.raises(rp.RpcaError):
+        rp.Batch([(256, 8), (256, 8)], params=[dict(), dict(dtype=rp.C64)])
