@@ -103,7 +103,7 @@ bool get_set(int T, KernelSet* out) {
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Layout {
-  size_t ctrl, eig, red, job, gw, ww, vw, evw, rlog, rrnd, gram_part, group_part, scal_part, gscal_part, ybuf, total;
+  size_t ctrl, eig, red, job, gw, ww, vw, evw, rlog, rk, rrnd, gram_part, group_part, scal_part, gscal_part, ybuf, total;
   int grid, ngroups;
   int ws_grid;     // CTAs of the warp-specialised pass (one per SM, 128-pixel tiles)
   int wide_grid;   // CTAs of the wide pass (T > kMaxT; one per SM, 32-pixel tiles)
@@ -146,7 +146,8 @@ Layout make_layout(int64_t m, int T, int sms, bool wide) {
   const size_t nrounds = wide ? (size_t)kWideLogSweeps * (size_t)(T + (T & 1)) : 1;
   const size_t npairs = wide ? (size_t)(T + (T & 1)) / 2 : 1;
   L.rlog = take(sizeof(float2) * nrounds * npairs);
-  L.rrnd = take(sizeof(int) * nrounds);
+  L.rk = take(sizeof(int) * nrounds * npairs);
+  L.rrnd = take(sizeof(int) * 2 * nrounds);
   L.gram_part = take(sizeof(float) * (size_t)maxgrid * T * T);
   L.group_part = take(sizeof(float) * (size_t)L.ngroups * T * T);
   L.scal_part = take(sizeof(double) * 2 * (size_t)maxgrid);
@@ -511,6 +512,7 @@ static rpca_status plan_create_impl(const rpca_params* p, void* workspace, size_
   b.Vw = (float*)(pl->ws + pl->lay.vw);
   b.evw = (double*)(pl->ws + pl->lay.evw);
   b.rot_log = (float2*)(pl->ws + pl->lay.rlog);
+  b.rot_k = (int*)(pl->ws + pl->lay.rk);
   b.rot_rnd = (int*)(pl->ws + pl->lay.rrnd);
   b.m = p->m;
   b.T = Tr;

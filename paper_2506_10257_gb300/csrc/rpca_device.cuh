@@ -149,8 +149,9 @@ struct Bufs {
   float* Ww;
   float* Vw;
   double* evw;
-  float2* rot_log;    // wide eigen-step: (c, s) of every pair of every executed round
-  int* rot_rnd;       // ... and the round number of each
+  float2* rot_log;    // wide eigen-step: (c, s) of every rotated pair of every executed round
+  int* rot_k;         // ... its pair slot in the round
+  int* rot_rnd;       // ... per round: round number and rotated pairs
 };
 
 }  // namespace rpca

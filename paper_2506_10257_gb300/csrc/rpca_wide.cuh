@@ -360,12 +360,15 @@ __host__ __device__ constexpr size_t eig_wide_smem(int T, int vrows) {
 static __device__ void eig_wide_body(Bufs b, int flags, cudaGraphConditionalHandle h, int use_cond, float* eigw_smem,
                               int vrows) {
   __shared__ float sC[kMaxTW / 2], sSn[kMaxTW / 2];
-  __shared__ int sP[kMaxTW / 2], sQ[kMaxTW / 2];
   __shared__ float sDp[kMaxTW / 2], sDq[kMaxTW / 2];
   __shared__ double sEv[kMaxTW];
   __shared__ float sG[kMaxTW];
-  __shared__ float2 sCS[2][kMaxTW / 2];
+  __shared__ float4 sCS[2][kMaxTW / 2];   // replay: (c, s, c - 1) per rotation
   __shared__ int2 sPQ[2][kMaxTW / 2];
+  __shared__ int sAct[kMaxTW / 2], sPos[kMaxTW / 2];
+  __shared__ int4 sPair[kMaxTW / 2];    // (p, q, c, s) of every pair slot of the round
+  __shared__ int sWarpCnt[(kMaxTW / 2 + 31) / 32];
+  __shared__ int sNa[2];
   __shared__ int sFlag;
   __shared__ double sTau;
 
@@ -393,12 +396,15 @@ static __device__ void eig_wide_body(Bufs b, int flags, cudaGraphConditionalHand
   const float eps2 = eps * eps;
   int max_sweeps = (cold || (flags & EF_FULL)) ? ctrl->cold_sweeps : ctrl->warm_sweeps;
   if (max_sweeps > kWideLogSweeps) max_sweeps = kWideLogSweeps;
-  const int nblk = K * (K + 1) / 2;
   int sweeps = 0, rounds_run = 0;
-  // Rotations are logged (round number, K (c, s) pairs) to the workspace and
-  // applied to V after the sweeps, with V staged in shared memory.
-  float2* log_cs = b.rot_log;
-  int* log_rnd = b.rot_rnd;
+  // Each round's rotated pairs are logged (round number, count, slots and
+  // (c, s)) to the workspace and applied to V after the sweeps, with V staged
+  // in shared memory.
+  float2* log_cs = b.rot_log;   // (c, s) of every rotated pair, round after round
+  int* log_k = b.rot_k;          // its pair slot in the round
+  int* log_rnd = b.rot_rnd;      // per logged round: round number, rotated pairs
+  const int KW = (K + 31) / 32;  // warps covering the pair slots
+  int logged = 0;                // entries logged so far
   while (sweeps < max_sweeps) {
     int need = 0;
     for (int i = tid; i < Te * Te; i += nthr) {
@@ -429,36 +435,67 @@ static __device__ void eig_wide_body(Bufs b, int flags, cudaGraphConditionalHand
           dp = app - t * apq;
           dq = aqq + t * apq;
         }
-        sP[tid] = p;
-        sQ[tid] = q;
         sC[tid] = c;
         sSn[tid] = s;
         sDp[tid] = dp;
         sDq[tid] = dq;
+        sPair[tid] = make_int4(p, q, __float_as_int(c), __float_as_int(s));
       }
-      if (!__syncthreads_or(act)) continue;
-      if (tid < K) log_cs[(size_t)rounds_run * K + tid] = make_float2(sC[tid], sSn[tid]);
-      if (tid == 0) log_rnd[rounds_run] = rnd;
+      // compact list of the rotated pairs (ballot per warp, then prefix)
+      unsigned bal = 0u;
+      if (tid < 32 * KW) {
+        bal = __ballot_sync(0xffffffffu, act);
+        if ((tid & 31) == 0) sWarpCnt[tid >> 5] = __popc(bal);
+      }
+      __syncthreads();
+      int na = 0, off = 0;
+      for (int wq = 0; wq < KW; ++wq) {
+        if (wq < (tid >> 5)) off += sWarpCnt[wq];
+        na += sWarpCnt[wq];
+      }
+      if (na == 0) {  // (uniform: every thread read the same counts)
+        __syncthreads();  // the counts are read before the next round rewrites them
+        continue;
+      }
+      if (tid < K) sPos[tid] = -1;
+      __syncthreads();
+      if (act) {
+        off += __popc(bal & ((1u << (tid & 31)) - 1u));
+        sAct[off] = tid;
+        sPos[tid] = off;
+        log_k[logged + off] = tid;
+        log_cs[logged + off] = make_float2(sC[tid], sSn[tid]);
+      }
+      if (tid == 0) {
+        log_rnd[2 * rounds_run] = rnd;
+        log_rnd[2 * rounds_run + 1] = na;
+      }
+      logged += na;
       ++rounds_run;
-      // ---- phase B: G <- J^T G J by 2 x 2 pair blocks, in place ----
-      for (int bidx = tid; bidx < nblk; bidx += nthr) {
-        int A, C;
-        tri_coords(bidx, K, A, C);
-        const float sA = sSn[A];
-        if (A == C) {
-          if (sA != 0.f) {
-            const int pA = sP[A], qA = sQ[A];
-            G[pA * LD + pA] = sDp[A];
-            G[qA * LD + qA] = sDq[A];
-            G[pA * LD + qA] = 0.f;
-            G[qA * LD + pA] = 0.f;
-          }
+      __syncthreads();
+      // ---- phase B: G <- J^T G J on every 2 x 2 block of pairs that holds a
+      //      rotated pair (a block of two rotated pairs once), in place ----
+      // warp w takes rotated pairs w, w + 32, ...; lane l takes partner pairs
+      // l, l + 32, ... (the rotated pair's values are read once per warp row;
+      // a partner's (p, q, c, s) is one 16-byte load)
+      for (int ai = tid >> 5; ai < na; ai += nthr / 32) {
+        const int A = sAct[ai];
+        const int4 pa4 = sPair[A];
+        const int pA = pa4.x, qA = pa4.y;
+        const float cA = __int_as_float(pa4.z), sA = __int_as_float(pa4.w);
+        for (int C = tid & 31; C < K; C += 32) {
+        if (C == A) {
+          G[pA * LD + pA] = sDp[A];
+          G[qA * LD + qA] = sDq[A];
+          G[pA * LD + qA] = 0.f;
+          G[qA * LD + pA] = 0.f;
           continue;
         }
-        const float sC_ = sSn[C];
-        if (sA == 0.f && sC_ == 0.f) continue;  // neither pair rotated: block unchanged
-        const int pA = sP[A], qA = sQ[A], pC = sP[C], qC = sQ[C];
-        const float cA = sC[A], cC = sC[C];
+        const int pc = sPos[C];
+        if (pc >= 0 && pc < ai) continue;  // the block of two rotated pairs belongs to the earlier one
+        const int4 pc4 = sPair[C];
+        const int pC = pc4.x, qC = pc4.y;
+        const float cC = __int_as_float(pc4.z), sC_ = __int_as_float(pc4.w);
         const float g00 = G[pA * LD + pC], g01 = G[pA * LD + qC];
         const float g10 = G[qA * LD + pC], g11 = G[qA * LD + qC];
         // columns of J for the pair: p -> (c, -s), q -> (s, c)
@@ -474,6 +511,7 @@ static __device__ void eig_wide_body(Bufs b, int flags, cudaGraphConditionalHand
         G[pC * LD + qA] = n10;
         G[qA * LD + qC] = n11;
         G[qC * LD + qA] = n11;
+        }
       }
       __syncthreads();
     }
@@ -488,46 +526,68 @@ static __device__ void eig_wide_body(Bufs b, int flags, cudaGraphConditionalHand
   //      are relative to small entries; then V <- V + V D ----
   float* D = G;  // [T][LD]
   for (int i = tid; i < T * LD; i += nthr) D[i] = 0.f;
-  if (rounds_run > 0) {
-    if (tid < K) {
-      sCS[0][tid] = __ldcg(&log_cs[tid]);
+  // rounds are fetched one ahead: loaded into registers at the start of a
+  // round, stored to the other shared buffer at its end
+  int lbase = 0;
+  auto fetch = [&](int lr, int base, float4& cs, int2& pq, int& n) {
+    n = __ldcg(&log_rnd[2 * lr + 1]);
+    if (tid < n) {
+      const float2 v = __ldcg(&log_cs[base + tid]);
+      cs = make_float4(v.x, v.y, -v.y * v.y / (1.f + v.x), 0.f);   // c - 1 = -s^2 / (1 + c)
       int pa, pb;
-      rr_pair(__ldcg(&log_rnd[0]), tid, Te, pa, pb);
-      sPQ[0][tid] = make_int2(min(pa, pb), max(pa, pb));
+      rr_pair(__ldcg(&log_rnd[2 * lr]), __ldcg(&log_k[base + tid]), Te, pa, pb);
+      pq = make_int2(min(pa, pb), max(pa, pb));
     }
+  };
+  if (rounds_run > 0) {
+    float4 cs;
+    int2 pq;
+    int n;
+    fetch(0, 0, cs, pq, n);
+    if (tid < n) {
+      sCS[0][tid] = cs;
+      sPQ[0][tid] = pq;
+    }
+    if (tid == 0) sNa[0] = n;
   }
   __syncthreads();
   for (int lr = 0; lr < rounds_run; ++lr) {
     const int cb = lr & 1;
-    // the next round's rotations and pairs, fetched while this one is applied
-    if (lr + 1 < rounds_run && tid < K) {
-      sCS[cb ^ 1][tid] = __ldcg(&log_cs[(size_t)(lr + 1) * K + tid]);
-      int pa, pb;
-      rr_pair(__ldcg(&log_rnd[lr + 1]), tid, Te, pa, pb);
-      sPQ[cb ^ 1][tid] = make_int2(min(pa, pb), max(pa, pb));
-    }
-    // warp w takes rows w, w + 32, ...; lane l takes pairs l, l + 32, ...
-    for (int r = tid >> 5; r < T; r += nthr / 32)
-      for (int k = tid & 31; k < K; k += 32) {
-      const float2 cs = sCS[cb][k];
-      if (cs.y == 0.f) continue;
+    const int na = sNa[cb];
+    float4 ncs = make_float4(1.f, 0.f, 0.f, 0.f);
+    int2 npq = make_int2(0, 0);
+    int nn = 0;
+    if (lr + 1 < rounds_run) fetch(lr + 1, lbase + na, ncs, npq, nn);
+    // lane l takes rotations l, l + 32, ... (read once), warp w rows w, w + 32, ...
+    for (int k = tid & 31; k < na; k += 32) {
+      const float4 cs = sCS[cb][k];
       const int2 pq = sPQ[cb][k];
       if (pq.y >= T) continue;
-      // Q' = Q J  <=>  D' = D J + (J - I), with c - 1 = -s^2 / (1 + c)
-      const float c = cs.x, sn = cs.y, cm1 = -sn * sn / (1.f + c);
-      float* dr = &D[r * LD];
-      const float dp = dr[pq.x], dq = dr[pq.y];
-      float np = fmaf(c, dp, -sn * dq), nq = fmaf(sn, dp, c * dq);
-      if (r == pq.x) {
-        np += cm1;
-        nq += sn;
-      } else if (r == pq.y) {
-        np -= sn;
-        nq += cm1;
+      // Q' = Q J  <=>  D' = D J + (J - I)
+      const float c = cs.x, sn = cs.y, cm1 = cs.z;
+      for (int r = tid >> 5; r < T; r += nthr / 32) {
+        float* dr = &D[r * LD];
+        const float dp = dr[pq.x], dq = dr[pq.y];
+        float np = fmaf(c, dp, -sn * dq), nq = fmaf(sn, dp, c * dq);
+        if (r == pq.x) {
+          np += cm1;
+          nq += sn;
+        } else if (r == pq.y) {
+          np -= sn;
+          nq += cm1;
+        }
+        dr[pq.x] = np;
+        dr[pq.y] = nq;
       }
-      dr[pq.x] = np;
-      dr[pq.y] = nq;
+    }
+    if (lr + 1 < rounds_run) {
+      if (tid < nn) {
+        sCS[cb ^ 1][tid] = ncs;
+        sPQ[cb ^ 1][tid] = npq;
       }
+      if (tid == 0) sNa[cb ^ 1] = nn;
+    }
+    lbase += na;
     __syncthreads();
   }
   // V <- V + V D, vrows rows of V at a time staged after D
