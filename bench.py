@@ -168,9 +168,9 @@ def launches_per_solve(drive: str, iters: int) -> int:
     return 4 + 4 * iters      # host: update pass, check, gram pass, eig per iteration
 
 
-def window(seed: int):
+def window(seed: int, workload: str = WORKLOAD, complex_iq: bool = False):
     from paper_2506_10257_gb300 import synth
-    return synth.make_preset(WORKLOAD, seed=seed)
+    return synth.make_preset(workload, seed=seed, complex_iq=complex_iq)
 
 
 def run_reference(args):
@@ -276,10 +276,11 @@ def _cpu_baseline(line, w, L, S, mask, theta, res_iters):
     t0 = time.perf_counter()
     ref = O.rpca_frames(w.frames)
     dt = time.perf_counter() - t0
-    Lg, Sg = L.cpu().numpy().astype(np.float64), S.cpu().numpy().astype(np.float64)
+    cdt = np.complex128 if np.iscomplexobj(w.frames) else np.float64
+    Lg, Sg = L.cpu().numpy().astype(cdt), S.cpu().numpy().astype(cdt)
     mask_ref = O.bound_mask(O.temporal_mean_abs(ref.L), theta)
     line["cpu_baseline"] = {"value": 1.0 / dt, "unit": "solves/s", "cores": n, "kind": "oracle",
-                            "sample": "one full 262144x20 solve of window 0 (FP64, LAPACK SVD)",
+                            "sample": f"one full {w.m}x{w.T} solve of window 0 (FP64, LAPACK SVD)",
                             "iters": ref.iters}
     line["parity"] = {"window": 0, "errL": float(np.linalg.norm(Lg - ref.L) / np.linalg.norm(ref.L)),
                       "errS": float(np.linalg.norm(Sg - ref.S) / np.linalg.norm(ref.S)),
@@ -703,13 +704,14 @@ def run_ours(args):
     import torch
     rpca, rank, local_rank, world = _setup(args)
 
-    w = window(1 + 1000 * rank)
+    wl = args.workload if args.workload.startswith("w") else WORKLOAD
+    w = window(1 + 1000 * rank, wl, args.complex)
     T, m = w.frames.shape
     X = torch.from_numpy(w.frames).cuda()
     prec = {"fp32": rpca.PREC_FP32, "tf32x3": rpca.PREC_TF32X3, "bf16x3": rpca.PREC_BF16X3,
             "tf32": rpca.PREC_TF32}[args.precision]
     drive = {"graph": rpca.DRIVE_GRAPH, "stream": rpca.DRIVE_STREAM, "host": rpca.DRIVE_HOST}[args.drive]
-    plan = rpca.Plan(m, T, precision=prec, drive=drive)
+    plan = rpca.Plan(m, T, precision=prec, drive=drive, dtype=rpca.C64 if args.complex else rpca.R32)
     L = torch.empty_like(X)
     S = torch.empty_like(X)
     theta = _theta(w)
@@ -726,9 +728,10 @@ def run_ours(args):
     value = world * args.steps / (total_ms * 1e-3)
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    edt = torch.complex64 if args.complex else torch.float32
     Xh = torch.from_numpy(w.frames).pin_memory().numpy()
-    Lh = torch.empty((T, m), dtype=torch.float32).pin_memory().numpy()
-    Sh = torch.empty((T, m), dtype=torch.float32).pin_memory().numpy()
+    Lh = torch.empty((T, m), dtype=edt).pin_memory().numpy()
+    Sh = torch.empty((T, m), dtype=edt).pin_memory().numpy()
     Mh = torch.empty(m, dtype=torch.uint8).pin_memory().numpy()
     plan.solve_host(Xh, Lh, Sh, mask=Mh, theta=theta)
     e2e_steps = max(3, args.steps // 2)
@@ -741,15 +744,16 @@ def run_ours(args):
     e2e_val = world * e2e_steps / e2e_s
 
     # roofline of the dominant kernel (the fused per-iteration pass), device-timer durations
-    alg_bytes = 5 * m * T * 4                    # read X, S, Y; write S, Y
+    esz = 8 if args.complex else 4
+    alg_bytes = 5 * m * T * esz                  # read X, S, Y; write S, Y
     pass_us = res["pass_us"]
     src_hash = kernel_source_hash()
     line = {
         "metric": "solves/s", "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic (seeded microbubble window, in HBM)",
-        "config": {"workload": WORKLOAD + " (512x512 px x 20 frames, Casorati 262144x20, fp32)",
+        "dtype": "c64" if args.complex else "f32", "data": "synthetic (seeded microbubble window, in HBM)",
+        "config": {"workload": f"{wl} (Casorati {m}x{T}, {'complex64 IQ' if args.complex else 'fp32'})",
                    "form": "plan: one solve per step",
                    "precision": args.precision,
                    "drive": {"graph": "cuda-graph device loop", "stream": "kernels launched one by one",
@@ -762,11 +766,12 @@ def run_ours(args):
         "kernel_us": {"pass": pass_us, "eig": res["eig_us"], "init": res["init_us"],
                       "eig_split": {k: round(v, 3) for k, v in plan.timings().items()}},
         "gpu_launches": args.steps * launches_per_solve(args.drive, res["iters"]),
-        "roofline": _roofline(alg_bytes, pass_us * 1e-6, "pass_kernel<20,FUSED>",
+        "roofline": _roofline(alg_bytes, pass_us * 1e-6,
+                              "pass_kernel<20,FUSED>" if (T <= 32 and not args.complex) else "pass_wide_kernel (FUSED)",
                               "device global timer per launch over the timed solves",
                               traffic=ncu_traffic(src_hash)),
-        "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": m * T * 4,
-                "d2h_bytes_per_step": 2 * m * T * 4 + m + 48, "steps": e2e_steps},
+        "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": m * T * esz,
+                "d2h_bytes_per_step": 2 * m * T * esz + m + 48, "steps": e2e_steps},
         "clocks": clocks,
         "kernel_source_sha256": src_hash,
     }
@@ -793,8 +798,10 @@ def main():
     ap.add_argument("--windows", type=int, default=8, help="windows per step (batch, serve)")
     ap.add_argument("--slots", type=int, default=4, help="server slots (serve)")
     ap.add_argument("--tune", action="store_true", help="autotune the batch schedule first")
-    ap.add_argument("--workload", choices=["w512x512_t20", "uneven", "probes8"], default="w512x512_t20",
-                    help="uneven: the uneven batch (with --form batch); probes8: served streaming (with --form serve)")
+    ap.add_argument("--workload", default="w512x512_t20",
+                    help="a synth preset (plan form: w512x512_t10/20/50/100, w338x260_t20/60/132, ...); "
+                         "uneven: the uneven batch; probes8: served streaming")
+    ap.add_argument("--complex", action="store_true", help="complex64 IQ window (plan form)")
     ap.add_argument("--duration", type=float, default=1.0, help="seconds of simulated streaming (probes8)")
     ap.add_argument("--cold", action="store_true", help="served streaming without warm start")
     ap.add_argument("--cold-every", type=int, default=0, help="served streaming: every n-th window cold")
