@@ -124,7 +124,9 @@ Layout make_layout(int64_t m, int T, int sms, bool wide) {
   grid = std::min<int64_t>(grid, (int64_t)kGroup * kMaxGroups);
   L.grid = (int)std::max<int64_t>(grid, 1);
   L.ws_grid = (int)std::max<int64_t>(std::min<int64_t>((m + 127) / 128, std::max(sms, 1)), 1);
-  L.wide_grid = (int)std::max<int64_t>(std::min<int64_t>((m + 31) / 32, std::max(sms, 1)), 1);
+  int wtile = 32, wper = 1;
+  if (wide) wide_launch_shape(T, &wtile, &wper);
+  L.wide_grid = (int)std::max<int64_t>(std::min<int64_t>((m + wtile - 1) / wtile, (int64_t)std::max(sms, 1) * wper), 1);
   const int maxgrid = std::max({L.grid, L.ws_grid, wide ? L.wide_grid : 1});
   L.ngroups = (maxgrid + kGroup - 1) / kGroup;
   size_t off = 0;

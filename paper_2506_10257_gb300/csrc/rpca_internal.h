@@ -24,6 +24,7 @@ struct WideKernels {
   size_t pass_smem;
   int pass_threads;
   int tile;             // pixels per tile
+  int per_sm;           // CTAs of a pass resident per SM
   void* eig;            // (Bufs, flags, handle, use_cond)
   size_t eig_smem;
   int eig_threads;
@@ -33,6 +34,9 @@ struct WideKernels {
 // false when T is not a wide column count (real T <= kMaxT unless force) or a
 // kernel attribute cannot be set.
 bool wide_kernels(int T, bool cplx, bool force, WideKernels* out);
+
+// Pixels per tile and CTAs per SM of the tiled pass for T real columns.
+void wide_launch_shape(int T, int* tile, int* per_sm);
 
 // rpca_plan_create with the tiled path forced for any frame count (the
 // batched form runs every window of a batch that holds a wide or complex

@@ -8,17 +8,37 @@ namespace rpca {
 
 template <int CW, bool CPLX>
 WideKernels make_wide() {
+  constexpr int TP = 8 * CW;
   WideKernels k;
-  k.pass[PM_INIT] = (void*)pass_wide_kernel<CW, PM_INIT, CPLX>;
-  k.pass[PM_FUSED] = (void*)pass_wide_kernel<CW, PM_FUSED, CPLX>;
-  k.pass[PM_UPDATE] = (void*)pass_wide_kernel<CW, PM_UPDATE, CPLX>;
-  k.pass[PM_GRAM] = (void*)pass_wide_kernel<CW, PM_GRAM, CPLX>;
-  k.pass_smem = WideShape<CW>::smem;
+  if constexpr (TP <= 128) {
+    // Wbar and V resident in shared memory, 64-pixel tiles
+    k.pass[PM_INIT] = (void*)pass_res_kernel<TP, PM_INIT, CPLX>;
+    k.pass[PM_FUSED] = (void*)pass_res_kernel<TP, PM_FUSED, CPLX>;
+    k.pass[PM_UPDATE] = (void*)pass_res_kernel<TP, PM_UPDATE, CPLX>;
+    k.pass[PM_GRAM] = (void*)pass_res_kernel<TP, PM_GRAM, CPLX>;
+    k.pass_smem = res_pass_smem_bytes(TP);
+    k.tile = kRP;
+    k.per_sm = res_blocks_per_sm(TP);
+  } else {
+    // Wbar and V streamed 32 rows at a time, 32-pixel tiles
+    k.pass[PM_INIT] = (void*)pass_wide_kernel<CW, PM_INIT, CPLX>;
+    k.pass[PM_FUSED] = (void*)pass_wide_kernel<CW, PM_FUSED, CPLX>;
+    k.pass[PM_UPDATE] = (void*)pass_wide_kernel<CW, PM_UPDATE, CPLX>;
+    k.pass[PM_GRAM] = (void*)pass_wide_kernel<CW, PM_GRAM, CPLX>;
+    k.pass_smem = WideShape<CW>::smem;
+    k.tile = kWP;
+    k.per_sm = 1;
+  }
   k.pass_threads = kWideThreads;
-  k.tile = kWP;
   k.eig = (void*)eig_wide_kernel;
   k.eig_threads = kEigWThreads;
   return k;
+}
+
+void wide_launch_shape(int T, int* tile, int* per_sm) {
+  const int TP = (T + 31) / 32 * 32;
+  *tile = TP <= 128 ? kRP : kWP;
+  *per_sm = TP <= 128 ? res_blocks_per_sm(TP) : 1;
 }
 
 template <bool CPLX>

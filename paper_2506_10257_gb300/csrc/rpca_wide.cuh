@@ -349,6 +349,328 @@ __global__ void __launch_bounds__(kWideThreads, 1) pass_wide_kernel(Bufs b) {
 }
 
 // ---------------------------------------------------------------------------
+// Tiled pass with Wbar and V resident in shared memory (TP <= 128 columns).
+// Tiles of 64 pixels; thread (tx, ty) of a 16 x 16 grid owns 4 pixels x TP/16
+// columns of both contractions (register-blocked: per k one 16-byte load of
+// Z and TP/16 values of Wbar or V feed 4 TP/16 FMAs).  The tile holds Z (in
+// place of X), S and Y/mu; Z' = Z - Y/mu - Q + clip(R) + Y'/mu' needs no X.
+// ---------------------------------------------------------------------------
+constexpr int kRP = 64;   // pixels per tile
+
+template <int TP, bool CPLX>
+struct ResShape {
+  static constexpr int CPT = TP / 16;                     // columns per thread
+  static constexpr int NR = CPLX ? 2 * kRP : kRP;         // Gram rows per tile
+  static constexpr int UP = CPLX ? TP : TP + 4;           // U row stride
+  static constexpr int NB = TP / 4;
+  static constexpr int NBLK = NB * (NB + 1) / 2;
+  static constexpr int BPT = (NBLK + kWideThreads - 1) / kWideThreads;
+  static constexpr size_t floats = 2 * (size_t)TP * TP + 3 * (size_t)TP * kRP;
+  static constexpr size_t smem = sizeof(float) * floats;
+  static_assert(TP % 32 == 0 && TP <= 128, "resident tiles need TP in {32, 64, 96, 128}");
+  static_assert((size_t)NR * UP <= 2 * (size_t)TP * kRP, "U must fit over the S and Y/mu tiles");
+};
+
+__host__ __device__ constexpr size_t res_pass_smem_bytes(int TP) {
+  return sizeof(float) * (2 * (size_t)TP * TP + 3 * (size_t)TP * kRP);
+}
+
+// acc[i][j] = sum_k zrow(k)[i] * M[k][c0 + j], 4 pixels i, CPT columns j
+template <int TP, typename ZF>
+__device__ __forceinline__ void res_times(float (&acc)[4][TP / 16], const float* sM, int T, int c0, ZF zrow) {
+  constexpr int CPT = TP / 16;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) acc[i][j] = 0.f;
+  for (int k = 0; k < T; ++k) {
+    const float4 z = zrow(k);
+    const float2* wr = reinterpret_cast<const float2*>(&sM[k * TP + c0]);
+    float w[CPT];
+#pragma unroll
+    for (int j2 = 0; j2 < CPT / 2; ++j2) {
+      const float2 v = wr[j2];
+      w[2 * j2] = v.x;
+      w[2 * j2 + 1] = v.y;
+    }
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) {
+      acc[0][j] = fmaf(z.x, w[j], acc[0][j]);
+      acc[1][j] = fmaf(z.y, w[j], acc[1][j]);
+      acc[2][j] = fmaf(z.z, w[j], acc[2][j]);
+      acc[3][j] = fmaf(z.w, w[j], acc[3][j]);
+    }
+  }
+}
+
+template <int TP, int MODE, bool CPLX>
+__device__ bool pass_res_body(Bufs b, int lc, int nc, float* smem) {
+  using RS = ResShape<TP, CPLX>;
+  constexpr int CPT = RS::CPT;
+  constexpr int UP = RS::UP;
+  constexpr bool kGram = (MODE != PM_UPDATE);
+  float* sW = smem;                    // Wbar [TP][TP]
+  float* sV = sW + TP * TP;            // V [TP][TP]
+  float* sZ = sV + TP * TP;            // [TP][kRP]: X, then Z, then Z'
+  float* sS = sZ + TP * kRP;           // [TP][kRP]
+  float* sD = sS + TP * kRP;           // [TP][kRP]: Y / mu
+  float* sU = sS;                      // [NR][UP], over S and Y/mu once they are used
+  __shared__ double sRed[2][kWideThreads / 32];
+  __shared__ double sScal[2 * kMaxGroups];
+  __shared__ int sLast;
+
+  const Ctrl* ctrl = b.ctrl;
+  if (__ldcg(&ctrl->done)) return false;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int tx = tid & 15, ty = tid >> 4;     // column group, pixel group
+  const int c0 = tx * CPT, p0 = 4 * ty;
+  if (tid == 0) atomicMin(&b.red->t_start, gtimer());
+  const int T = b.T;
+  const int64_t m = b.m;
+  const Job job = *b.job;
+  const int kc = __ldcg(&ctrl->k);
+  const bool first = (kc == 0) && !__ldcg(&ctrl->warm);
+  const float f_mu = __ldcg(&ctrl->f_mu), inv_mu = __ldcg(&ctrl->f_inv_mu), gamma = __ldcg(&ctrl->f_gamma);
+  const float inv_mu_nxt = __ldcg(&ctrl->f_inv_mu_nxt);
+  const float* Yin = (kc & 1) ? job.Y1 : job.Y0;
+  float* Yout = (kc & 1) ? job.Y0 : job.Y1;
+
+  // Wbar and V resident for the whole pass (zero outside T x T)
+  if (MODE != PM_INIT) {
+    for (int i = tid; i < TP * TP; i += kWideThreads) {
+      const int r = i / TP, c = i % TP;
+      const bool in = r < T && c < T;
+      sW[i] = in ? __ldcg(&b.Ww[r * T + c]) : 0.f;
+      sV[i] = in ? __ldcg(&b.Vw[r * T + c]) : 0.f;
+    }
+  }
+
+  int gbi[RS::BPT], gbj[RS::BPT];
+  float gacc[RS::BPT][16];
+#pragma unroll
+  for (int u = 0; u < RS::BPT; ++u) {
+    const int blk = tid + u * kWideThreads;
+    gbi[u] = gbj[u] = -1;
+    if (blk < RS::NBLK) blk_coords(blk, RS::NB, gbi[u], gbj[u]);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) gacc[u][i] = 0.f;
+  }
+  float e2 = 0.f, l1 = 0.f;
+
+  const int64_t ntiles = (m + kRP - 1) / kRP;
+  for (int64_t tile = lc; tile < ntiles; tile += nc) {
+    const int64_t pb = tile * kRP;
+    __syncthreads();  // the previous tile (and the resident matrices) are ready / consumed
+    // ---- 1. stage: warp w takes frames w, w + 8, ...; lane l pixels l, l + 32 ----
+    if constexpr (CPLX) {
+      const float2* X2 = reinterpret_cast<const float2*>(job.X);
+      const float2* S2 = reinterpret_cast<const float2*>(job.S);
+      const float2* Y2 = reinterpret_cast<const float2*>(Yin);
+      for (int f = w; f < TP / 2; f += 8) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int pp = lane + 32 * h;
+          const bool in = (pb + pp < m) && 2 * f < T;
+          const int64_t gi = (int64_t)f * m + pb + pp;
+          const float2 x = in ? X2[gi] : make_float2(0.f, 0.f);
+          if (MODE == PM_INIT) {
+            sZ[(2 * f) * kRP + pp] = x.x;
+            sZ[(2 * f + 1) * kRP + pp] = x.y;
+            const float a2 = fmaf(x.x, x.x, x.y * x.y);
+            e2 += a2;
+            l1 += sqrtf(a2);
+          } else {
+            const float2 sv = (in && !first) ? S2[gi] : make_float2(0.f, 0.f);
+            const float2 yv = (in && !first) ? Y2[gi] : make_float2(0.f, 0.f);
+            sZ[(2 * f) * kRP + pp] = form_z(x.x, sv.x, yv.x, inv_mu);
+            sZ[(2 * f + 1) * kRP + pp] = form_z(x.y, sv.y, yv.y, inv_mu);
+            sS[(2 * f) * kRP + pp] = sv.x;
+            sS[(2 * f + 1) * kRP + pp] = sv.y;
+            sD[(2 * f) * kRP + pp] = yv.x * inv_mu;
+            sD[(2 * f + 1) * kRP + pp] = yv.y * inv_mu;
+          }
+        }
+      }
+    } else {
+      for (int t = w; t < TP; t += 8) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int pp = lane + 32 * h;
+          const bool in = (pb + pp < m) && t < T;
+          const int64_t gi = (int64_t)t * m + pb + pp;
+          const float x = in ? job.X[gi] : 0.f;
+          if (MODE == PM_INIT) {
+            sZ[t * kRP + pp] = x;
+            e2 = fmaf(x, x, e2);
+            l1 += fabsf(x);
+          } else {
+            const float sv = (in && !first) ? job.S[gi] : 0.f;
+            const float yv = (in && !first) ? Yin[gi] : 0.f;
+            sZ[t * kRP + pp] = form_z(x, sv, yv, inv_mu);
+            sS[t * kRP + pp] = sv;
+            sD[t * kRP + pp] = yv * inv_mu;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    auto zrow = [&](int k) { return *reinterpret_cast<const float4*>(&sZ[k * kRP + p0]); };
+    auto zrow_i = [&](int k) {  // rows of i Z (complex): (-Im, Re) per frame
+      const float4 v = (k & 1) ? *reinterpret_cast<const float4*>(&sZ[(k - 1) * kRP + p0])
+                               : *reinterpret_cast<const float4*>(&sZ[(k + 1) * kRP + p0]);
+      return (k & 1) ? v : make_float4(-v.x, -v.y, -v.z, -v.w);
+    };
+    if (MODE == PM_INIT) {
+      // U = X (standard basis), pixel-major; complex: also the rows of i X
+      for (int i = tid; i < TP * kRP; i += kWideThreads) {
+        const int t = i / kRP, pp = i % kRP;
+        sU[pp * UP + t] = sZ[t * kRP + pp];
+        if (CPLX) sU[(kRP + pp) * UP + t] = (t & 1) ? sZ[(t - 1) * kRP + pp] : -sZ[(t + 1) * kRP + pp];
+      }
+    } else {
+      if (MODE != PM_GRAM) {
+        // ---- 2. Q = Z Wbar ----
+        float q[4][CPT];
+        res_times<TP>(q, sW, T, c0, zrow);
+        __syncthreads();  // every thread has read Z before Z' replaces it
+        // ---- 3. Eq. 5-6 for (4 pixels, CPT columns) ----
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int pp = p0 + i;
+          const bool valid = pb + pp < m;
+          if constexpr (CPLX) {
+            float2* S2 = reinterpret_cast<float2*>(job.S);
+            float2* Yo2 = reinterpret_cast<float2*>(Yout);
+#pragma unroll
+            for (int j = 0; j < CPT; j += 2) {
+              const int t = c0 + j;
+              if (t < T) {
+                const float zr = sZ[t * kRP + pp], zi = sZ[(t + 1) * kRP + pp];
+                const float sr = sS[t * kRP + pp], si = sS[(t + 1) * kRP + pp];
+                const float dr = sD[t * kRP + pp], di = sD[(t + 1) * kRP + pp];
+                const float rr = sr + q[i][j], ri = si + q[i][j + 1];
+                const float mag = sqrtf(fmaf(rr, rr, ri * ri));
+                const float f = (mag > gamma) ? gamma / mag : 1.f;
+                const float cr = rr * f, ci = ri * f;
+                const float ynr = f_mu * cr, yni = f_mu * ci;
+                const float er = cr - dr, ei = ci - di;
+                e2 = fmaf(er, er, fmaf(ei, ei, e2));
+                if (valid) {
+                  S2[(int64_t)(t >> 1) * m + pb + pp] = make_float2(rr - cr, ri - ci);
+                  Yo2[(int64_t)(t >> 1) * m + pb + pp] = make_float2(ynr, yni);
+                }
+                sZ[t * kRP + pp] = valid ? ((zr - dr) - q[i][j]) + cr + ynr * inv_mu_nxt : 0.f;
+                sZ[(t + 1) * kRP + pp] = valid ? ((zi - di) - q[i][j + 1]) + ci + yni * inv_mu_nxt : 0.f;
+              }
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) {
+              const int t = c0 + j;
+              if (t < T) {
+                const float z = sZ[t * kRP + pp], sv = sS[t * kRP + pp], d = sD[t * kRP + pp];
+                const float r = sv + q[i][j];                      // X - L + Y/mu
+                const float c = fminf(fmaxf(r, -gamma), gamma);    // clip to +-lambda/mu
+                const float yn = f_mu * c;                         // Eq. 6
+                const float e = c - d;                             // X - L - S'
+                e2 = fmaf(e, e, e2);
+                if (valid) {
+                  job.S[(int64_t)t * m + pb + pp] = r - c;         // Eq. 5
+                  Yout[(int64_t)t * m + pb + pp] = yn;
+                }
+                // Z' = X - S' + Y'/mu' with X = Z + S - Y/mu and S' = S + Q - clip
+                sZ[t * kRP + pp] = valid ? ((z - d) - q[i][j]) + c + yn * inv_mu_nxt : 0.f;
+              }
+            }
+          }
+        }
+        __syncthreads();  // Z' complete; S, Y/mu are free for U
+      }
+      if (kGram) {
+        // ---- 4. U = Z' V (complex: and (i Z') V), pixel-major ----
+        float u[4][CPT];
+        res_times<TP>(u, sV, T, c0, zrow);
+        if (MODE == PM_GRAM) __syncthreads();  // (no update phase: S, Y/mu read up to here)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < CPT; ++j) sU[(p0 + i) * UP + c0 + j] = u[i][j];
+        if constexpr (CPLX) {
+          res_times<TP>(u, sV, T, c0, zrow_i);
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) sU[(kRP + p0 + i) * UP + c0 + j] = u[i][j];
+        }
+      }
+    }
+    if (kGram) {
+      __syncthreads();
+      // ---- 5. partial Gram U^T U (upper 4 x 4 blocks) ----
+#pragma unroll
+      for (int uu = 0; uu < RS::BPT; ++uu) {
+        if (gbi[uu] < 0) continue;
+        const int bi = gbi[uu], bj = gbj[uu];
+        for (int pp = 0; pp < RS::NR; ++pp) {
+          const float4 a = *reinterpret_cast<const float4*>(&sU[pp * UP + 4 * bi]);
+          const float4 c = *reinterpret_cast<const float4*>(&sU[pp * UP + 4 * bj]);
+          const float av[4] = {a.x, a.y, a.z, a.w};
+          const float cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) gacc[uu][i * 4 + j] = fmaf(av[i], cv[j], gacc[uu][i * 4 + j]);
+        }
+      }
+    }
+  }
+
+  // ---- CTA partials ----
+  const int TT = T * T;
+  if (kGram) {
+#pragma unroll
+    for (int uu = 0; uu < RS::BPT; ++uu) {
+      if (gbi[uu] < 0) continue;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int a = 4 * gbi[uu] + i / 4, c = 4 * gbj[uu] + i % 4;
+        if (a < T && c < T && a <= c) {
+          b.gram_part[(int64_t)lc * TT + a * T + c] = gacc[uu][i];
+          b.gram_part[(int64_t)lc * TT + c * T + a] = gacc[uu][i];
+        }
+      }
+    }
+  }
+  {
+    const double v0 = warp_sum_d((double)e2), v1 = warp_sum_d((double)l1);
+    if (lane == 0) {
+      sRed[0][w] = v0;
+      sRed[1][w] = v1;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double s0 = 0, s1 = 0;
+      for (int i = 0; i < kWideThreads / 32; ++i) {
+        s0 += sRed[0][i];
+        s1 += sRed[1][i];
+      }
+      b.scal_part[2 * lc] = s0;
+      b.scal_part[2 * lc + 1] = s1;
+    }
+  }
+  return cross_cta_reduce<4>(b, kGram, sScal, &sLast, lc, nc);
+}
+
+// CTAs per SM: two below 64 columns (128 registers a thread), else one.
+__host__ __device__ constexpr int res_blocks_per_sm(int TP) { return TP <= 64 ? 2 : 1; }
+
+template <int TP, int MODE, bool CPLX>
+__global__ void __launch_bounds__(kWideThreads, res_blocks_per_sm(TP)) pass_res_kernel(Bufs b) {
+  extern __shared__ __align__(16) float res_smem[];
+  pass_res_body<TP, MODE, CPLX>(b, blockIdx.x, gridDim.x, res_smem);
+}
+
+// ---------------------------------------------------------------------------
 // Eigen-step for wide windows (one CTA; the stand-alone kernel uses kEigWThreads threads).
 // ---------------------------------------------------------------------------
 // The eigen-step on one CTA of any multiple of 32 threads; `eigw_smem` holds
