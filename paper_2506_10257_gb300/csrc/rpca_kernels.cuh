@@ -374,16 +374,17 @@ __device__ bool pass_body(Bufs b, int lc, int nc, unsigned char* dsm) {
         l1 += fabsf(x);
       }
     } else {
-      // z = X - S + Y/mu for this pixel row (the argument of Eq. 4)
-      float x[TB], s[TB], d[TB], z[TB];
+      // z = X - S + Y/mu for this pixel row (the argument of Eq. 4); X itself
+      // is not kept (Z' below needs only Z, Y/mu, Q and the clip)
+      float s[TB], d[TB], z[TB];
 #pragma unroll
       for (int t = 0; t < TB; ++t) {
         const bool in = valid && t < T;
-        x[t] = in ? job.X[t * m + p] : 0.f;
+        const float x = in ? job.X[t * m + p] : 0.f;
         s[t] = (in && !first) ? job.S[t * m + p] : 0.f;
         const float y = (in && !first) ? Yin[t * m + p] : 0.f;
         d[t] = y * inv_mu;
-        z[t] = form_z(x[t], s[t], y, inv_mu);
+        z[t] = form_z(x, s[t], y, inv_mu);
       }
       if (MODE == PM_GRAM) {
 #pragma unroll
@@ -405,7 +406,8 @@ __device__ bool pass_body(Bufs b, int lc, int nc, unsigned char* dsm) {
               job.S[t * m + p] = sn;
               Yout[t * m + p] = yn;
             }
-            z[t] = valid ? form_z(x[t], sn, yn, inv_mu_nxt) : 0.f;
+            // Z' = X - S' + Y'/mu' with X = Z + S - Y/mu and S' = S + Q - clip
+            z[t] = valid ? ((z[t] - d[t]) - q[t]) + c + yn * inv_mu_nxt : 0.f;
           }
         }
         if (MODE == PM_FUSED) {
