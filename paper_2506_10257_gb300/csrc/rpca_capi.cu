@@ -25,6 +25,8 @@ struct KernelSet {
   size_t pass_tc_smem[4];
   void* pass_ws[4];        // the same, warp-specialised and fed by TMA (needs m % 4 == 0)
   size_t pass_ws_smem[4];
+  void* pass_fs[4];        // CUDA-core FP32 passes fed by TMA, by mode (needs m % 4 == 0)
+  size_t pass_fs_smem;
   void* eig32;       // smem Jacobi, FP32 rotations (reference form)
   void* eig64;       // smem Jacobi, FP64 rotations
   void* eig_fast;    // FP32 rotations, logged and accumulated once
@@ -41,6 +43,11 @@ KernelSet make_set() {
   k.pass[PM_UPDATE] = (void*)pass_kernel<TB, PM_UPDATE>;
   k.pass[PM_GRAM] = (void*)pass_kernel<TB, PM_GRAM>;
   k.pass_smem = pass_simt_smem<TB>();
+  k.pass_fs[PM_INIT] = (void*)pass_fs_kernel<TB, PM_INIT>;
+  k.pass_fs[PM_FUSED] = (void*)pass_fs_kernel<TB, PM_FUSED>;
+  k.pass_fs[PM_UPDATE] = (void*)pass_fs_kernel<TB, PM_UPDATE>;
+  k.pass_fs[PM_GRAM] = (void*)pass_fs_kernel<TB, PM_GRAM>;
+  k.pass_fs_smem = FsShape<TB>::SMEM;
   k.eig32 = (void*)eig_kernel<TB, float>;
   k.eig64 = (void*)eig_kernel<TB, double>;
   k.eig_fast = (void*)eig_fast_kernel<TB>;
@@ -204,6 +211,7 @@ struct rpca_plan_s {
   cudaGraphExec_t exec;
   Ctrl* ctrl_host;  // pinned
   bool use_ws;      // fused pass = warp-specialised TMA kernel
+  bool use_fs;      // FP32 passes = TMA-fed CUDA-core kernels (narrow windows, m % 4 == 0)
   // device staging of rpca_solve_host (allocated on first use)
   float* stage_x;
   float* stage_l;
@@ -270,11 +278,24 @@ static dim3 eig_block(const rpca_plan_s* pl) {
   if (pl->wide) return dim3(pl->wk.eig_threads);
   return dim3(pl->eig_fp64 ? pl->ks.eig_threads : kEigThreads);
 }
-// CUDA-core FP32 passes by mode (narrow: one pixel row per thread; wide: tiles).
-static void* pass_fn(const rpca_plan_s* pl, int mode) { return pl->wide ? pl->wk.pass[mode] : pl->ks.pass[mode]; }
-static size_t pass_smem(const rpca_plan_s* pl) { return pl->wide ? pl->wk.pass_smem : pl->ks.pass_smem; }
-static dim3 pass_grid(const rpca_plan_s* pl) { return dim3(pl->wide ? pl->lay.wide_grid : pl->lay.grid); }
-static dim3 pass_block(const rpca_plan_s* pl) { return dim3(pl->wide ? pl->wk.pass_threads : kPassThreads); }
+// CUDA-core FP32 passes by mode (narrow: one pixel row per thread, TMA-fed when
+// the plan has tensor maps; wide: tiles).
+static void* pass_fn(const rpca_plan_s* pl, int mode) {
+  if (pl->wide) return pl->wk.pass[mode];
+  return pl->use_fs ? pl->ks.pass_fs[mode] : pl->ks.pass[mode];
+}
+static size_t pass_smem(const rpca_plan_s* pl) {
+  if (pl->wide) return pl->wk.pass_smem;
+  return pl->use_fs ? pl->ks.pass_fs_smem : pl->ks.pass_smem;
+}
+static dim3 pass_grid(const rpca_plan_s* pl) {
+  if (pl->wide) return dim3(pl->lay.wide_grid);
+  return dim3(pl->use_fs ? pl->lay.ws_grid : pl->lay.grid);
+}
+static dim3 pass_block(const rpca_plan_s* pl) {
+  if (pl->wide) return dim3(pl->wk.pass_threads);
+  return dim3(pl->use_fs ? kFsThreads : kPassThreads);
+}
 // Fused per-iteration pass: CUDA-core FP32 or the tensor-core form of the plan's precision.
 static void* fused_fn(const rpca_plan_s* pl) {
   if (pl->p.precision == RPCA_PREC_FP32) return pass_fn(pl, PM_FUSED);
@@ -464,6 +485,18 @@ static rpca_status plan_create_impl(const rpca_params* p, void* workspace, size_
   }
   pl->use_ws = (p->precision != RPCA_PREC_FP32) && (p->m % 4 == 0) && tma_encoder() != nullptr &&
                !(getenv("RPCA_NO_WS") && atoi(getenv("RPCA_NO_WS")) != 0);
+  pl->use_fs = !pl->wide && (p->precision == RPCA_PREC_FP32) && (p->m % 4 == 0) && (p->m < ((int64_t)1 << 31)) &&
+               tma_encoder() != nullptr && !(getenv("RPCA_NO_FS") && atoi(getenv("RPCA_NO_FS")) != 0);
+  if (pl->use_fs) {
+    for (int i = 0; i < 4; ++i) {
+      const cudaError_t ea = cudaFuncSetAttribute(pl->ks.pass_fs[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)pl->ks.pass_fs_smem);
+      if (ea != cudaSuccess) {
+        delete pl;
+        return cuda_status(ea);
+      }
+    }
+  }
   if (p->precision != RPCA_PREC_FP32) {
     cudaError_t ea = cudaFuncSetAttribute(pl->ks.pass_tc[p->precision], cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)pl->ks.pass_tc_smem[p->precision]);
@@ -666,7 +699,7 @@ rpca_status rpca::plan_solve_ex(rpca_plan_t pl, const void* X, void* L, void* S,
   TmaMaps maps;
   memset(&maps, 0, sizeof(maps));
   int use_maps = 0;
-  if (pl->use_ws) {
+  if (pl->use_ws || pl->use_fs) {
     const float* y1 = (const float*)(pl->ws + pl->lay.ybuf);
     if (!encode_map(&maps.x, X, pl->p.m, pl->p.T) || !encode_map(&maps.s, S, pl->p.m, pl->p.T) ||
         !encode_map(&maps.y0, L, pl->p.m, pl->p.T) || !encode_map(&maps.y1, y1, pl->p.m, pl->p.T))

@@ -58,20 +58,52 @@ __device__ __forceinline__ void blk_coords(int blk, int nb, int& bi, int& bj) {
   }
 }
 
-// sum_t z[t] * w[t] with w a 16-byte aligned shared-memory row (vector loads)
+// Two FP32 lanes in one 64-bit register pair.  fma.rn.f32x2 (PTX ISA 8.6,
+// sm_100 and later) rounds each lane exactly as fmaf does, so a loop written
+// with it gives the same bits as the scalar loop with the same per-lane order,
+// in half the FMA instructions.
+__device__ __forceinline__ uint64_t f2_pack(float a, float b) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float2 f2_unpack(uint64_t v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// out[j] = sum_t z[t] M[t][j] for a TB x TB row-major shared-memory matrix M
+// (16-byte aligned rows), summed over t in increasing order.  Each step t is
+// TB/2 independent paired FMAs (z[t] times one row of M), so the steps of the
+// TB dependency chains overlap and the row loads are broadcasts.
 template <int TB>
-__device__ __forceinline__ float row_dot(const float (&z)[TB], const float* w) {
-  const float4* w4 = reinterpret_cast<const float4*>(w);
-  float a0 = 0.f, a1 = 0.f;
+__device__ __forceinline__ void vec_mat(const float (&z)[TB], const float* M, float (&out)[TB]) {
+  uint64_t acc[TB / 2];
 #pragma unroll
-  for (int k = 0; k < TB / 4; ++k) {
-    const float4 v = w4[k];
-    a0 = fmaf(z[4 * k], v.x, a0);
-    a1 = fmaf(z[4 * k + 1], v.y, a1);
-    a0 = fmaf(z[4 * k + 2], v.z, a0);
-    a1 = fmaf(z[4 * k + 3], v.w, a1);
+  for (int i = 0; i < TB / 2; ++i) acc[i] = 0;  // (+0.f, +0.f)
+#pragma unroll
+  for (int t = 0; t < TB; ++t) {
+    const uint64_t zz = f2_pack(z[t], z[t]);
+    const float4* row = reinterpret_cast<const float4*>(M + t * TB);
+#pragma unroll
+    for (int k = 0; k < TB / 4; ++k) {
+      const float4 w = row[k];
+      acc[2 * k] = f2_fma(zz, f2_pack(w.x, w.y), acc[2 * k]);
+      acc[2 * k + 1] = f2_fma(zz, f2_pack(w.z, w.w), acc[2 * k + 1]);
+    }
   }
-  return a0 + a1;
+#pragma unroll
+  for (int i = 0; i < TB / 2; ++i) {
+    const float2 h = f2_unpack(acc[i]);
+    out[2 * i] = h.x;
+    out[2 * i + 1] = h.y;
+  }
 }
 
 __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
@@ -226,21 +258,37 @@ static __device__ __noinline__ bool cross_cta_reduce(Bufs b, bool kGram, double*
   return true;
 }
 
-// sum over the pixels of a staged tile of the 4x4 Gram block (bi, bj) owned by
-// this thread (its pixel group ggrp strides by GramMap<TB>::NGRP)
-template <int TB>
-__device__ __forceinline__ void gram_tile(const float* sZ, float (&acc)[16], int ggrp, int bi, int bj) {
+// sum over the NPIX pixel rows of a staged tile (row stride TB + 4) of the 4x4
+// Gram block (bi, bj) owned by this thread (its pixel group ggrp strides by NGRP)
+template <int TB, int NPIX, int NGRP>
+__device__ __forceinline__ void gram_rows(const float* sZ, float (&acc)[16], int ggrp, int bi, int bj) {
   constexpr int ZS = TB + 4;
-  for (int pp = ggrp; pp < kTile; pp += GramMap<TB>::NGRP) {
+  uint64_t a2[8];  // a2[2u + h] = (acc[4u + 2h], acc[4u + 2h + 1])
+#pragma unroll
+  for (int i = 0; i < 8; ++i) a2[i] = f2_pack(acc[2 * i], acc[2 * i + 1]);
+  for (int pp = ggrp; pp < NPIX; pp += NGRP) {
     const float4 a = *reinterpret_cast<const float4*>(&sZ[pp * ZS + 4 * bi]);
     const float4 c = *reinterpret_cast<const float4*>(&sZ[pp * ZS + 4 * bj]);
     const float av[4] = {a.x, a.y, a.z, a.w};
-    const float cv[4] = {c.x, c.y, c.z, c.w};
+    const uint64_t c01 = f2_pack(c.x, c.y), c23 = f2_pack(c.z, c.w);
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int v = 0; v < 4; ++v) acc[u * 4 + v] = fmaf(av[u], cv[v], acc[u * 4 + v]);
+    for (int u = 0; u < 4; ++u) {
+      const uint64_t au = f2_pack(av[u], av[u]);
+      a2[2 * u] = f2_fma(au, c01, a2[2 * u]);
+      a2[2 * u + 1] = f2_fma(au, c23, a2[2 * u + 1]);
+    }
   }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float2 h = f2_unpack(a2[i]);
+    acc[2 * i] = h.x;
+    acc[2 * i + 1] = h.y;
+  }
+}
+
+template <int TB>
+__device__ __forceinline__ void gram_tile(const float* sZ, float (&acc)[16], int ggrp, int bi, int bj) {
+  gram_rows<TB, kTile, GramMap<TB>::NGRP>(sZ, acc, ggrp, bi, bj);
 }
 
 // End of a pass (all threads of the CTA): write this CTA's partial Gram and
@@ -305,7 +353,25 @@ __device__ __forceinline__ bool pass_epilogue(Bufs b, const float (&acc)[16], fl
 // stride over tiles; partial Grams and scalars are reduced across CTAs by the
 // last CTA to arrive (two levels, fixed summation order => deterministic).
 // ---------------------------------------------------------------------------
-// dynamic shared memory of pass_body: Wbar^T, V^T and the staged tile
+// Pulls this CTA's next tile (its X rows, and S, Y rows unless `xonly`) from
+// HBM into L2 while the current tile is computed, so that the next tile's
+// loads hit L2: one prefetch per 32-pixel (128-byte) piece of a frame row.
+__device__ __forceinline__ void prefetch_l2(const float* a) { asm volatile("prefetch.global.L2 [%0];" ::"l"(a)); }
+
+__device__ __forceinline__ void prefetch_tile_l2(const Job& job, const float* Yin, int64_t m, int T, int64_t p0,
+                                                 bool xonly) {
+  for (int k = threadIdx.x; k < T * (kTile / 32); k += blockDim.x) {
+    const int64_t off = (int64_t)(k / (kTile / 32)) * m + p0 + 32 * (k % (kTile / 32));
+    if (off - (int64_t)(k / (kTile / 32)) * m >= m) continue;  // piece past the last pixel
+    prefetch_l2(job.X + off);
+    if (!xonly) {
+      prefetch_l2(job.S + off);
+      prefetch_l2(Yin + off);
+    }
+  }
+}
+
+// dynamic shared memory of pass_body: Wbar, V and the staged tile
 template <int TB>
 __host__ __device__ constexpr size_t pass_simt_smem() {
   return sizeof(float) * (2 * (size_t)TB * TB + (size_t)kTile * (TB + 4));
@@ -320,9 +386,9 @@ __device__ bool pass_body(Bufs b, int lc, int nc, unsigned char* dsm) {
   constexpr bool kGram = (MODE != PM_UPDATE);
   constexpr int ZS = TB + 4;  // staged row stride in floats (16-byte aligned rows)
   using GM = GramMap<TB>;
-  float* sWT = reinterpret_cast<float*>(dsm);   // Wbar transposed: sWT[j*TB + t] = Wbar[t][j]
-  float* sVT = sWT + TB * TB;                   // V transposed
-  float* sZ = sVT + TB * TB;                    // [kTile][ZS]
+  float* sW = reinterpret_cast<float*>(dsm);    // Wbar, row-major TB x TB (zero outside T)
+  float* sV = sW + TB * TB;                     // V
+  float* sZ = sV + TB * TB;                     // [kTile][ZS]
   __shared__ double sRed[2][kPassThreads / 32];
   __shared__ double sScal[2 * kMaxGroups];
   __shared__ int sLast;
@@ -345,8 +411,8 @@ __device__ bool pass_body(Bufs b, int lc, int nc, unsigned char* dsm) {
     for (int i = tid; i < TB * TB; i += kPassThreads) {
       const int r = i / TB, c = i % TB;
       const bool in = (r < T && c < T);
-      sWT[c * TB + r] = in ? __ldcg(&b.eig->Wbar[r * kMaxT + c]) : 0.f;
-      sVT[c * TB + r] = in ? __ldcg(&b.eig->V32[r * kMaxT + c]) : 0.f;
+      sW[r * TB + c] = in ? __ldcg(&b.eig->Wbar[r * kMaxT + c]) : 0.f;
+      sV[r * TB + c] = in ? __ldcg(&b.eig->V32[r * kMaxT + c]) : 0.f;
     }
   }
   __syncthreads();
@@ -373,6 +439,7 @@ __device__ bool pass_body(Bufs b, int lc, int nc, unsigned char* dsm) {
         e2 = fmaf(x, x, e2);
         l1 += fabsf(x);
       }
+      if (tile + nc < ntiles) prefetch_tile_l2(job, Yin, m, T, (tile + nc) * kTile, true);
     } else {
       // z = X - S + Y/mu for this pixel row (the argument of Eq. 4); X itself
       // is not kept (Z' below needs only Z, Y/mu, Q and the clip)
@@ -387,12 +454,11 @@ __device__ bool pass_body(Bufs b, int lc, int nc, unsigned char* dsm) {
         z[t] = form_z(x, s[t], y, inv_mu);
       }
       if (MODE == PM_GRAM) {
-#pragma unroll
-        for (int j = 0; j < TB; ++j) zt[j] = row_dot<TB>(z, &sVT[j * TB]);
+        if (tile + nc < ntiles) prefetch_tile_l2(job, Yin, m, T, (tile + nc) * kTile, first);
+        vec_mat<TB>(z, sV, zt);
       } else {
         float q[TB];
-#pragma unroll
-        for (int j = 0; j < TB; ++j) q[j] = row_dot<TB>(z, &sWT[j * TB]);   // (Z Wbar)_j
+        vec_mat<TB>(z, sW, q);   // (Z Wbar)_j
 #pragma unroll
         for (int t = 0; t < TB; ++t) {
           if (t < T) {
@@ -410,9 +476,10 @@ __device__ bool pass_body(Bufs b, int lc, int nc, unsigned char* dsm) {
             z[t] = valid ? ((z[t] - d[t]) - q[t]) + c + yn * inv_mu_nxt : 0.f;
           }
         }
+        // S and Y of this tile are written; the next tile's rows can come
+        if (tile + nc < ntiles) prefetch_tile_l2(job, Yin, m, T, (tile + nc) * kTile, first);
         if (MODE == PM_FUSED) {
-#pragma unroll
-          for (int j = 0; j < TB; ++j) zt[j] = row_dot<TB>(z, &sVT[j * TB]);
+          vec_mat<TB>(z, sV, zt);
         }
       }
     }
@@ -914,6 +981,7 @@ static __global__ void begin_kernel(Bufs b, const float* X, float* L, float* S, 
 #include "rpca_tc.cuh"
 #include "rpca_pass_tc.cuh"
 #include "rpca_pass_ws.cuh"
+#include "rpca_pass_fs.cuh"
 #include "rpca_eig_fast.cuh"
 
 }  // namespace rpca
