@@ -80,12 +80,14 @@ __device__ __forceinline__ void stage_rows(float* sM, const float* M, int k0, in
   }
 }
 
-// acc[j] = sum_t z(t) * M[t][w*CW + j], z(t) from zfun(t), M streamed from global.
+// acc[j] = sum_t z(t) * M[t][w*CW + j], z(t) from zfun(t), M streamed from
+// global, in increasing t; column pairs share one paired FMA (fma.rn.f32x2).
 template <int CW, typename ZF>
 __device__ __forceinline__ void tile_times(float (&acc)[CW], float* sM, const float* M, int T, int w, ZF zfun) {
   constexpr int TP = WideShape<CW>::TP;
+  uint64_t a2[CW / 2];  // a2[h] = (acc[2h], acc[2h + 1])
 #pragma unroll
-  for (int j = 0; j < CW; ++j) acc[j] = 0.f;
+  for (int h = 0; h < CW / 2; ++h) a2[h] = 0;  // (+0.f, +0.f)
   for (int k0 = 0; k0 < T; k0 += kWKC) {
     __syncthreads();
     stage_rows<TP>(sM, M, k0, T);
@@ -93,16 +95,21 @@ __device__ __forceinline__ void tile_times(float (&acc)[CW], float* sM, const fl
     const int kn = min(kWKC, T - k0);
     for (int kk = 0; kk < kn; ++kk) {
       const float z = zfun(k0 + kk);
+      const uint64_t zz = f2_pack(z, z);
       const float4* row = reinterpret_cast<const float4*>(&sM[kk * TP + w * CW]);
 #pragma unroll
       for (int j4 = 0; j4 < CW / 4; ++j4) {
         const float4 v = row[j4];
-        acc[4 * j4] = fmaf(z, v.x, acc[4 * j4]);
-        acc[4 * j4 + 1] = fmaf(z, v.y, acc[4 * j4 + 1]);
-        acc[4 * j4 + 2] = fmaf(z, v.z, acc[4 * j4 + 2]);
-        acc[4 * j4 + 3] = fmaf(z, v.w, acc[4 * j4 + 3]);
+        a2[2 * j4] = f2_fma(zz, f2_pack(v.x, v.y), a2[2 * j4]);
+        a2[2 * j4 + 1] = f2_fma(zz, f2_pack(v.z, v.w), a2[2 * j4 + 1]);
       }
     }
+  }
+#pragma unroll
+  for (int h = 0; h < CW / 2; ++h) {
+    const float2 v = f2_unpack(a2[h]);
+    acc[2 * h] = v.x;
+    acc[2 * h + 1] = v.y;
   }
 }
 
@@ -292,15 +299,26 @@ __device__ bool pass_wide_body(Bufs b, int lc, int nc, float* wide_smem) {
       for (int uu = 0; uu < WS::BPT; ++uu) {
         if (gbi[uu] < 0) continue;
         const int bi = gbi[uu], bj = gbj[uu];
+        uint64_t g2[8];  // g2[2i + h] = (gacc[4i + 2h], gacc[4i + 2h + 1])
+#pragma unroll
+        for (int i = 0; i < 8; ++i) g2[i] = f2_pack(gacc[uu][2 * i], gacc[uu][2 * i + 1]);
         for (int pp = 0; pp < NROWS; ++pp) {
           const float4 a = *reinterpret_cast<const float4*>(&sU[pp * UP + 4 * bi]);
           const float4 c = *reinterpret_cast<const float4*>(&sU[pp * UP + 4 * bj]);
           const float av[4] = {a.x, a.y, a.z, a.w};
-          const float cv[4] = {c.x, c.y, c.z, c.w};
+          const uint64_t c01 = f2_pack(c.x, c.y), c23 = f2_pack(c.z, c.w);
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
+          for (int i = 0; i < 4; ++i) {
+            const uint64_t ai = f2_pack(av[i], av[i]);
+            g2[2 * i] = f2_fma(ai, c01, g2[2 * i]);
+            g2[2 * i + 1] = f2_fma(ai, c23, g2[2 * i + 1]);
+          }
+        }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) gacc[uu][i * 4 + j] = fmaf(av[i], cv[j], gacc[uu][i * 4 + j]);
+        for (int i = 0; i < 8; ++i) {
+          const float2 v = f2_unpack(g2[i]);
+          gacc[uu][2 * i] = v.x;
+          gacc[uu][2 * i + 1] = v.y;
         }
       }
     }
@@ -375,32 +393,36 @@ __host__ __device__ constexpr size_t res_pass_smem_bytes(int TP) {
   return sizeof(float) * (2 * (size_t)TP * TP + 3 * (size_t)TP * kRP);
 }
 
-// acc[i][j] = sum_k zrow(k)[i] * M[k][c0 + j], 4 pixels i, CPT columns j
+// acc[i][j] = sum_k zrow(k)[i] * M[k][c0 + j], 4 pixels i, CPT columns j, in
+// increasing k; column pairs (j, j + 1) share one paired FMA (fma.rn.f32x2)
 template <int TP, typename ZF>
 __device__ __forceinline__ void res_times(float (&acc)[4][TP / 16], const float* sM, int T, int c0, ZF zrow) {
   constexpr int CPT = TP / 16;
+  uint64_t a2[4][CPT / 2];  // a2[i][h] = (acc[i][2h], acc[i][2h + 1])
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < CPT; ++j) acc[i][j] = 0.f;
+    for (int h = 0; h < CPT / 2; ++h) a2[i][h] = 0;  // (+0.f, +0.f)
   for (int k = 0; k < T; ++k) {
     const float4 z = zrow(k);
     const float2* wr = reinterpret_cast<const float2*>(&sM[k * TP + c0]);
-    float w[CPT];
+    const uint64_t zz[4] = {f2_pack(z.x, z.x), f2_pack(z.y, z.y), f2_pack(z.z, z.z), f2_pack(z.w, z.w)};
 #pragma unroll
-    for (int j2 = 0; j2 < CPT / 2; ++j2) {
-      const float2 v = wr[j2];
-      w[2 * j2] = v.x;
-      w[2 * j2 + 1] = v.y;
-    }
+    for (int h = 0; h < CPT / 2; ++h) {
+      const float2 v = wr[h];
+      const uint64_t w2 = f2_pack(v.x, v.y);
 #pragma unroll
-    for (int j = 0; j < CPT; ++j) {
-      acc[0][j] = fmaf(z.x, w[j], acc[0][j]);
-      acc[1][j] = fmaf(z.y, w[j], acc[1][j]);
-      acc[2][j] = fmaf(z.z, w[j], acc[2][j]);
-      acc[3][j] = fmaf(z.w, w[j], acc[3][j]);
+      for (int i = 0; i < 4; ++i) a2[i][h] = f2_fma(zz[i], w2, a2[i][h]);
     }
   }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int h = 0; h < CPT / 2; ++h) {
+      const float2 v = f2_unpack(a2[i][h]);
+      acc[i][2 * h] = v.x;
+      acc[i][2 * h + 1] = v.y;
+    }
 }
 
 template <int TP, int MODE, bool CPLX>
@@ -611,15 +633,26 @@ __device__ bool pass_res_body(Bufs b, int lc, int nc, float* smem) {
       for (int uu = 0; uu < RS::BPT; ++uu) {
         if (gbi[uu] < 0) continue;
         const int bi = gbi[uu], bj = gbj[uu];
+        uint64_t g2[8];  // g2[2i + h] = (gacc[4i + 2h], gacc[4i + 2h + 1])
+#pragma unroll
+        for (int i = 0; i < 8; ++i) g2[i] = f2_pack(gacc[uu][2 * i], gacc[uu][2 * i + 1]);
         for (int pp = 0; pp < RS::NR; ++pp) {
           const float4 a = *reinterpret_cast<const float4*>(&sU[pp * UP + 4 * bi]);
           const float4 c = *reinterpret_cast<const float4*>(&sU[pp * UP + 4 * bj]);
           const float av[4] = {a.x, a.y, a.z, a.w};
-          const float cv[4] = {c.x, c.y, c.z, c.w};
+          const uint64_t c01 = f2_pack(c.x, c.y), c23 = f2_pack(c.z, c.w);
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
+          for (int i = 0; i < 4; ++i) {
+            const uint64_t ai = f2_pack(av[i], av[i]);
+            g2[2 * i] = f2_fma(ai, c01, g2[2 * i]);
+            g2[2 * i + 1] = f2_fma(ai, c23, g2[2 * i + 1]);
+          }
+        }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) gacc[uu][i * 4 + j] = fmaf(av[i], cv[j], gacc[uu][i * 4 + j]);
+        for (int i = 0; i < 8; ++i) {
+          const float2 v = f2_unpack(g2[i]);
+          gacc[uu][2 * i] = v.x;
+          gacc[uu][2 * i + 1] = v.y;
         }
       }
     }
