@@ -297,6 +297,18 @@ def _roofline(alg_bytes, seconds, kernel, timing, traffic=None):
             "peak_kind": peak_kind + " (hbm_gbs, burst copy)"}
 
 
+def _plan_pass_name(T, m, args):
+    """The fused pass kernel a plan runs (the rule of the plan's kernel choice)."""
+    if args.complex or T > 32:
+        return "pass_res_kernel / pass_wide_kernel (tiled, FUSED)"
+    tb = next(b for b in (8, 12, 16, 20, 24, 32) if T <= b)
+    if args.precision != "fp32":
+        return f"pass_ws_kernel / pass_tc_kernel ({args.precision}, tcgen05)"
+    if m % 4 == 0 and not os.environ.get("RPCA_NO_FS"):
+        return f"pass_fs_kernel<{tb},FUSED> (TMA-fed)"
+    return f"pass_kernel<{tb},FUSED>"
+
+
 def _solve_bytes(m, T, iters):
     """Algorithmic HBM bytes of one solve: init pass reads X; each iteration
     reads X, S, Y and writes S, Y; the final step reads X, S, Y_k, Y_k-1 and
@@ -766,10 +778,10 @@ def run_ours(args):
         "kernel_us": {"pass": pass_us, "eig": res["eig_us"], "init": res["init_us"],
                       "eig_split": {k: round(v, 3) for k, v in plan.timings().items()}},
         "gpu_launches": args.steps * launches_per_solve(args.drive, res["iters"]),
-        "roofline": _roofline(alg_bytes, pass_us * 1e-6,
-                              "pass_kernel<20,FUSED>" if (T <= 32 and not args.complex) else "pass_wide_kernel (FUSED)",
+        "roofline": _roofline(alg_bytes, pass_us * 1e-6, _plan_pass_name(T, m, args),
                               "device global timer per launch over the timed solves",
-                              traffic=ncu_traffic(src_hash)),
+                              traffic=(ncu_traffic(src_hash) if (wl == "w512x512_t20" and not args.complex
+                                                                  and args.precision == "fp32") else None)),
         "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": m * T * esz,
                 "d2h_bytes_per_step": 2 * m * T * esz + m + 48, "steps": e2e_steps},
         "clocks": clocks,
