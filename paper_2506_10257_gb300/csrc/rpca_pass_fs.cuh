@@ -13,6 +13,11 @@
 //   * a warpgroup stages its tile's Z~ rows in the same stage for its Gram
 //     blocks; once done with tile j it refills the stage with tile j + NS
 //     (one elected thread issues the TMA), so no producer warp is needed.
+//     The warpgroups are not in lockstep: the one that owns tile j + NS may
+//     reach it before tile j is done, when the stage's barrier still waits for
+//     tile j and a parity wait would alias with the phase before.  So every
+//     stage records the tile whose load was issued last (fs_issued), and a
+//     consumer waits for its own tile's issue before the parity wait.
 // S' and Y' are written straight to global memory (coalesced rows), and the
 // next Z is formed as X - S' + Y'/mu' from the staged X.
 // Every wait is bounded: a wait that runs out marks red->err and the pass
@@ -47,6 +52,16 @@ __device__ __forceinline__ void mbar_inval(uint64_t* mbar) {
   asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(mbar)) : "memory");
 }
 
+// Waits (bounded) until the stage's last issued load is local tile j.
+__device__ __forceinline__ bool wait_issued(const int* issued, int j, uint32_t limit) {
+  const volatile int* v = issued;
+  for (uint32_t it = 0; it < limit; ++it) {
+    if (*v == j) return true;
+    __nanosleep(64);
+  }
+  return false;
+}
+
 // One pass over the pixels of this CTA (number lc of nc) with kFsThreads
 // threads; `dsm` holds FsShape<TB>::SMEM bytes (1024-byte aligned).  Needs the
 // job's tensor maps (m % 4 == 0).  Returns true in the CTA that wrote the final
@@ -60,6 +75,7 @@ __device__ bool pass_fs_body(Bufs b, int lc, int nc, unsigned char* dsm) {
   float* sW = reinterpret_cast<float*>(dsm + (size_t)NS * FS::STAGE);  // Wbar, row-major TB x TB
   float* sV = sW + TB * TB;                                          // V
   __shared__ __align__(8) uint64_t fs_full[NS];
+  __shared__ int fs_issued[NS];  // local tile whose load into the stage was issued last
   __shared__ double sRed[2][kFsThreads / 32];
   __shared__ double sScal[2 * kMaxGroups];
   __shared__ int sLast;
@@ -91,7 +107,8 @@ __device__ bool pass_fs_body(Bufs b, int lc, int nc, unsigned char* dsm) {
   }
   const int64_t ntiles = (m + kFsTile - 1) / kFsTile;
   const int64_t nloc = (ntiles > lc) ? (ntiles - 1 - lc) / nc + 1 : 0;  // tiles lc, lc + nc, ...
-  // TMA of local tile j into its stage j % NS, completion counted on fs_full
+  // TMA of local tile j into its stage j % NS, completion counted on fs_full;
+  // the expected bytes are armed before the stage records tile j as issued
   auto load_tile = [&](int64_t j) {
     const int st = (int)(j % NS);
     unsigned char* dst = sStage + (size_t)st * FS::STAGE;
@@ -102,6 +119,8 @@ __device__ bool pass_fs_body(Bufs b, int lc, int nc, unsigned char* dsm) {
       tma_load_2d(dst + rows_bytes, &jobp->map_s, x0, 0, &fs_full[st]);
       tma_load_2d(dst + 2 * rows_bytes, mapY, x0, 0, &fs_full[st]);
     }
+    __threadfence_block();
+    *reinterpret_cast<volatile int*>(&fs_issued[st]) = (int)j;
   };
   const int wg = tid >> 7;   // warpgroup
   const int r = tid & 127;   // pixel of the tile
@@ -114,7 +133,10 @@ __device__ bool pass_fs_body(Bufs b, int lc, int nc, unsigned char* dsm) {
     }
   }
   if (tid == 0) {
-    for (int i = 0; i < NS; ++i) mbar_init(&fs_full[i], 1);
+    for (int i = 0; i < NS; ++i) {
+      mbar_init(&fs_full[i], 1);
+      fs_issued[i] = -1;
+    }
     for (int64_t j = 0; j < nloc && j < NS; ++j) load_tile(j);
   }
   __syncthreads();
@@ -136,6 +158,7 @@ __device__ bool pass_fs_body(Bufs b, int lc, int nc, unsigned char* dsm) {
       const uint32_t use = (uint32_t)(j / NS);
       const int64_t p = (lc + j * nc) * kFsTile + r;
       const bool valid = p < m;  // pixels past m arrive as zeros
+      ok = wait_issued(&fs_issued[st], (int)j, kTcWaitLimit) && ok;
       ok = mbar_wait(&fs_full[st], use & 1u, kTcWaitLimit) && ok;
       float* tx = reinterpret_cast<float*>(sStage + (size_t)st * FS::STAGE);
       const float* ts = tx + T * kFsTile;
@@ -210,7 +233,13 @@ __device__ bool pass_fs_body(Bufs b, int lc, int nc, unsigned char* dsm) {
   if (!ok) atomicExch(&b.red->err, 1);
   __syncthreads();
   if (tid == 0) {
-    for (int i = 0; i < NS; ++i) mbar_inval(&fs_full[i]);
+    // every issued load has been waited for; after a wait that ran out, give
+    // the copies still in flight (bounded) time to land before the exit
+    for (int i = 0; i < NS; ++i) {
+      const int jl = fs_issued[i];
+      if (jl >= 0 && !mbar_wait(&fs_full[i], (uint32_t)(jl / NS) & 1u, kTcWaitLimit)) atomicExch(&b.red->err, 1);
+      mbar_inval(&fs_full[i]);
+    }
   }
 
   // ---- CTA partials: the warpgroups' Gram blocks, residual, ||X|| sums ----
