@@ -96,11 +96,16 @@ def ncu_batch_traffic(kernel_src_hash: str, iters):
 
 
 def kernel_source_hash() -> str:
+    """Hash of the device code: every kernel body lives in the csrc/*.cuh
+    headers (the wide batch kernel in rpca_batch_wide.cu) and is compiled with
+    the flags of build.py; host-only sources do not enter it."""
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2506_10257_gb300", "csrc")
+    pkg = os.path.join(ROOT, "paper_2506_10257_gb300")
+    csrc = os.path.join(pkg, "csrc")
     for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh")):
+        if fn.endswith(".cuh") or fn == "rpca_batch_wide.cu":
             h.update(open(os.path.join(csrc, fn), "rb").read())
+    h.update(open(os.path.join(pkg, "build.py"), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -304,7 +309,7 @@ def _plan_pass_name(T, m, args):
     tb = next(b for b in (8, 12, 16, 20, 24, 32) if T <= b)
     if args.precision != "fp32":
         return f"pass_ws_kernel / pass_tc_kernel ({args.precision}, tcgen05)"
-    if m % 4 == 0 and not os.environ.get("RPCA_NO_FS"):
+    if m % 4 == 0 and os.environ.get("RPCA_PASS_TMA", "0") not in ("", "0"):
         return f"pass_fs_kernel<{tb},FUSED> (TMA-fed)"
     return f"pass_kernel<{tb},FUSED>"
 

@@ -485,8 +485,10 @@ static rpca_status plan_create_impl(const rpca_params* p, void* workspace, size_
   }
   pl->use_ws = (p->precision != RPCA_PREC_FP32) && (p->m % 4 == 0) && tma_encoder() != nullptr &&
                !(getenv("RPCA_NO_WS") && atoi(getenv("RPCA_NO_WS")) != 0);
+  // The TMA-fed FP32 pass is opt-in (RPCA_PASS_TMA=1): at 10..32 frames the
+  // register-resident pass with two CTAs per SM measured as fast or faster.
   pl->use_fs = !pl->wide && (p->precision == RPCA_PREC_FP32) && (p->m % 4 == 0) && (p->m < ((int64_t)1 << 31)) &&
-               tma_encoder() != nullptr && !(getenv("RPCA_NO_FS") && atoi(getenv("RPCA_NO_FS")) != 0);
+               tma_encoder() != nullptr && getenv("RPCA_PASS_TMA") && atoi(getenv("RPCA_PASS_TMA")) != 0;
   if (pl->use_fs) {
     for (int i = 0; i < 4; ++i) {
       const cudaError_t ea = cudaFuncSetAttribute(pl->ks.pass_fs[i], cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -238,3 +238,36 @@ def test_host_drive_rejects_tensor_core_precision(rp):
     with pytest.raises(rp.RpcaError) as ei:
         rp.Plan(4096, 20, precision=rp.PREC_BF16X3, drive=rp.DRIVE_HOST)
     assert ei.value.status == rp.ERR_UNSUPPORTED
+
+
+# ---- TMA-fed FP32 pass (opt-in: RPCA_PASS_TMA=1 at plan creation) ---------------
+
+@pytest.fixture
+def tma_pass(monkeypatch):
+    monkeypatch.setenv("RPCA_PASS_TMA", "1")
+
+
+@pytest.mark.parametrize("ny,nx,T", [(64, 64, 20), (63, 64, 20), (20, 20, 7), (32, 48, 12), (16, 16, 32), (40, 40, 3)])
+def test_tma_fed_pass_matches_oracle(rp, tma_pass, ny, nx, T):
+    # m % 4 == 0 selects the TMA-fed kernels; ragged last tiles arrive zero-filled
+    w = synth.make_window(seed=900 + ny * nx + T, ny=ny, nx=nx, T=T, n_bound=4, n_free=6)
+    ref = O.rpca_frames(w.frames)
+    gpu = gpu_solve(rp, w.frames)
+    assert gpu["res"]["status"] == rp.OK
+    _check_parity(gpu, ref)
+
+
+def test_tma_fed_pass_many_tiles_per_warpgroup(rp, monkeypatch):
+    # 393216 pixels: ~20 tiles per CTA, so the four warpgroups of a CTA drift
+    # apart by whole tiles; every tile must still be read after its own load.
+    # Compared with the register-resident FP32 pass (the Gram grouping differs,
+    # so within the FP32 tolerance) and run twice (bitwise repeatable).
+    w = synth.make_window(seed=77, ny=768, nx=512, T=20, n_bound=40, n_free=80)
+    base = gpu_solve(rp, w.frames)
+    monkeypatch.setenv("RPCA_PASS_TMA", "1")
+    a = gpu_solve(rp, w.frames)
+    b = gpu_solve(rp, w.frames)
+    assert a["res"]["status"] == rp.OK
+    assert np.array_equal(a["L"], b["L"]) and np.array_equal(a["S"], b["S"])
+    assert abs(a["res"]["iters"] - base["res"]["iters"]) <= 1
+    assert rel(a["L"], base["L"]) <= FP32_TOL and rel(a["S"], base["S"]) <= FP32_TOL

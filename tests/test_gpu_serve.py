@@ -57,8 +57,11 @@ def cuda(a):
 
 # ---- warm start through the plan API ---------------------------------------------
 
+@pytest.mark.parametrize("tma", [False, True])
 @pytest.mark.parametrize("mu_scale", [None, 0.1])
-def test_warm_start_matches_oracle(rp, mu_scale):
+def test_warm_start_matches_oracle(rp, mu_scale, tma, monkeypatch):
+    if tma:
+        monkeypatch.setenv("RPCA_PASS_TMA", "1")  # the TMA-fed FP32 pass (reads S0, Y0 through TMA)
     wins, _ = stream(31, 32, 32, 12, 2)
     prev = O.rpca_frames(wins[0])
     S0 = shift(prev.S).astype(np.float32)
@@ -151,7 +154,8 @@ def test_served_results_same_alone_and_in_mix(rp):
             assert rel(b[2], a[2]) <= 1e-6 and rel(b[3], a[3]) <= 1e-6
 
 
-def test_served_warm_chain_follows_oracle(rp):
+@pytest.mark.parametrize("tma", [False, True])
+def test_served_warm_chain_follows_oracle(rp, tma, monkeypatch):
     # warm_mu_scale = 0: each window's first mu is its own mu0.  The server
     # starts window k from its own FP32 state of window k-1, the oracle chain
     # from its FP64 state; the iteration stops on the primal residual alone, so
@@ -160,6 +164,8 @@ def test_served_warm_chain_follows_oracle(rp):
     # held to 1e-5 by test_warm_start_matches_oracle (identical starts); here
     # the chain is held to CHAIN_TOL and to the bound-bubble mask (Dice).
     CHAIN_TOL = 2e-3
+    if tma:
+        monkeypatch.setenv("RPCA_PASS_TMA", "1")
     s, ny, nx, T = PROBES[0]
     wins, w = stream(s, ny, nx, T, 4)
     got, _ = serve(rp, {0: wins}, slots=2, mu_scale=0.0)
