@@ -489,6 +489,17 @@ static rpca_status plan_create_impl(const rpca_params* p, void* workspace, size_
   // register-resident pass with two CTAs per SM measured as fast or faster.
   pl->use_fs = !pl->wide && (p->precision == RPCA_PREC_FP32) && (p->m % 4 == 0) && (p->m < ((int64_t)1 << 31)) &&
                tma_encoder() != nullptr && getenv("RPCA_PASS_TMA") && atoi(getenv("RPCA_PASS_TMA")) != 0;
+  if (!pl->wide) {
+    // the register-resident passes stage two tiles of Z~ rows (over 48 KB from 20 frames)
+    for (int i = 0; i < 4; ++i) {
+      const cudaError_t ea = cudaFuncSetAttribute(pl->ks.pass[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)pl->ks.pass_smem);
+      if (ea != cudaSuccess) {
+        delete pl;
+        return cuda_status(ea);
+      }
+    }
+  }
   if (pl->use_fs) {
     for (int i = 0; i < 4; ++i) {
       const cudaError_t ea = cudaFuncSetAttribute(pl->ks.pass_fs[i], cudaFuncAttributeMaxDynamicSharedMemorySize,

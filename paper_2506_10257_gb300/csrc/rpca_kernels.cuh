@@ -371,10 +371,11 @@ __device__ __forceinline__ void prefetch_tile_l2(const Job& job, const float* Yi
   }
 }
 
-// dynamic shared memory of pass_body: Wbar, V and the staged tile
+// dynamic shared memory of pass_body: Wbar, V and two staging buffers for the
+// tiles' Z~ rows
 template <int TB>
 __host__ __device__ constexpr size_t pass_simt_smem() {
-  return sizeof(float) * (2 * (size_t)TB * TB + (size_t)kTile * (TB + 4));
+  return sizeof(float) * (2 * (size_t)TB * TB + 2 * (size_t)kTile * (TB + 4));
 }
 
 // One pass over the pixels of this CTA (number lc of nc); `dsm` holds
@@ -388,7 +389,7 @@ __device__ bool pass_body(Bufs b, int lc, int nc, unsigned char* dsm) {
   using GM = GramMap<TB>;
   float* sW = reinterpret_cast<float*>(dsm);    // Wbar, row-major TB x TB (zero outside T)
   float* sV = sW + TB * TB;                     // V
-  float* sZ = sV + TB * TB;                     // [kTile][ZS]
+  float* sZ = sV + TB * TB;                     // [2][kTile][ZS]: tiles alternate buffers
   __shared__ double sRed[2][kPassThreads / 32];
   __shared__ double sScal[2 * kMaxGroups];
   __shared__ int sLast;
@@ -427,7 +428,8 @@ __device__ bool pass_body(Bufs b, int lc, int nc, unsigned char* dsm) {
   float e2 = 0.f, l1 = 0.f;
 
   const int64_t ntiles = (m + kTile - 1) / kTile;
-  for (int64_t tile = lc; tile < ntiles; tile += nc) {
+  int parity = 0;  // staging buffer of this tile
+  for (int64_t tile = lc; tile < ntiles; tile += nc, parity ^= 1) {
     const int64_t p = tile * kTile + tid;
     const bool valid = p < m;
     float zt[TB];
@@ -484,15 +486,18 @@ __device__ bool pass_body(Bufs b, int lc, int nc, unsigned char* dsm) {
       }
     }
     if (kGram) {
-      float4* dst = reinterpret_cast<float4*>(&sZ[tid * ZS]);
+      // one barrier per tile: the next tile stages into the other buffer, and
+      // this tile's barrier orders the buffer's reuse two tiles later
+      float* zb = sZ + parity * kTile * ZS;
+      float4* dst = reinterpret_cast<float4*>(&zb[tid * ZS]);
 #pragma unroll
       for (int j4 = 0; j4 < TB / 4; ++j4)
         dst[j4] = make_float4(zt[4 * j4], zt[4 * j4 + 1], zt[4 * j4 + 2], zt[4 * j4 + 3]);
       __syncthreads();
-      if (gthr) gram_tile<TB>(sZ, acc, ggrp, bi, bj);
-      __syncthreads();
+      if (gthr) gram_tile<TB>(zb, acc, ggrp, bi, bj);
     }
   }
+  if (kGram) __syncthreads();  // the last tile's Gram reads are done before the scratch reuse
 
   return pass_epilogue<TB, kGram>(b, acc, e2, l1, sZ, sRed, sScal, &sLast, gthr, ggrp, gblk, lc, nc);
 }

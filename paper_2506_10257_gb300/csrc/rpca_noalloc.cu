@@ -156,6 +156,8 @@ extern "C" rpca_status rpca_gram_noalloc(const float* X, int64_t m, int32_t T, c
   if (e == cudaSuccess) e = cudaLaunchKernel((void*)na_setup_kernel, dim3(1), dim3(256), a_setup, 0, s);
   void* a_pass[] = {&b};
   if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(na_pass_fn(T), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)na_pass_smem(T));
+  if (e == cudaSuccess)
     e = cudaLaunchKernel(na_pass_fn(T), dim3((unsigned)grid), dim3(kPassThreads), a_pass, na_pass_smem(T), s);
   void* a_store[] = {&b, &G, &T};
   if (e == cudaSuccess) e = cudaLaunchKernel((void*)na_store_kernel, dim3(1), dim3(256), a_store, 0, s);
