@@ -518,6 +518,69 @@ def uneven_windows(n: int, seed: int = 3000):
     return out
 
 
+def run_frames_sweep(args):
+    """Frames against accuracy (the trade-off of Sec. IV): windows of the
+    paper's 338 x 260 execution-time shape (200 bound / 400 free blobs) at
+    T = 5 ... 132 frames, several seeds each, solved by the plan form (FP32);
+    per T the mean and STD over seeds of the RMSE (Eq. 7) of L and S against
+    the generator's ground truth, the Dice of the bound-bubble mask against
+    the ground-truth mask (threshold: half the mean temporal-mean |L| over the
+    ground-truth bound pixels, as in the solver's mask rule), iterations and
+    ms per solve (device events, L2 flushed before each solve)."""
+    import numpy as np
+    import torch
+    from paper_2506_10257_gb300 import synth
+    rpca, rank, local_rank, world = _setup(args)
+    frames_list = [5, 10, 20, 30, 40, 60, 100, 132]
+    seeds = list(range(5))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    rows = []
+    for T in frames_list:
+        acc = {"rmse_L": [], "rmse_S": [], "dice": [], "iters": [], "ms": []}
+        plan = None
+        for sd in seeds:
+            w = synth.make_window(seed=9000 + 100 * T + sd, ny=338, nx=260, T=T, n_bound=200, n_free=400,
+                                  speed=(0.5, 5.0))
+            if plan is None:
+                plan = rpca.Plan(w.m, T)
+            X = torch.from_numpy(w.frames).cuda()
+            L, S = torch.empty_like(X), torch.empty_like(X)
+            plan.solve(X, L, S)                                  # warm-up (untimed)
+            flush.fill_(float(sd))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            _, _, res = plan.solve(X, L, S, wait=False)
+            e1.record()
+            torch.cuda.synchronize()
+            res = plan.result()
+            Lh, Sh = L.cpu().numpy().astype(np.float64), S.cpu().numpy().astype(np.float64)
+            img = np.abs(Lh).mean(axis=0)
+            gt = w.bound_mask_gt
+            theta = 0.5 * img[gt].mean() if gt.any() else float("inf")
+            mask = img >= theta
+            inter = np.logical_and(mask, gt).sum()
+            acc["dice"].append(2.0 * inter / max(mask.sum() + gt.sum(), 1))
+            acc["rmse_L"].append(float(np.sqrt(np.mean((Lh - w.L_gt) ** 2))))
+            acc["rmse_S"].append(float(np.sqrt(np.mean((Sh - w.S_gt) ** 2))))
+            acc["iters"].append(res["iters"])
+            acc["ms"].append(e0.elapsed_time(e1))
+        plan.close()
+        rows.append({"T": T, **{k: {"mean": float(np.mean(v)), "std": float(np.std(v))} for k, v in acc.items()}})
+    line = {
+        "metric": "solves/s", "value": 1000.0 / rows[2]["ms"]["mean"], "unit": "solves/s", "n_gpus": world,
+        "steps": len(seeds), "warmup": len(seeds), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded microbubble windows, ground truth L, S, bound mask)",
+        "config": {"workload": "frames sweep: 338x260 px windows, T in %s, %d seeds each" % (frames_list, len(seeds)),
+                   "form": "plan: one solve per step (value: the 20-frame windows)", "precision": "fp32",
+                   "tol": 1e-7, "l2": "flushed before every timed solve"},
+        "per_frames": rows,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_uneven(args):
     """Uneven batch: one persistent launch (autotuned schedule) solving
     --windows windows of uneven pixel and frame counts, against the same
@@ -817,7 +880,8 @@ def main():
     ap.add_argument("--tune", action="store_true", help="autotune the batch schedule first")
     ap.add_argument("--workload", default="w512x512_t20",
                     help="a synth preset (plan form: w512x512_t10/20/50/100, w338x260_t20/60/132, ...); "
-                         "uneven: the uneven batch; probes8: served streaming")
+                         "uneven: the uneven batch; probes8: served streaming; "
+                         "frames_sweep: accuracy against frames on 338x260 windows")
     ap.add_argument("--complex", action="store_true", help="complex64 IQ window (plan form)")
     ap.add_argument("--duration", type=float, default=1.0, help="seconds of simulated streaming (probes8)")
     ap.add_argument("--cold", action="store_true", help="served streaming without warm start")
@@ -834,6 +898,8 @@ def main():
         return run_uneven(args)
     if args.workload == "probes8":
         return run_stream(args)
+    if args.workload == "frames_sweep":
+        return run_frames_sweep(args)
     if args.form == "batch":
         return run_batch(args)
     if args.form == "serve":
