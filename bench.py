@@ -96,16 +96,14 @@ def ncu_batch_traffic(kernel_src_hash: str, iters):
 
 
 def kernel_source_hash() -> str:
-    """Hash of the device code: every kernel body lives in the csrc/*.cuh
-    headers (the wide batch kernel in rpca_batch_wide.cu) and is compiled with
-    the flags of build.py; host-only sources do not enter it."""
+    """Hash of the solver's device code: every kernel body of the solver lives
+    in the csrc/*.cuh headers (the wide batch kernel in rpca_batch_wide.cu);
+    host-only sources and the pre-filter's own unit do not enter it."""
     h = hashlib.sha256()
-    pkg = os.path.join(ROOT, "paper_2506_10257_gb300")
-    csrc = os.path.join(pkg, "csrc")
+    csrc = os.path.join(ROOT, "paper_2506_10257_gb300", "csrc")
     for fn in sorted(os.listdir(csrc)):
         if fn.endswith(".cuh") or fn == "rpca_batch_wide.cu":
             h.update(open(os.path.join(csrc, fn), "rb").read())
-    h.update(open(os.path.join(pkg, "build.py"), "rb").read())
     return h.hexdigest()[:16]
 
 

@@ -336,6 +336,37 @@ rpca_status rpca_eig(const double* G, int32_t T, double* evals, double* evecs, v
  *   - G is valid once `stream` has been synchronised. */
 rpca_status rpca_gram_noalloc(const float* X, int64_t m, int32_t T, const float* V, double* G, void* stream);
 
+/* ---- frame pre-filter of the in vivo reference ---------------------------- */
+
+/* Before its 132-frame reference solve (Sec. III, "Applying the RPCA method")
+ * the paper excludes the frames whose correlation with their neighbouring
+ * frames is below 0.8 and applies a temporal moving average over 20 frames.
+ * rpca_prefilter does both on the device, stream-ordered, with no host round
+ * trip, so its output can feed rpca_solve on the same stream.  Readings (the
+ * paper gives no formula): the correlation of frames t and t+1 is Pearson's
+ * coefficient over all m pixels (a frame without variance correlates 0);
+ * frame t is kept when it correlates at or above corr_min with at least one
+ * neighbour (frames t-1, t+1; a window of one frame keeps it); the moving
+ * average covers whole windows of kept frames only: output frame j is the
+ * mean of kept frames j .. j+window-1, j = 0 .. K-window (K kept frames).
+ *   X       frame-major T x m float32 on the device (frame t at X + t*m), read only.
+ *   Y       device, room for max(T - window + 1, 0) frames of m floats (frame-major);
+ *           the first count[1] frames are written.
+ *   kept    device int32[T]: the kept frame indices, increasing (first count[0]).
+ *   count   device int32[2]: {K, max(K - window + 1, 0)}.
+ *   corr    device float64[T - 1] (nullable): the neighbour correlations,
+ *           corr[t] between frames t and t+1.
+ *   scratch device memory of rpca_prefilter_scratch_bytes(m, T) bytes, owned by
+ *           the caller, not shared with a call in flight.
+ * Correlations are accumulated in FP64 (FP32 inputs make every product exact);
+ * the window sums slide in FP64.  Errors: RPCA_ERR_ARG (a null pointer, m < 1,
+ * T < 1, window < 1, corr_min NaN, X or Y not 4-byte aligned),
+ * RPCA_ERR_UNSUPPORTED (T > 65535), RPCA_ERR_CUDA (a launch failed).  The
+ * outputs are valid once `stream` has reached the call. */
+size_t rpca_prefilter_scratch_bytes(int64_t m, int32_t T);
+rpca_status rpca_prefilter(const float* X, int64_t m, int32_t T, double corr_min, int32_t window, float* Y,
+                           int32_t* kept, int32_t* count, double* corr, void* scratch, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

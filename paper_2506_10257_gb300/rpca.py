@@ -31,7 +31,7 @@ EXPORTED = ["rpca_params_default", "rpca_workspace_size", "rpca_plan_create", "r
             "rpca_gram_noalloc", "rpca_plan_timings", "rpca_batch_create", "rpca_batch_solve",
             "rpca_batch_tune", "rpca_batch_info", "rpca_batch_window_ctas", "rpca_batch_destroy",
             "rpca_server_create", "rpca_server_set_warm", "rpca_submit", "rpca_poll", "rpca_server_wait",
-            "rpca_server_stats", "rpca_server_destroy"]
+            "rpca_server_stats", "rpca_server_destroy", "rpca_prefilter_scratch_bytes", "rpca_prefilter"]
 
 
 class Params(ctypes.Structure):
@@ -98,6 +98,9 @@ def load(build_if_missing: bool = True):
     lib.rpca_gram.argtypes = [vp, i64, i32, vp, vp, i32, vp]
     lib.rpca_eig.argtypes = [vp, i32, vp, vp, vp]
     lib.rpca_gram_noalloc.argtypes = [vp, i64, i32, vp, vp, vp]
+    lib.rpca_prefilter_scratch_bytes.argtypes = [i64, i32]
+    lib.rpca_prefilter_scratch_bytes.restype = ctypes.c_size_t
+    lib.rpca_prefilter.argtypes = [vp, i64, i32, ctypes.c_double, i32, vp, vp, vp, vp, vp, vp]
     lib.rpca_plan_timings.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i32]
     lib.rpca_batch_create.argtypes = [ctypes.POINTER(Params), i32, ctypes.POINTER(vp)]
     lib.rpca_batch_solve.argtypes = [vp, ctypes.POINTER(Window), vp, ctypes.POINTER(Result)]
@@ -316,6 +319,39 @@ def gram_noalloc(frames, V=None, G=None, stream=None):
     if st != OK:
         raise RpcaError(st, "rpca_gram_noalloc")
     return G
+
+
+def prefilter(frames, corr_min: float = 0.8, window: int = 20, stream=None, wait: bool = True):
+    """Frame pre-filter of the in vivo reference (rpca_prefilter): frames that
+    correlate below corr_min with every neighbour are dropped, then a whole-window
+    moving average of `window` frames runs over the kept frames.  frames: (T, m)
+    float32 CUDA tensor.  Returns (Y, kept, corr): Y (n, m) float32 with
+    n = max(K - window + 1, 0), kept (K,) int32 indices, corr (T - 1,) float64.
+    With wait=False the full-size buffers and the device counts are returned
+    instead: (Y_full, kept_full, corr, count)."""
+    torch = _torch()
+    if frames.dim() != 2 or frames.dtype != torch.float32 or not frames.is_cuda or not frames.is_contiguous():
+        raise ValueError("frames must be a contiguous (T, m) float32 CUDA tensor")
+    T, m = frames.shape
+    Y = torch.empty((max(T - window + 1, 0), m), dtype=torch.float32, device=frames.device)
+    kept = torch.empty(T, dtype=torch.int32, device=frames.device)
+    count = torch.zeros(2, dtype=torch.int32, device=frames.device)
+    corr = torch.zeros(max(T - 1, 0), dtype=torch.float64, device=frames.device)
+    lib = load()
+    scratch = torch.empty(max(int(lib.rpca_prefilter_scratch_bytes(m, T)), 8), dtype=torch.uint8,
+                          device=frames.device)
+    st = lib.rpca_prefilter(ctypes.c_void_p(frames.data_ptr()), m, T, float(corr_min), int(window),
+                            ctypes.c_void_p(Y.data_ptr() if Y.numel() else frames.data_ptr()),
+                            ctypes.c_void_p(kept.data_ptr()), ctypes.c_void_p(count.data_ptr()),
+                            ctypes.c_void_p(corr.data_ptr() if corr.numel() else 0),
+                            ctypes.c_void_p(scratch.data_ptr()), _stream_handle(stream))
+    if st != OK:
+        raise RpcaError(st, "rpca_prefilter")
+    if not wait:
+        return Y, kept, corr, count
+    torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+    K, n = (int(v) for v in count.cpu().tolist())
+    return Y[:n], kept[:K], corr
 
 
 class Batch:
