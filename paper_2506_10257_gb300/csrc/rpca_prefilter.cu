@@ -17,9 +17,10 @@
 //                     in FP64);
 //   pf_decide_kernel  one CTA: sums the chunks in fixed order, forms the
 //                     neighbour correlations, keeps frames, writes the counts;
-//   pf_average_kernel pixel per thread: sliding FP64 window sum over the kept
-//                     frames (exact for FP32 inputs of similar magnitude),
-//                     each output frame written as FP32.
+//   pf_average_kernel a thread per (pixel, 16 output frames): the window sum
+//                     in FP64, formed directly for the first output and slid
+//                     for the rest (exact for FP32 inputs of similar
+//                     magnitude), each output frame written as FP32.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -90,8 +91,15 @@ __global__ void __launch_bounds__(kPfThreads) pf_decide_kernel(const double* __r
   const double dm = (double)m;
   for (int i = threadIdx.x; i < 3 * T; i += blockDim.x) {
     const int t = i / 3, k = i % 3;
+    const double* src = partial + (int64_t)t * nch * 3 + k;
     double s = 0.0;
-    for (int c = 0; c < nch; ++c) s += partial[((int64_t)t * nch + c) * 3 + k];
+    for (int c0 = 0; c0 < nch; c0 += 16) {
+      double v[16];  // sixteen loads in flight, then added in chunk order
+#pragma unroll
+      for (int u = 0; u < 16; ++u) v[u] = (c0 + u < nch) ? src[(int64_t)(c0 + u) * 3] : 0.0;
+#pragma unroll
+      for (int u = 0; u < 16; ++u) s += v[u];
+    }
     st[i] = s;
   }
   __syncthreads();
@@ -120,7 +128,11 @@ __global__ void __launch_bounds__(kPfThreads) pf_decide_kernel(const double* __r
   }
 }
 
-// kept list in dynamic shared memory (T ints)
+constexpr int kPfSeg = 16;  // output frames of one moving-average thread
+
+// kept list in dynamic shared memory (T ints).  Work item (segment g, pixel p):
+// output frames g*kPfSeg .. +kPfSeg-1 of pixel p; items run pixel-fastest, so
+// a warp reads and writes 32 consecutive pixels of one frame.
 __global__ void __launch_bounds__(kPfThreads) pf_average_kernel(const float* __restrict__ X, int64_t m, int T,
                                                                 const int* __restrict__ kept,
                                                                 const int* __restrict__ count, int window,
@@ -131,11 +143,17 @@ __global__ void __launch_bounds__(kPfThreads) pf_average_kernel(const float* __r
   const int n = count[1];
   if (n <= 0) return;
   const double inv_w = 1.0 / (double)window;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t nseg = (n + kPfSeg - 1) / kPfSeg;
+  for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < nseg * m;
+       it += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = it % m;
+    const int j0 = (int)(it / m) * kPfSeg;
+    const int j1 = (j0 + kPfSeg < n) ? j0 + kPfSeg : n;
     double s = 0.0;
-    for (int i = 0; i < window; ++i) s += (double)X[(int64_t)pf_kept[i] * m + p];
-    Y[p] = (float)(s * inv_w);
-    for (int j = 1; j < n; ++j) {
+#pragma unroll 4
+    for (int i = 0; i < window; ++i) s += (double)X[(int64_t)pf_kept[j0 + i] * m + p];
+    Y[(int64_t)j0 * m + p] = (float)(s * inv_w);
+    for (int j = j0 + 1; j < j1; ++j) {
       s += (double)X[(int64_t)pf_kept[j + window - 1] * m + p];
       s -= (double)X[(int64_t)pf_kept[j - 1] * m + p];
       Y[(int64_t)j * m + p] = (float)(s * inv_w);
@@ -173,7 +191,8 @@ rpca_status rpca_prefilter(const float* X, int64_t m, int32_t T, double corr_min
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
                                                cudaSuccess)
     return RPCA_ERR_CUDA;
-  const int64_t want = (m + kPfThreads - 1) / kPfThreads;
+  const int64_t items = m * (int64_t)((T + kPfSeg - 1) / kPfSeg);  // at most this many (segment, pixel) items
+  const int64_t want = (items + kPfThreads - 1) / kPfThreads;
   const int grid = (int)(want < (int64_t)sms * 8 ? want : (int64_t)sms * 8);
   pf_average_kernel<<<grid, kPfThreads, sizeof(int) * (size_t)T, s>>>(X, m, T, kept, count, window, Y);
   return cudaGetLastError() == cudaSuccess ? RPCA_OK : RPCA_ERR_CUDA;

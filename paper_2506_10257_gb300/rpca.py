@@ -321,25 +321,34 @@ def gram_noalloc(frames, V=None, G=None, stream=None):
     return G
 
 
-def prefilter(frames, corr_min: float = 0.8, window: int = 20, stream=None, wait: bool = True):
+def prefilter_buffers(frames, window: int = 20):
+    """Device buffers of a prefilter call on (T, m) frames: (Y, kept, count, corr, scratch)."""
+    torch = _torch()
+    T, m = frames.shape
+    Y = torch.empty((max(T - window + 1, 0), m), dtype=torch.float32, device=frames.device)
+    kept = torch.empty(T, dtype=torch.int32, device=frames.device)
+    count = torch.zeros(2, dtype=torch.int32, device=frames.device)
+    corr = torch.zeros(max(T - 1, 0), dtype=torch.float64, device=frames.device)
+    scratch = torch.empty(max(int(load().rpca_prefilter_scratch_bytes(m, T)), 8), dtype=torch.uint8,
+                          device=frames.device)
+    return Y, kept, count, corr, scratch
+
+
+def prefilter(frames, corr_min: float = 0.8, window: int = 20, stream=None, wait: bool = True, out=None):
     """Frame pre-filter of the in vivo reference (rpca_prefilter): frames that
     correlate below corr_min with every neighbour are dropped, then a whole-window
     moving average of `window` frames runs over the kept frames.  frames: (T, m)
     float32 CUDA tensor.  Returns (Y, kept, corr): Y (n, m) float32 with
     n = max(K - window + 1, 0), kept (K,) int32 indices, corr (T - 1,) float64.
     With wait=False the full-size buffers and the device counts are returned
-    instead: (Y_full, kept_full, corr, count)."""
+    instead: (Y_full, kept_full, corr, count).  out: buffers from an earlier
+    call's prefilter_buffers(frames, window), reused (no allocation)."""
     torch = _torch()
     if frames.dim() != 2 or frames.dtype != torch.float32 or not frames.is_cuda or not frames.is_contiguous():
         raise ValueError("frames must be a contiguous (T, m) float32 CUDA tensor")
     T, m = frames.shape
-    Y = torch.empty((max(T - window + 1, 0), m), dtype=torch.float32, device=frames.device)
-    kept = torch.empty(T, dtype=torch.int32, device=frames.device)
-    count = torch.zeros(2, dtype=torch.int32, device=frames.device)
-    corr = torch.zeros(max(T - 1, 0), dtype=torch.float64, device=frames.device)
     lib = load()
-    scratch = torch.empty(max(int(lib.rpca_prefilter_scratch_bytes(m, T)), 8), dtype=torch.uint8,
-                          device=frames.device)
+    Y, kept, count, corr, scratch = out if out is not None else prefilter_buffers(frames, window)
     st = lib.rpca_prefilter(ctypes.c_void_p(frames.data_ptr()), m, T, float(corr_min), int(window),
                             ctypes.c_void_p(Y.data_ptr() if Y.numel() else frames.data_ptr()),
                             ctypes.c_void_p(kept.data_ptr()), ctypes.c_void_p(count.data_ptr()),
