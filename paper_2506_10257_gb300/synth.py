@@ -17,6 +17,10 @@ Recipe (one window of ``T`` frames of ``ny x nx`` pixels, ``m = ny*nx``):
 * free bubbles: ``n_free`` blobs of the same shape on straight tracks with
   speed U[vmin, vmax] px/frame and direction U[-pi, pi]; a blob whose centre
   leaves the grid is no longer drawn;
+* curved tracks (``accel`` given; the motion model of Sec. II-C): every frame
+  each free bubble gets a random acceleration of magnitude U[amin, amax]
+  px/frame^2 in a direction U[-pi, pi], and v(t) = v(t-1) + a, x(t) = x(t-1)
+  + v(t) (dt = one frame), so tracks bend gradually;
 * additive N(0, noise^2) noise, noise = 0.1.
 
 For the complex (IQ) variant every pixel of the background carries one fixed
@@ -97,6 +101,7 @@ def make_window(
     noise: float = 0.1,
     drift: float = 0.02,
     complex_iq: bool = False,
+    accel: tuple[float, float] | None = None,
 ) -> Window:
     """Draw one window; every argument is a recipe parameter (module docstring)."""
     if ny <= 0 or nx <= 0 or T <= 0:
@@ -136,11 +141,25 @@ def make_window(
         if complex_iq:
             a = a * np.exp(1j * rng.uniform(-np.pi, np.pi))
         vy, vx = v * math.sin(th), v * math.cos(th)
-        for t in range(T):
-            py, px = cy + vy * t, cx + vx * t
-            if not (0 <= py < ny and 0 <= px < nx):
-                break          # left the grid: dropped from here on
-            _splat(free[t], py, px, a, ny, nx)
+        if accel is None:
+            for t in range(T):
+                py, px = cy + vy * t, cx + vx * t
+                if not (0 <= py < ny and 0 <= px < nx):
+                    break          # left the grid: dropped from here on
+                _splat(free[t], py, px, a, ny, nx)
+        else:
+            py, px = cy, cx
+            gone = False
+            for t in range(T):
+                if t > 0:
+                    am = rng.uniform(*accel)
+                    ath = rng.uniform(-np.pi, np.pi)
+                    vy, vx = vy + am * math.sin(ath), vx + am * math.cos(ath)
+                    py, px = py + vy, px + vx
+                if gone or not (0 <= py < ny and 0 <= px < nx):
+                    gone = True    # left the grid: dropped from here on (draws continue)
+                    continue
+                _splat(free[t], py, px, a, ny, nx)
 
     L_gt = bg + bound_img.reshape(1, m)
     S_gt = free.reshape(T, m)
@@ -168,6 +187,10 @@ PRESETS = {
     "w338x260_t20": dict(ny=338, nx=260, T=20, n_bound=200, n_free=400, speed=(0.5, 5.0)),
     "w338x260_t60": dict(ny=338, nx=260, T=60, n_bound=200, n_free=400, speed=(0.5, 5.0)),
     "w338x260_t132": dict(ny=338, nx=260, T=132, n_bound=200, n_free=400, speed=(0.5, 5.0)),
+    # curved free-bubble tracks (random per-frame accelerations, Sec. II-C)
+    "w64x64_t20_curved": dict(ny=64, nx=64, T=20, n_bound=15, n_free=30, speed=(1.0, 3.0), accel=(0.05, 0.5)),
+    "w512x512_t20_curved": dict(ny=512, nx=512, T=20, n_bound=400, n_free=800, speed=(0.5, 5.0),
+                                accel=(0.05, 0.5)),
 }
 
 

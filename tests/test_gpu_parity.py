@@ -271,3 +271,14 @@ def test_tma_fed_pass_many_tiles_per_warpgroup(rp, monkeypatch):
     assert np.array_equal(a["L"], b["L"]) and np.array_equal(a["S"], b["S"])
     assert abs(a["res"]["iters"] - base["res"]["iters"]) <= 1
     assert rel(a["L"], base["L"]) <= FP32_TOL and rel(a["S"], base["S"]) <= FP32_TOL
+
+
+def test_curved_tracks_window_matches_oracle(rp):
+    # free bubbles on curved tracks (random per-frame accelerations, Sec. II-C)
+    w = synth.make_preset("w64x64_t20_curved", seed=3)
+    ref = O.rpca_frames(w.frames)
+    theta = O.mask_threshold(O.temporal_mean_abs(ref.L), w.bound_mask_gt)
+    gpu = gpu_solve(rp, w.frames, theta=theta)
+    assert gpu["res"]["status"] == rp.OK
+    _check_parity(gpu, ref)
+    assert O.dice(gpu["mask"], O.bound_mask(O.temporal_mean_abs(ref.L), theta)) >= 0.999

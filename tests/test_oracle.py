@@ -283,3 +283,4 @@ def test_frames_wrapper_transposes_the_warm_state():
     a = O.rpca(X, S0=cold.S, Y0=cold.Y, mu_init=cold.mu)
     b = O.rpca_frames(w.frames, S0=cold.S.T, Y0=cold.Y.T, mu_init=cold.mu)
     assert np.array_equal(a.L.T, b.L) and np.array_equal(a.S.T, b.S)
+
