@@ -25,10 +25,10 @@ struct EigFastSmem {
   float G[2][TB * (TB + 1)];
   float2 log[kEigLogSweeps][TB - 1][TB / 2];
   int ran[kEigLogSweeps][TB - 1];
-  float2 cs[TB / 2];
+  float2 cs[2][TB / 2];       // rotations of the current round and of the next (by round parity)
   int2 pq[TB - 1][TB / 2];   // (p, q), p < q, of every pair of every round (fixed order)
   int2 pinfo[TB - 1][TB];    // (pair index, slot) of every index in every round
-  float dnew[TB];
+  float dnew[2][TB];          // new diagonal entries, same double buffering
   float A[TB * (TB + 1)];
   double ev[TB];
   float g[TB];
@@ -91,6 +91,53 @@ __device__ void eig_fast_body(Bufs b, int flags, cudaGraphConditionalHandle h, i
       ec[u] = a + e;
     }
   }
+  // Entry (a, c), a <= c, of J^T G J for round rnd's rotations (buffers cb):
+  // pairs not rotated have c = 1, s = 0; a rotated pair's own entry is 0.
+  auto rotated_entry = [&](int rnd, int cb, int cur, int a, int c) -> float {
+    if (a == c) return S.dnew[cb][a];
+    const int2 ia = S.pinfo[rnd][a], ic = S.pinfo[rnd][c];
+    if (ia.x == ic.x) {
+      const float2 r = S.cs[cb][ia.x];
+      return (r.y != 0.f) ? 0.f : S.G[cur][a * LD + c];  // annihilated when rotated
+    }
+    const int2 pa2 = S.pq[rnd][ia.x], pc2 = S.pq[rnd][ic.x];
+    const float2 ra = S.cs[cb][ia.x], rc = S.cs[cb][ic.x];
+    // column a of J: slot 0 (c, -s) at (p, q); slot 1 (s, c)
+    const float wa0 = ia.y ? ra.y : ra.x, wa1 = ia.y ? ra.x : -ra.y;
+    const float wc0 = ic.y ? rc.y : rc.x, wc1 = ic.y ? rc.x : -rc.y;
+    const float* g0 = &S.G[cur][pa2.x * LD];
+    const float* g1 = &S.G[cur][pa2.y * LD];
+    return wa0 * (wc0 * g0[pc2.x] + wc1 * g0[pc2.y]) + wa1 * (wc0 * g1[pc2.x] + wc1 * g1[pc2.y]);
+  };
+  // Rotation of pair k of round rnd from (app, aqq, apq) into buffers cb (GVL
+  // sym.schur2: t = 2 apq sgn(d) / (|d| + sqrt(d^2 + 4 apq^2)), d = aqq - app);
+  // returns whether the pair rotates.
+  auto make_rotation = [&](int rnd, int cb, int sw, int k, float app, float aqq, float apq) -> int {
+    const int2 pq = S.pq[rnd][k];
+    float c = 1.f, s = 0.f, dp = app, dq = aqq;
+    int act = 0;
+    if (apq != 0.f && apq * apq > eps2 * fabsf(app * aqq)) {
+      act = 1;
+      const float dd = aqq - app;
+      const float r2 = fmaf(dd, dd, 4.f * apq * apq);
+      const float den = fabsf(dd) + r2 * rsqrtf(r2);
+      const float t = copysignf(1.f, dd) * (2.f * apq) * __fdividef(1.f, den);
+      c = rsqrtf(fmaf(t, t, 1.f));
+      s = t * c;
+      dp = app - t * apq;
+      dq = aqq + t * apq;
+    }
+    S.cs[cb][k] = make_float2(c, s);
+    S.log[sw][rnd][k] = make_float2(c, s);
+    S.dnew[cb][pq.x] = dp;
+    S.dnew[cb][pq.y] = dq;
+    return act;
+  };
+  // The next round's rotations are formed by the last K threads of the CTA
+  // (the ones with the fewest upper-triangle entries) while every thread
+  // updates its entries for the current round, so a round needs one barrier.
+  const int pk = tid - (nthr - K);  // pair of this thread, or < 0
+
   int cur = 0, sweeps = 0;
   while (sweeps < max_sweeps) {
     int need = 0;
@@ -103,70 +150,46 @@ __device__ void eig_fast_body(Bufs b, int flags, cudaGraphConditionalHandle h, i
       }
     }
     if (!__syncthreads_or(need)) break;
+    int act = 0;
+    if (pk >= 0) {
+      const int2 pq = S.pq[0][pk];
+      act = make_rotation(0, 0, sweeps, pk, S.G[cur][pq.x * LD + pq.x], S.G[cur][pq.y * LD + pq.y],
+                          S.G[cur][pq.x * LD + pq.y]);
+    }
+    int any = __syncthreads_or(act);
     for (int rnd = 0; rnd < NR; ++rnd) {
-      // round tables (static) first, so phase B waits only on c, s and G
-      int2 ia[EPT], ic[EPT], pa2[EPT], pc2[EPT];
-#pragma unroll
-      for (int u = 0; u < EPT; ++u) {
-        if (ea[u] >= 0) {
-          ia[u] = S.pinfo[rnd][ea[u]];
-          ic[u] = S.pinfo[rnd][ec[u]];
-          pa2[u] = S.pq[rnd][ia[u].x];
-          pc2[u] = S.pq[rnd][ic[u].x];
-        }
-      }
-      int act = 0;
-      if (tid < K) {
-        const int2 pq = S.pq[rnd][tid];
-        const int p = pq.x, q = pq.y;
-        const float app = S.G[cur][p * LD + p], aqq = S.G[cur][q * LD + q], apq = S.G[cur][p * LD + q];
-        float c = 1.f, s = 0.f, dp = app, dq = aqq;
-        if (apq != 0.f && apq * apq > eps2 * fabsf(app * aqq)) {
-          // GVL sym.schur2: t = 2 apq sgn(d) / (|d| + sqrt(d^2 + 4 apq^2)), d = aqq - app
-          act = 1;
-          const float dd = aqq - app;
-          const float r2 = fmaf(dd, dd, 4.f * apq * apq);
-          const float den = fabsf(dd) + r2 * rsqrtf(r2);
-          const float t = copysignf(1.f, dd) * (2.f * apq) * __fdividef(1.f, den);
-          c = rsqrtf(fmaf(t, t, 1.f));
-          s = t * c;
-          dp = app - t * apq;
-          dq = aqq + t * apq;
-        }
-        S.cs[tid] = make_float2(c, s);
-        S.log[sweeps][rnd][tid] = make_float2(c, s);
-        S.dnew[p] = dp;
-        S.dnew[q] = dq;
-      }
-      const int any = __syncthreads_or(act);
+      const int cb = rnd & 1;
       if (tid == 0) S.ran[sweeps][rnd] = any;
-      if (!any) continue;
-      ++rounds_run;
-      const int nxt = cur ^ 1;
+      const int nxt = any ? (cur ^ 1) : cur;
+      if (any) {
+        ++rounds_run;
 #pragma unroll
-      for (int u = 0; u < EPT; ++u) {
-        const int a = ea[u], c = ec[u];
-        if (a < 0) continue;
-        float v;
-        if (a == c) {
-          v = S.dnew[a];
-        } else if (ia[u].x == ic[u].x) {
-          const float2 r = S.cs[ia[u].x];
-          v = (r.y != 0.f) ? 0.f : S.G[cur][a * LD + c];  // annihilated when rotated
-        } else {
-          const float2 ra = S.cs[ia[u].x], rc = S.cs[ic[u].x];
-          // column a of J: slot 0 (c, -s) at (p, q); slot 1 (s, c)
-          const float wa0 = ia[u].y ? ra.y : ra.x, wa1 = ia[u].y ? ra.x : -ra.y;
-          const float wc0 = ic[u].y ? rc.y : rc.x, wc1 = ic[u].y ? rc.x : -rc.y;
-          const float* g0 = &S.G[cur][pa2[u].x * LD];
-          const float* g1 = &S.G[cur][pa2[u].y * LD];
-          v = wa0 * (wc0 * g0[pc2[u].x] + wc1 * g0[pc2[u].y]) + wa1 * (wc0 * g1[pc2[u].x] + wc1 * g1[pc2[u].y]);
+        for (int u = 0; u < EPT; ++u) {
+          const int a = ea[u], c = ec[u];
+          if (a < 0) continue;
+          const float v = rotated_entry(rnd, cb, cur, a, c);
+          S.G[nxt][a * LD + c] = v;
+          S.G[nxt][c * LD + a] = v;
         }
-        S.G[nxt][a * LD + c] = v;
-        S.G[nxt][c * LD + a] = v;
+      }
+      int act_next = 0;
+      if (pk >= 0 && rnd + 1 < NR) {
+        // the entries (p, p), (q, q), (p, q) of the next round's pair after this round
+        const int2 pq = S.pq[rnd + 1][pk];
+        float app, aqq, apq;
+        if (any) {
+          app = S.dnew[cb][pq.x];
+          aqq = S.dnew[cb][pq.y];
+          apq = rotated_entry(rnd, cb, cur, pq.x, pq.y);
+        } else {
+          app = S.G[cur][pq.x * LD + pq.x];
+          aqq = S.G[cur][pq.y * LD + pq.y];
+          apq = S.G[cur][pq.x * LD + pq.y];
+        }
+        act_next = make_rotation(rnd + 1, cb ^ 1, sweeps, pk, app, aqq, apq);
       }
       cur = nxt;
-      __syncthreads();
+      any = __syncthreads_or(act_next);
     }
     ++sweeps;
   }
