@@ -100,7 +100,8 @@ typedef struct {
    * Z1 = X - S0 + Y0/mu1 (one extra Gram pass) and every later step is the
    * same iteration.  0 (default) ignores the buffers' contents. */
   int32_t warm_start;
-  int32_t pad_;
+  int32_t sharded;          /* 1: the window is split by pixel rows across processes and driven
+                               step by step (rpca_step_*, below); default 0 */
   double mu_init;           /* > 0: first mu of the solve (default 0: the schedule's mu0) */
   double mu_prev_scale;     /* > 0 with warm_start and mu_init == 0: first mu = this times the
                                final mu of this plan's previous solve (default 0) */
@@ -335,6 +336,47 @@ rpca_status rpca_eig(const double* G, int32_t T, double* evals, double* evecs, v
  *     on it and must be serialised by the caller.
  *   - G is valid once `stream` has been synchronised. */
 rpca_status rpca_gram_noalloc(const float* X, int64_t m, int32_t T, const float* V, double* G, void* stream);
+
+/* ---- one window split by pixel rows across processes ----------------------- */
+
+/* The method's only exchange is through the T x T Gram (Eq. 4 through the
+ * eigen-decomposition of Z^T Z): with the pixel rows of one window spread over
+ * several processes (one GPU each), every process runs the pass over its own
+ * rows, the processes sum the Gram and the residual sums (an all-reduce of
+ * T*32 floats and 2 doubles per iteration), and every process then runs the
+ * same eigen-step on the same sums, so the iteration is the one of the whole
+ * window.  A plan created with params.sharded = 1 (real FP32, T <=
+ * RPCA_MAX_T_NARROW, IALM schedule, no warm start; params.lambda set from the
+ * whole window: 1/sqrt(max(m_total, T)); params.m = this process's rows)
+ * exposes the steps:
+ *   rpca_step_begin  binds this call's X, L, S (this process's rows, frame-major
+ *                    m x T, 16-byte aligned) and mask/theta as rpca_solve does;
+ *   rpca_step_run    launches one step: RPCA_STEP_INIT (the norms and Gram of X),
+ *                    RPCA_STEP_EIG_INIT (mu0 and the first eigen-step),
+ *                    RPCA_STEP_PASS (the fused pass of an iteration),
+ *                    RPCA_STEP_EIG (residual test, mu update, eigen-step),
+ *                    RPCA_STEP_FINAL (L and the mask);
+ *   rpca_step_sums   device pointers of the sums to reduce after RPCA_STEP_INIT and
+ *                    RPCA_STEP_PASS: the Gram (T rows of 32 floats, row stride 32,
+ *                    columns >= T zero) and {e2, l1} (2 doubles);
+ *   rpca_step_done   synchronises `stream` and reports whether the solve has
+ *                    ended (and its result, when `out` is not NULL).
+ * Order: begin, INIT, reduce, EIG_INIT, then while not done: PASS, reduce, EIG;
+ * then FINAL.  A plan with sharded = 1 also solves a whole window with
+ * rpca_solve.  Errors: RPCA_ERR_ARG (NULL plan or pointers, a plan without
+ * sharded = 1, an unknown step), RPCA_ERR_CUDA (a launch failed). */
+typedef enum {
+  RPCA_STEP_INIT = 0,
+  RPCA_STEP_EIG_INIT = 1,
+  RPCA_STEP_PASS = 2,
+  RPCA_STEP_EIG = 3,
+  RPCA_STEP_FINAL = 4
+} rpca_step;
+rpca_status rpca_step_begin(rpca_plan_t plan, const float* X, float* L, float* S, uint8_t* mask, float theta,
+                            void* stream);
+rpca_status rpca_step_run(rpca_plan_t plan, int32_t step, void* stream);
+rpca_status rpca_step_sums(rpca_plan_t plan, float** gram, double** sums);
+rpca_status rpca_step_done(rpca_plan_t plan, int32_t* done, rpca_result* out, void* stream);
 
 /* ---- frame pre-filter of the in vivo reference ---------------------------- */
 

@@ -189,6 +189,10 @@ rpca_status validate(const rpca_params* p) {
   if (p->precision != RPCA_PREC_FP32 && p->T > kMaxT) return RPCA_ERR_UNSUPPORTED;  // wide path is FP32
   if (p->m * (int64_t)p->T > (int64_t)1 << 40) return RPCA_ERR_ARG;
   if (p->warm_start != 0 && p->warm_start != 1) return RPCA_ERR_ARG;
+  if (p->sharded != 0 && p->sharded != 1) return RPCA_ERR_ARG;
+  if (p->sharded && (p->dtype != RPCA_R32 || p->T > kMaxT || p->precision != RPCA_PREC_FP32 ||
+                     p->mu_schedule != RPCA_MU_IALM || p->warm_start))
+    return RPCA_ERR_UNSUPPORTED;
   if (!(p->mu_init >= 0.0) || !(p->mu_prev_scale >= 0.0) || !isfinite(p->mu_init) || !isfinite(p->mu_prev_scale))
     return RPCA_ERR_ARG;
   return RPCA_OK;
@@ -568,7 +572,9 @@ static rpca_status plan_create_impl(const rpca_params* p, void* workspace, size_
   b.wide = pl->wide ? 1 : 0;
   b.grid = pl->lay.grid;
   b.ngroups = pl->lay.ngroups;
-  b.finalize = 0;
+  // a sharded plan's passes finish their reduction themselves, so the summed
+  // Gram and residual sums sit in the reduction record between the steps
+  b.finalize = p->sharded ? 1 : 0;
 
   const int mT = (int)std::max<int64_t>(p->m, p->T);
   pl->lambda = p->lambda > 0 ? p->lambda : 1.0 / sqrt((double)mT);
@@ -905,6 +911,91 @@ rpca_status rpca_eig(const double* G, int32_t T, double* evals, double* evecs, v
   if (vv) cudaFree(vv);
   rpca_plan_destroy(pl);
   return cuda_status(e);
+}
+
+}  // extern "C"
+
+// ---- one window split by pixel rows across processes: the steps one by one ----
+static_assert(offsetof(RedState, l1) == offsetof(RedState, e2) + sizeof(double), "e2, l1 adjacent");
+
+extern "C" {
+
+rpca_status rpca_step_begin(rpca_plan_t pl, const float* X, float* L, float* S, uint8_t* mask, float theta,
+                            void* stream) {
+  if (!pl || !pl->p.sharded || !X || !L || !S) return RPCA_ERR_ARG;
+  if (((uintptr_t)X | (uintptr_t)L | (uintptr_t)S) & 15u) return RPCA_ERR_ARG;
+  if ((const void*)X == (const void*)L || (const void*)X == (const void*)S || L == S) return RPCA_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  Bufs b = pl->bufs;
+  TmaMaps maps;
+  memset(&maps, 0, sizeof(maps));
+  int use_maps = 0;
+  if (pl->use_fs) {
+    const float* y1 = (const float*)(pl->ws + pl->lay.ybuf);
+    if (!encode_map(&maps.x, X, pl->p.m, pl->p.T) || !encode_map(&maps.s, S, pl->p.m, pl->p.T) ||
+        !encode_map(&maps.y0, L, pl->p.m, pl->p.T) || !encode_map(&maps.y1, y1, pl->p.m, pl->p.T))
+      return RPCA_ERR_CUDA;
+    use_maps = 1;
+  }
+  float* Sout = nullptr;
+  float* Yout = nullptr;
+  double mu_prev_scale = 0.0;
+  void* a_begin[] = {&b, (void*)&X, &L, &S, &mask, &theta, &Sout, &Yout, &mu_prev_scale, &maps, &use_maps};
+  CK(cudaLaunchKernel((void*)begin_kernel, dim3(1), dim3(64), a_begin, 0, s));
+  return RPCA_OK;
+}
+
+rpca_status rpca_step_run(rpca_plan_t pl, int32_t step, void* stream) {
+  if (!pl || !pl->p.sharded) return RPCA_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  Bufs b = pl->bufs;
+  cudaGraphConditionalHandle h = 0;
+  const double* nulld = nullptr;
+  double* nullo = nullptr;
+  int use_cond = 0;
+  int flags = 0;
+  void* a_pass[] = {&b};
+  void* a_eig[] = {&b, &flags, &h, &use_cond, &nulld, &nullo, &nullo};
+  switch (step) {
+    case RPCA_STEP_INIT:
+      CK(launch(pass_fn(pl, PM_INIT), pass_grid(pl), pass_block(pl), a_pass, s, pass_smem(pl)));
+      return RPCA_OK;
+    case RPCA_STEP_EIG_INIT:
+      flags = EF_INIT | EF_EIG;
+      CK(launch(eig_fn(pl), dim3(1), eig_block(pl), a_eig, s, eig_smem(pl)));
+      return RPCA_OK;
+    case RPCA_STEP_PASS:
+      CK(launch(fused_fn(pl), fused_grid(pl), fused_block(pl), a_pass, s, fused_smem(pl)));
+      return RPCA_OK;
+    case RPCA_STEP_EIG:
+      flags = EF_CHECK | EF_EIG;
+      CK(launch(eig_fn(pl), dim3(1), eig_block(pl), a_eig, s, eig_smem(pl)));
+      return RPCA_OK;
+    case RPCA_STEP_FINAL: {
+      const int fgrid = (int)std::min<int64_t>((pl->p.m + 255) / 256, 4096);
+      CK(launch((void*)final_kernel, dim3(fgrid), dim3(256), a_pass, s));
+      return RPCA_OK;
+    }
+    default:
+      return RPCA_ERR_ARG;
+  }
+}
+
+rpca_status rpca_step_sums(rpca_plan_t pl, float** gram, double** sums) {
+  if (!pl || !pl->p.sharded || !gram || !sums) return RPCA_ERR_ARG;
+  *gram = pl->bufs.red->G;
+  *sums = &pl->bufs.red->e2;
+  return RPCA_OK;
+}
+
+rpca_status rpca_step_done(rpca_plan_t pl, int32_t* done, rpca_result* out, void* stream) {
+  if (!pl || !pl->p.sharded || !done) return RPCA_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(pl->ctrl_host, pl->bufs.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  *done = pl->ctrl_host->done ? 1 : 0;
+  if (out) fill_result(pl, *pl->ctrl_host, out);
+  return RPCA_OK;
 }
 
 }  // extern "C"

@@ -31,7 +31,8 @@ EXPORTED = ["rpca_params_default", "rpca_workspace_size", "rpca_plan_create", "r
             "rpca_gram_noalloc", "rpca_plan_timings", "rpca_batch_create", "rpca_batch_solve",
             "rpca_batch_tune", "rpca_batch_info", "rpca_batch_window_ctas", "rpca_batch_destroy",
             "rpca_server_create", "rpca_server_set_warm", "rpca_submit", "rpca_poll", "rpca_server_wait",
-            "rpca_server_stats", "rpca_server_destroy", "rpca_prefilter_scratch_bytes", "rpca_prefilter"]
+            "rpca_server_stats", "rpca_server_destroy", "rpca_prefilter_scratch_bytes", "rpca_prefilter",
+            "rpca_step_begin", "rpca_step_run", "rpca_step_sums", "rpca_step_done"]
 
 
 class Params(ctypes.Structure):
@@ -40,7 +41,7 @@ class Params(ctypes.Structure):
                 ("drive", ctypes.c_int32), ("max_iter", ctypes.c_int32),
                 ("lambda_", ctypes.c_double), ("mu0_scale", ctypes.c_double),
                 ("rho", ctypes.c_double), ("mu_max_factor", ctypes.c_double),
-                ("tol", ctypes.c_double), ("warm_start", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("tol", ctypes.c_double), ("warm_start", ctypes.c_int32), ("sharded", ctypes.c_int32),
                 ("mu_init", ctypes.c_double), ("mu_prev_scale", ctypes.c_double)]
 
 
@@ -98,6 +99,11 @@ def load(build_if_missing: bool = True):
     lib.rpca_gram.argtypes = [vp, i64, i32, vp, vp, i32, vp]
     lib.rpca_eig.argtypes = [vp, i32, vp, vp, vp]
     lib.rpca_gram_noalloc.argtypes = [vp, i64, i32, vp, vp, vp]
+    lib.rpca_step_begin.argtypes = [vp, vp, vp, vp, vp, f32, vp]
+    lib.rpca_step_run.argtypes = [vp, i32, vp]
+    lib.rpca_step_sums.argtypes = [vp, ctypes.POINTER(ctypes.POINTER(ctypes.c_float)),
+                                   ctypes.POINTER(ctypes.POINTER(ctypes.c_double))]
+    lib.rpca_step_done.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(Result), vp]
     lib.rpca_prefilter_scratch_bytes.argtypes = [i64, i32]
     lib.rpca_prefilter_scratch_bytes.restype = ctypes.c_size_t
     lib.rpca_prefilter.argtypes = [vp, i64, i32, ctypes.c_double, i32, vp, vp, vp, vp, vp, vp]
