@@ -236,10 +236,12 @@ def _theta(w):
 
 
 def _max_over_ranks(v, world):
+    """The largest of the ranks' values (NCCL on the device, gloo on the host)."""
     if world == 1:
         return v
     import torch
-    t = torch.tensor([v], device="cuda", dtype=torch.float64)
+    dev = "cuda" if torch.distributed.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], device=dev, dtype=torch.float64)
     torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
     return float(t.item())
 
