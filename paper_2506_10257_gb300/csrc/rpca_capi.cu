@@ -588,7 +588,6 @@ static rpca_status plan_create_impl(const rpca_params* p, void* workspace, size_
   c.mu_max_factor = p->mu_max_factor;
   c.tol = p->tol;
   c.jacobi_eps = pl->eig_fp64 ? 1e-12 : 1e-6;
-  if (getenv("RPCA_JACOBI_EPS")) c.jacobi_eps = atof(getenv("RPCA_JACOBI_EPS"));  // tuning override
   c.warm_sweeps = 4;
   c.cold_sweeps = 30;
   c.warm = p->warm_start;
