@@ -375,6 +375,13 @@ __global__ void __launch_bounds__(kWideThreads, 1) pass_wide_kernel(Bufs b) {
 // ---------------------------------------------------------------------------
 constexpr int kRP = 64;   // pixels per tile
 
+// Shared-memory position of pixel pp of frame row t in the frame-major tiles
+// (Z, S, Y/mu): rows of 64 pixels, the pixel index XOR-ed with 4 * ((t / 4) % 8)
+// so that the Eq. 5-6 update, whose threads walk down the columns of a tile 4
+// rows apart, spreads over eight banks instead of one; groups of 4 pixels stay
+// contiguous and 16-byte aligned for the contractions' vector loads.
+__device__ __forceinline__ int res_at(int t, int pp) { return t * kRP + (pp ^ (((t >> 2) & 7) << 2)); }
+
 template <int TP, bool CPLX>
 struct ResShape {
   static constexpr int CPT = TP / 16;                     // columns per thread
@@ -496,20 +503,20 @@ __device__ bool pass_res_body(Bufs b, int lc, int nc, float* smem) {
           const int64_t gi = (int64_t)f * m + pb + pp;
           const float2 x = in ? X2[gi] : make_float2(0.f, 0.f);
           if (MODE == PM_INIT) {
-            sZ[(2 * f) * kRP + pp] = x.x;
-            sZ[(2 * f + 1) * kRP + pp] = x.y;
+            sZ[res_at(2 * f, pp)] = x.x;
+            sZ[res_at(2 * f + 1, pp)] = x.y;
             const float a2 = fmaf(x.x, x.x, x.y * x.y);
             e2 += a2;
             l1 += sqrtf(a2);
           } else {
             const float2 sv = (in && !first) ? S2[gi] : make_float2(0.f, 0.f);
             const float2 yv = (in && !first) ? Y2[gi] : make_float2(0.f, 0.f);
-            sZ[(2 * f) * kRP + pp] = form_z(x.x, sv.x, yv.x, inv_mu);
-            sZ[(2 * f + 1) * kRP + pp] = form_z(x.y, sv.y, yv.y, inv_mu);
-            sS[(2 * f) * kRP + pp] = sv.x;
-            sS[(2 * f + 1) * kRP + pp] = sv.y;
-            sD[(2 * f) * kRP + pp] = yv.x * inv_mu;
-            sD[(2 * f + 1) * kRP + pp] = yv.y * inv_mu;
+            sZ[res_at(2 * f, pp)] = form_z(x.x, sv.x, yv.x, inv_mu);
+            sZ[res_at(2 * f + 1, pp)] = form_z(x.y, sv.y, yv.y, inv_mu);
+            sS[res_at(2 * f, pp)] = sv.x;
+            sS[res_at(2 * f + 1, pp)] = sv.y;
+            sD[res_at(2 * f, pp)] = yv.x * inv_mu;
+            sD[res_at(2 * f + 1, pp)] = yv.y * inv_mu;
           }
         }
       }
@@ -522,32 +529,32 @@ __device__ bool pass_res_body(Bufs b, int lc, int nc, float* smem) {
           const int64_t gi = (int64_t)t * m + pb + pp;
           const float x = in ? job.X[gi] : 0.f;
           if (MODE == PM_INIT) {
-            sZ[t * kRP + pp] = x;
+            sZ[res_at(t, pp)] = x;
             e2 = fmaf(x, x, e2);
             l1 += fabsf(x);
           } else {
             const float sv = (in && !first) ? job.S[gi] : 0.f;
             const float yv = (in && !first) ? Yin[gi] : 0.f;
-            sZ[t * kRP + pp] = form_z(x, sv, yv, inv_mu);
-            sS[t * kRP + pp] = sv;
-            sD[t * kRP + pp] = yv * inv_mu;
+            sZ[res_at(t, pp)] = form_z(x, sv, yv, inv_mu);
+            sS[res_at(t, pp)] = sv;
+            sD[res_at(t, pp)] = yv * inv_mu;
           }
         }
       }
     }
     __syncthreads();
-    auto zrow = [&](int k) { return *reinterpret_cast<const float4*>(&sZ[k * kRP + p0]); };
+    auto zrow = [&](int k) { return *reinterpret_cast<const float4*>(&sZ[res_at(k, p0)]); };
     auto zrow_i = [&](int k) {  // rows of i Z (complex): (-Im, Re) per frame
-      const float4 v = (k & 1) ? *reinterpret_cast<const float4*>(&sZ[(k - 1) * kRP + p0])
-                               : *reinterpret_cast<const float4*>(&sZ[(k + 1) * kRP + p0]);
+      const float4 v = (k & 1) ? *reinterpret_cast<const float4*>(&sZ[res_at(k - 1, p0)])
+                               : *reinterpret_cast<const float4*>(&sZ[res_at(k + 1, p0)]);
       return (k & 1) ? v : make_float4(-v.x, -v.y, -v.z, -v.w);
     };
     if (MODE == PM_INIT) {
       // U = X (standard basis), pixel-major; complex: also the rows of i X
       for (int i = tid; i < TP * kRP; i += kWideThreads) {
         const int t = i / kRP, pp = i % kRP;
-        sU[pp * UP + t] = sZ[t * kRP + pp];
-        if (CPLX) sU[(kRP + pp) * UP + t] = (t & 1) ? sZ[(t - 1) * kRP + pp] : -sZ[(t + 1) * kRP + pp];
+        sU[pp * UP + t] = sZ[res_at(t, pp)];
+        if (CPLX) sU[(kRP + pp) * UP + t] = (t & 1) ? sZ[res_at(t - 1, pp)] : -sZ[res_at(t + 1, pp)];
       }
     } else {
       if (MODE != PM_GRAM) {
@@ -567,9 +574,9 @@ __device__ bool pass_res_body(Bufs b, int lc, int nc, float* smem) {
             for (int j = 0; j < CPT; j += 2) {
               const int t = c0 + j;
               if (t < T) {
-                const float zr = sZ[t * kRP + pp], zi = sZ[(t + 1) * kRP + pp];
-                const float sr = sS[t * kRP + pp], si = sS[(t + 1) * kRP + pp];
-                const float dr = sD[t * kRP + pp], di = sD[(t + 1) * kRP + pp];
+                const float zr = sZ[res_at(t, pp)], zi = sZ[res_at(t + 1, pp)];
+                const float sr = sS[res_at(t, pp)], si = sS[res_at(t + 1, pp)];
+                const float dr = sD[res_at(t, pp)], di = sD[res_at(t + 1, pp)];
                 const float rr = sr + q[i][j], ri = si + q[i][j + 1];
                 const float mag = sqrtf(fmaf(rr, rr, ri * ri));
                 const float f = (mag > gamma) ? gamma / mag : 1.f;
@@ -581,8 +588,8 @@ __device__ bool pass_res_body(Bufs b, int lc, int nc, float* smem) {
                   S2[(int64_t)(t >> 1) * m + pb + pp] = make_float2(rr - cr, ri - ci);
                   Yo2[(int64_t)(t >> 1) * m + pb + pp] = make_float2(ynr, yni);
                 }
-                sZ[t * kRP + pp] = valid ? ((zr - dr) - q[i][j]) + cr + ynr * inv_mu_nxt : 0.f;
-                sZ[(t + 1) * kRP + pp] = valid ? ((zi - di) - q[i][j + 1]) + ci + yni * inv_mu_nxt : 0.f;
+                sZ[res_at(t, pp)] = valid ? ((zr - dr) - q[i][j]) + cr + ynr * inv_mu_nxt : 0.f;
+                sZ[res_at(t + 1, pp)] = valid ? ((zi - di) - q[i][j + 1]) + ci + yni * inv_mu_nxt : 0.f;
               }
             }
           } else {
@@ -590,7 +597,7 @@ __device__ bool pass_res_body(Bufs b, int lc, int nc, float* smem) {
             for (int j = 0; j < CPT; ++j) {
               const int t = c0 + j;
               if (t < T) {
-                const float z = sZ[t * kRP + pp], sv = sS[t * kRP + pp], d = sD[t * kRP + pp];
+                const float z = sZ[res_at(t, pp)], sv = sS[res_at(t, pp)], d = sD[res_at(t, pp)];
                 const float r = sv + q[i][j];                      // X - L + Y/mu
                 const float c = fminf(fmaxf(r, -gamma), gamma);    // clip to +-lambda/mu
                 const float yn = f_mu * c;                         // Eq. 6
@@ -601,7 +608,7 @@ __device__ bool pass_res_body(Bufs b, int lc, int nc, float* smem) {
                   Yout[(int64_t)t * m + pb + pp] = yn;
                 }
                 // Z' = X - S' + Y'/mu' with X = Z + S - Y/mu and S' = S + Q - clip
-                sZ[t * kRP + pp] = valid ? ((z - d) - q[i][j]) + c + yn * inv_mu_nxt : 0.f;
+                sZ[res_at(t, pp)] = valid ? ((z - d) - q[i][j]) + c + yn * inv_mu_nxt : 0.f;
               }
             }
           }
