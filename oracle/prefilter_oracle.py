@@ -21,6 +21,15 @@ applied to the data.  The paper gives no formula; the readings taken here
   j = 0 .. K-w (K kept frames; none when K < w);
 * a frame with zero variance has correlation 0 with every frame.
 
+Sec. IV names a temporal high-pass filter before RPCA (to take out slowly
+varying background motion) as an option, without defining one.  The reading
+taken here is the complement of the same moving average: output frame j is
+the kept frame at the centre of window j minus the window's mean,
+kept[j + h] - mean(kept[j] .. kept[j+w-1]) with h = (w - 1) // 2 (exactly
+centred for odd w), so a signal that is constant or linear in time over a
+window (odd w) gives 0, and a temporal sinusoid of frequency f (cycles per
+frame) is scaled by 1 - sin(pi f w) / (w sin(pi f)).
+
 Frames are rows of a (T, m) array (frame t = row t), the layout of the
 solver's frame-major Casorati matrix.
 """
@@ -81,8 +90,21 @@ def moving_average(frames: np.ndarray, kept: np.ndarray, window: int) -> np.ndar
     return out
 
 
-def prefilter(frames: np.ndarray, corr_min: float = 0.8, window: int = 20):
-    """The reference pre-filter: (filtered frames, kept indices, neighbour correlations)."""
+def highpass(frames: np.ndarray, kept: np.ndarray, window: int) -> np.ndarray:
+    """Temporal high-pass over the kept frames: row j is frame kept[j + h]
+    minus the mean of frames kept[j] .. kept[j+window-1], h = (window-1)//2."""
+    avg = moving_average(frames, kept, window)
+    h = (window - 1) // 2
+    out = np.empty_like(avg)
+    for j in range(avg.shape[0]):
+        out[j] = frames[kept[j + h]].astype(np.float64) - avg[j]
+    return out
+
+
+def prefilter(frames: np.ndarray, corr_min: float = 0.8, window: int = 20, high_pass: bool = False):
+    """The reference pre-filter: (filtered frames, kept indices, neighbour
+    correlations); the moving average, or with high_pass its complement."""
     c = neighbour_correlations(frames) if frames.shape[0] > 1 else np.zeros(0)
     kept = kept_frames(frames, corr_min)
-    return moving_average(frames, kept, window), kept, c
+    filt = highpass if high_pass else moving_average
+    return filt(frames, kept, window), kept, c

@@ -91,3 +91,58 @@ def test_moving_average_skips_excluded_frames():
     want = [np.mean([F[kept[j + i]] for i in range(3)], axis=0) for j in range(len(kept) - 2)]
     np.testing.assert_allclose(out, np.array(want), rtol=1e-15)
     assert out[2, 0] == pytest.approx((2 + 4 + 5) / 3.0)
+
+
+def test_highpass_removes_constant_and_linear_trends():
+    # centred window (odd w): the mean of a linear sequence is its centre value
+    m, T, w = 5, 25, 7
+    v = np.linspace(-2.0, 3.0, m)
+    kept = np.arange(T)
+    trend = 4.0 + np.arange(T, dtype=np.float64)[:, None] * v[None, :]
+    out = P.highpass(trend, kept, w)
+    assert out.shape == (T - w + 1, m)
+    np.testing.assert_allclose(out, 0.0, atol=1e-12)
+    # even window: centre half a frame early, so a unit ramp leaves -1/2
+    np.testing.assert_allclose(P.highpass(np.arange(T, dtype=np.float64)[:, None], kept, 6), -0.5, atol=1e-12)
+
+
+def test_highpass_frequency_response_of_a_temporal_sinusoid():
+    # a centred w-frame mean scales cos(2 pi f t + phi) by sin(pi f w) / (w sin(pi f))
+    T, w = 60, 9
+    t = np.arange(T, dtype=np.float64)
+    kept = np.arange(T)
+    h = (w - 1) // 2
+    for f, phi in [(0.05, 0.3), (0.21, -1.1), (1.0 / w, 0.7), (3.0 / w, 2.0), (0.5, 0.0)]:
+        x = np.cos(2 * np.pi * f * t + phi)[:, None] * np.array([[1.0, -0.5]])
+        H = np.sin(np.pi * f * w) / (w * np.sin(np.pi * f))
+        want = (1.0 - H) * x[h:h + T - w + 1]
+        np.testing.assert_allclose(P.highpass(x, kept, w), want, atol=1e-12)
+    # at multiples of 1/w the window mean is zero: the sinusoid passes unchanged
+    x = np.sin(2 * np.pi * (2.0 / w) * t)[:, None]
+    np.testing.assert_allclose(P.highpass(x, kept, w), x[h:h + T - w + 1], atol=1e-12)
+
+
+def test_highpass_brute_force_with_excluded_frames():
+    rng = np.random.default_rng(11)
+    T, m, w = 11, 4, 4
+    F = rng.standard_normal((T, m))
+    kept = np.array([0, 2, 3, 4, 6, 7, 8, 10])
+    out = P.highpass(F, kept, w)
+    assert out.shape == (len(kept) - w + 1, m)
+    for j in range(out.shape[0]):
+        for p in range(m):
+            s = 0.0
+            for i in range(w):
+                s += F[kept[j + i], p]
+            assert out[j, p] == pytest.approx(F[kept[j + 1], p] - s / w, abs=1e-14)
+    assert P.highpass(F, np.arange(3), 4).shape == (0, m)
+    np.testing.assert_array_equal(P.highpass(F, kept, 1), 0.0)   # a one-frame window removes everything
+
+
+def test_prefilter_high_pass_is_frames_minus_average():
+    F = smooth_frames(12, 30, 200)
+    avg, kept, c = P.prefilter(F, 0.8, 5)
+    hp, kept2, c2 = P.prefilter(F, 0.8, 5, high_pass=True)
+    np.testing.assert_array_equal(kept, kept2)
+    np.testing.assert_array_equal(c, c2)
+    np.testing.assert_allclose(hp + avg, F[kept[2:2 + avg.shape[0]]], atol=1e-13)
