@@ -610,14 +610,15 @@ def run_frames_sweep(args):
 def run_prefilter(args):
     """The frame pre-filter of the in vivo reference on its shape: a 338 x 260
     window of 132 frames (three frames displaced by a whole-image shift),
-    frames below 0.8 neighbour correlation dropped, 20-frame moving average.
-    Device-timed (CUDA events, L2 flushed before each call); the oracle timed on
+    frames below 0.8 neighbour correlation dropped, 20-frame moving average
+    (--high-pass: the centre frame minus that average).  Device-timed (CUDA events, L2 flushed before each call); the oracle timed on
     the host cores on the same window."""
     import numpy as np
     import torch
     from paper_2506_10257_gb300 import synth
     rpca, rank, local_rank, world = _setup(args)
     ny, nx, T, wdw = 338, 260, 132, 20
+    hp = bool(args.high_pass)
     w = synth.make_window(seed=4242 + rank, ny=ny, nx=nx, T=T, n_bound=200, n_free=400, speed=(0.5, 5.0))
     F = w.frames.copy()
     for t in (40, 41, 90):
@@ -626,7 +627,7 @@ def run_prefilter(args):
     X = torch.from_numpy(F).cuda()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
-        Y, kept, corr = rpca.prefilter(X, 0.8, wdw)
+        Y, kept, corr = rpca.prefilter(X, 0.8, wdw, high_pass=hp)
     K, n = int(kept.numel()), int(Y.shape[0])
     bufs = rpca.prefilter_buffers(X, wdw)     # allocated once: the timed calls launch kernels only
     ms = []
@@ -635,28 +636,33 @@ def run_prefilter(args):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record()
-        rpca.prefilter(X, 0.8, wdw, wait=False, out=bufs)
+        rpca.prefilter(X, 0.8, wdw, wait=False, out=bufs, high_pass=hp)
         e1.record()
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
     ms_mean = statistics.mean(ms)
-    alg = 4 * m * (T + K + n)                    # read X (statistics), read the kept frames, write the averages
+    alg = 4 * m * (T + K + n)                    # read X (statistics), read the kept frames, write the outputs
+    aop = 8 if hp else 6
     line = {
         "metric": "pre-filters/s", "value": world * 1000.0 / ms_mean, "unit": "pre-filters/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mean, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64 accumulation, f32 data",
         "data": "synthetic (seeded microbubble window, three frames displaced)",
-        "config": {"workload": f"frame pre-filter, {ny}x{nx} px x {T} frames (corr >= 0.8, {wdw}-frame average)",
-                   "form": "rpca_prefilter (statistics, decision, moving average; stream-ordered)",
+        "config": {"workload": f"frame pre-filter, {ny}x{nx} px x {T} frames (corr >= 0.8, {wdw}-frame "
+                               + ("high-pass)" if hp else "average)"),
+                   "form": ("rpca_prefilter_highpass (statistics, decision, centre frame minus moving average"
+                            if hp else "rpca_prefilter (statistics, decision, moving average")
+                           + "; stream-ordered)",
                    "l2": "flushed before every call (256 MB write, outside the events)"},
         "kept_frames": K, "output_frames": n,
         # FP64 pipe operations of a call: statistics 7 per element (two FP32->FP64
         # conversions, two shifts, the sum, two FMAs), averages 6 per output
-        # (two conversions, two adds, the scale, the FP32 conversion); peak: the
+        # (two conversions, two adds, the scale, the FP32 conversion; the high-pass
+        # two more: the centre frame's conversion and the subtraction); peak: the
         # measured FP64 FMA rate of 1.89 per SM per clock x 152 SMs x 2.07 GHz
-        "roofline": {"bound": "alu (FP64 pipe)", "achieved": (7 * T * m + 6 * n * m) / (ms_mean * 1e-3) / 1e9,
+        "roofline": {"bound": "alu (FP64 pipe)", "achieved": (7 * T * m + aop * n * m) / (ms_mean * 1e-3) / 1e9,
                      "peak": 152 * 1.89 * 2.07, "unit": "GFLOP/s (FP64 pipe ops)",
-                     "frac": (7 * T * m + 6 * n * m) / (ms_mean * 1e-3) / 1e9 / (152 * 1.89 * 2.07),
+                     "frac": (7 * T * m + aop * n * m) / (ms_mean * 1e-3) / 1e9 / (152 * 1.89 * 2.07),
                      "traffic": None, "hbm_achieved_gbs": alg / (ms_mean * 1e-3) / 1e9,
                      "hbm_peak_gbs": measured_peaks()[0], "algorithmic_bytes_per_launch": alg},
         "gpu_launches": 3 * args.steps,
@@ -665,7 +671,7 @@ def run_prefilter(args):
         from oracle import prefilter_oracle as P
         import os as _os
         t0 = time.perf_counter()
-        Yo, ko, _ = P.prefilter(F, 0.8, wdw)
+        Yo, ko, _ = P.prefilter(F, 0.8, wdw, high_pass=hp)
         cpu_s = time.perf_counter() - t0
         Yg = Y.cpu().numpy().astype(np.float64)
         line["cpu_baseline"] = {"value": 1.0 / cpu_s, "unit": "pre-filters/s", "cores": _os.cpu_count(),
@@ -983,6 +989,7 @@ def main():
     ap.add_argument("--duration", type=float, default=1.0, help="seconds of simulated streaming (probes8)")
     ap.add_argument("--cold", action="store_true", help="served streaming without warm start")
     ap.add_argument("--cold-every", type=int, default=0, help="served streaming: every n-th window cold")
+    ap.add_argument("--high-pass", action="store_true", help="prefilter: the temporal high-pass variant")
     ap.add_argument("--drive", choices=["graph", "stream", "host"], default="graph",
                     help="graph: the product path; stream: same kernels launched one by one (for ncu); "
                          "host: the plain unfused form")

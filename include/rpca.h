@@ -409,6 +409,19 @@ size_t rpca_prefilter_scratch_bytes(int64_t m, int32_t T);
 rpca_status rpca_prefilter(const float* X, int64_t m, int32_t T, double corr_min, int32_t window, float* Y,
                            int32_t* kept, int32_t* count, double* corr, void* scratch, void* stream);
 
+/* Temporal high-pass variant of rpca_prefilter.  Sec. IV suggests a
+ * high-pass temporal filter before RPCA to take out slowly varying background
+ * motion, without defining one; it is read here as the complement of the
+ * moving average above: output frame j is kept frame j + h minus the mean of
+ * kept frames j .. j+window-1, h = (window - 1) / 2 rounded down (the window's
+ * centre for odd window), so what is constant or linear in time over a window
+ * (odd window) is removed.  Same arguments, outputs, frame exclusion, scratch
+ * and errors as rpca_prefilter; Y receives the high-passed frames (the
+ * difference formed in FP64, rounded once to FP32). */
+rpca_status rpca_prefilter_highpass(const float* X, int64_t m, int32_t T, double corr_min, int32_t window,
+                                    float* Y, int32_t* kept, int32_t* count, double* corr, void* scratch,
+                                    void* stream);
+
 #ifdef __cplusplus
 }
 #endif

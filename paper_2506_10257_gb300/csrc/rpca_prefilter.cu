@@ -21,6 +21,11 @@
 //                     in FP64, formed directly for the first output and slid
 //                     for the rest (exact for FP32 inputs of similar
 //                     magnitude), each output frame written as FP32.
+//
+// The temporal high-pass that Sec. IV suggests before RPCA (no filter is
+// defined there) is read as the complement of the same moving average: output
+// j = kept frame j + (w-1)/2 (rounded down) minus the mean of window j, formed
+// in FP64 from the same sliding sum and rounded once to FP32.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -132,7 +137,9 @@ constexpr int kPfSeg = 16;  // output frames of one moving-average thread
 
 // kept list in dynamic shared memory (T ints).  Work item (segment g, pixel p):
 // output frames g*kPfSeg .. +kPfSeg-1 of pixel p; items run pixel-fastest, so
-// a warp reads and writes 32 consecutive pixels of one frame.
+// a warp reads and writes 32 consecutive pixels of one frame.  HP: write the
+// centre frame minus the mean instead of the mean.
+template <bool HP>
 __global__ void __launch_bounds__(kPfThreads) pf_average_kernel(const float* __restrict__ X, int64_t m, int T,
                                                                 const int* __restrict__ kept,
                                                                 const int* __restrict__ count, int window,
@@ -143,7 +150,12 @@ __global__ void __launch_bounds__(kPfThreads) pf_average_kernel(const float* __r
   const int n = count[1];
   if (n <= 0) return;
   const double inv_w = 1.0 / (double)window;
+  const int h = (window - 1) / 2;
   const int64_t nseg = (n + kPfSeg - 1) / kPfSeg;
+  auto out = [&](int j, int64_t p, double s) {
+    const double mean = s * inv_w;
+    Y[(int64_t)j * m + p] = HP ? (float)((double)X[(int64_t)pf_kept[j + h] * m + p] - mean) : (float)mean;
+  };
   for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < nseg * m;
        it += (int64_t)gridDim.x * blockDim.x) {
     const int64_t p = it % m;
@@ -152,26 +164,18 @@ __global__ void __launch_bounds__(kPfThreads) pf_average_kernel(const float* __r
     double s = 0.0;
 #pragma unroll 4
     for (int i = 0; i < window; ++i) s += (double)X[(int64_t)pf_kept[j0 + i] * m + p];
-    Y[(int64_t)j0 * m + p] = (float)(s * inv_w);
+    out(j0, p, s);
     for (int j = j0 + 1; j < j1; ++j) {
       s += (double)X[(int64_t)pf_kept[j + window - 1] * m + p];
       s -= (double)X[(int64_t)pf_kept[j - 1] * m + p];
-      Y[(int64_t)j * m + p] = (float)(s * inv_w);
+      out(j, p, s);
     }
   }
 }
 
-}  // namespace
-
-extern "C" {
-
-size_t rpca_prefilter_scratch_bytes(int64_t m, int32_t T) {
-  if (m < 1 || T < 1) return 0;
-  return sizeof(double) * 3 * (size_t)T * (size_t)pf_chunks(m);
-}
-
-rpca_status rpca_prefilter(const float* X, int64_t m, int32_t T, double corr_min, int32_t window, float* Y,
-                           int32_t* kept, int32_t* count, double* corr, void* scratch, void* stream) {
+rpca_status prefilter_impl(const float* X, int64_t m, int32_t T, double corr_min, int32_t window, float* Y,
+                           int32_t* kept, int32_t* count, double* corr, void* scratch, void* stream,
+                           bool high_pass) {
   if (!X || !Y || !kept || !count || !scratch || m < 1 || T < 1 || window < 1 || !(corr_min == corr_min))
     return RPCA_ERR_ARG;
   if (((uintptr_t)X | (uintptr_t)Y) & 3u) return RPCA_ERR_ARG;
@@ -194,8 +198,31 @@ rpca_status rpca_prefilter(const float* X, int64_t m, int32_t T, double corr_min
   const int64_t items = m * (int64_t)((T + kPfSeg - 1) / kPfSeg);  // at most this many (segment, pixel) items
   const int64_t want = (items + kPfThreads - 1) / kPfThreads;
   const int grid = (int)(want < (int64_t)sms * 8 ? want : (int64_t)sms * 8);
-  pf_average_kernel<<<grid, kPfThreads, sizeof(int) * (size_t)T, s>>>(X, m, T, kept, count, window, Y);
+  if (high_pass)
+    pf_average_kernel<true><<<grid, kPfThreads, sizeof(int) * (size_t)T, s>>>(X, m, T, kept, count, window, Y);
+  else
+    pf_average_kernel<false><<<grid, kPfThreads, sizeof(int) * (size_t)T, s>>>(X, m, T, kept, count, window, Y);
   return cudaGetLastError() == cudaSuccess ? RPCA_OK : RPCA_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t rpca_prefilter_scratch_bytes(int64_t m, int32_t T) {
+  if (m < 1 || T < 1) return 0;
+  return sizeof(double) * 3 * (size_t)T * (size_t)pf_chunks(m);
+}
+
+rpca_status rpca_prefilter(const float* X, int64_t m, int32_t T, double corr_min, int32_t window, float* Y,
+                           int32_t* kept, int32_t* count, double* corr, void* scratch, void* stream) {
+  return prefilter_impl(X, m, T, corr_min, window, Y, kept, count, corr, scratch, stream, false);
+}
+
+rpca_status rpca_prefilter_highpass(const float* X, int64_t m, int32_t T, double corr_min, int32_t window,
+                                    float* Y, int32_t* kept, int32_t* count, double* corr, void* scratch,
+                                    void* stream) {
+  return prefilter_impl(X, m, T, corr_min, window, Y, kept, count, corr, scratch, stream, true);
 }
 
 }  // extern "C"

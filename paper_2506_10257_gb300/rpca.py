@@ -32,7 +32,7 @@ EXPORTED = ["rpca_params_default", "rpca_workspace_size", "rpca_plan_create", "r
             "rpca_batch_tune", "rpca_batch_info", "rpca_batch_window_ctas", "rpca_batch_destroy",
             "rpca_server_create", "rpca_server_set_warm", "rpca_submit", "rpca_poll", "rpca_server_wait",
             "rpca_server_stats", "rpca_server_destroy", "rpca_prefilter_scratch_bytes", "rpca_prefilter",
-            "rpca_step_begin", "rpca_step_run", "rpca_step_sums", "rpca_step_done"]
+            "rpca_prefilter_highpass", "rpca_step_begin", "rpca_step_run", "rpca_step_sums", "rpca_step_done"]
 
 
 class Params(ctypes.Structure):
@@ -107,6 +107,7 @@ def load(build_if_missing: bool = True):
     lib.rpca_prefilter_scratch_bytes.argtypes = [i64, i32]
     lib.rpca_prefilter_scratch_bytes.restype = ctypes.c_size_t
     lib.rpca_prefilter.argtypes = [vp, i64, i32, ctypes.c_double, i32, vp, vp, vp, vp, vp, vp]
+    lib.rpca_prefilter_highpass.argtypes = [vp, i64, i32, ctypes.c_double, i32, vp, vp, vp, vp, vp, vp]
     lib.rpca_plan_timings.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i32]
     lib.rpca_batch_create.argtypes = [ctypes.POINTER(Params), i32, ctypes.POINTER(vp)]
     lib.rpca_batch_solve.argtypes = [vp, ctypes.POINTER(Window), vp, ctypes.POINTER(Result)]
@@ -340,10 +341,12 @@ def prefilter_buffers(frames, window: int = 20):
     return Y, kept, count, corr, scratch
 
 
-def prefilter(frames, corr_min: float = 0.8, window: int = 20, stream=None, wait: bool = True, out=None):
+def prefilter(frames, corr_min: float = 0.8, window: int = 20, stream=None, wait: bool = True, out=None,
+              high_pass: bool = False):
     """Frame pre-filter of the in vivo reference (rpca_prefilter): frames that
     correlate below corr_min with every neighbour are dropped, then a whole-window
-    moving average of `window` frames runs over the kept frames.  frames: (T, m)
+    moving average of `window` frames runs over the kept frames (with high_pass,
+    rpca_prefilter_highpass: the window's centre frame minus that average).  frames: (T, m)
     float32 CUDA tensor.  Returns (Y, kept, corr): Y (n, m) float32 with
     n = max(K - window + 1, 0), kept (K,) int32 indices, corr (T - 1,) float64.
     With wait=False the full-size buffers and the device counts are returned
@@ -355,13 +358,14 @@ def prefilter(frames, corr_min: float = 0.8, window: int = 20, stream=None, wait
     T, m = frames.shape
     lib = load()
     Y, kept, count, corr, scratch = out if out is not None else prefilter_buffers(frames, window)
-    st = lib.rpca_prefilter(ctypes.c_void_p(frames.data_ptr()), m, T, float(corr_min), int(window),
+    fn = lib.rpca_prefilter_highpass if high_pass else lib.rpca_prefilter
+    st = fn(ctypes.c_void_p(frames.data_ptr()), m, T, float(corr_min), int(window),
                             ctypes.c_void_p(Y.data_ptr() if Y.numel() else frames.data_ptr()),
                             ctypes.c_void_p(kept.data_ptr()), ctypes.c_void_p(count.data_ptr()),
                             ctypes.c_void_p(corr.data_ptr() if corr.numel() else 0),
                             ctypes.c_void_p(scratch.data_ptr()), _stream_handle(stream))
     if st != OK:
-        raise RpcaError(st, "rpca_prefilter")
+        raise RpcaError(st, "rpca_prefilter_highpass" if high_pass else "rpca_prefilter")
     if not wait:
         return Y, kept, corr, count
     torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
