@@ -37,6 +37,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "w512x512_t20"
+WORKLOAD_DESC = WORKLOAD + " (512x512 px x 20 frames, Casorati 262144x20, fp32)"
 HBM_FALLBACK_GBS = 6800.0
 
 
@@ -205,7 +206,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": est * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic (seeded microbubble window)",
-        "config": {"workload": WORKLOAD + " (Casorati 262144x20)", "tol": 1e-7},
+        "config": {"workload": WORKLOAD_DESC, "tol": 1e-7},
         "cpu_baseline": {"value": val, "unit": "solves/s", "cores": cores(), "kind": "oracle",
                          "sample": f"first {strip} pixels (32 image rows) x 20 frames per step, "
                                    f"time x{scale:.0f}; oracle iterations {its[0]}"},
@@ -422,7 +423,7 @@ def run_batch(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded microbubble windows, in HBM)",
-        "config": {"workload": WORKLOAD + " (512x512 px x 20 frames, Casorati 262144x20, fp32)",
+        "config": {"workload": WORKLOAD_DESC,
                    "form": f"batched persistent launch, {NB} windows per step (different seeds)",
                    "precision": "fp32", "tol": 1e-7,
                    "l2": "flushed before every step (256 MB write, outside step events); "
@@ -502,7 +503,7 @@ def run_serve(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded microbubble windows, in HBM)",
-        "config": {"workload": WORKLOAD + " (512x512 px x 20 frames, Casorati 262144x20, fp32)",
+        "config": {"workload": WORKLOAD_DESC,
                    "form": f"served: {NB} probes submit one window each per step, {args.slots} slots, cold starts",
                    "precision": args.precision, "tol": 1e-7,
                    "l2": "flushed before every step (256 MB write, outside step events)"},
