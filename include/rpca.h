@@ -233,6 +233,25 @@ rpca_status rpca_batch_info(rpca_batch_t batch, int32_t* info, int32_t n);
 /* CTAs each window uses (n >= number of windows). */
 rpca_status rpca_batch_window_ctas(rpca_batch_t batch, int32_t* ctas, int32_t n);
 
+/* The batch form's CTA schedule as a pure host computation (no device call),
+ * for inspecting a schedule before creating a batch.  Windows go to lanes
+ * (contiguous CTA ranges that run their windows one after another) by
+ * longest-processing-time first on m[w] * T[w], equal loads in index order;
+ * L = min(lanes, n, ctas) lanes; lane l gets CTAs proportional to (its load)^alpha,
+ * at least one and at most the largest max_ctas[w] of its windows (NULL: no
+ * limit), summing to at most `ctas`, fractional shares settled by largest
+ * remainders.  rpca_batch_create and rpca_batch_tune build their schedules
+ * with this computation (ctas = SMs x CTAs per SM, max_ctas the windows' useful
+ * CTA counts).  Outputs: *n_lanes = L; lane_ctas[0..L) the lanes' CTAs;
+ * order[0..n) the windows in lane order, lane l running order[lane_end[l-1] ..
+ * lane_end[l]) (lane_end[-1] = 0) in descending load; lane_ctas and lane_end
+ * need n entries.  Errors: RPCA_ERR_ARG (n < 1, a null pointer other than
+ * max_ctas, ctas < 1, lanes < 1, alpha negative or not finite, an m, T or
+ * max_ctas entry < 1). */
+rpca_status rpca_batch_schedule(int32_t n, const int64_t* m, const int32_t* T, const int32_t* max_ctas,
+                                int32_t ctas, int32_t lanes, double alpha, int32_t* n_lanes, int32_t* lane_ctas,
+                                int32_t* order, int32_t* lane_end);
+
 void rpca_batch_destroy(rpca_batch_t batch);
 
 /* ---- served form ----------------------------------------------------------- */

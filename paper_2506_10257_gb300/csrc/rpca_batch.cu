@@ -117,33 +117,41 @@ namespace {
 
 double window_load(const rpca_params& p) { return (double)p.m * (double)p.T; }
 
-// Lanes, their CTAs and the window order for configuration cfg.
-void make_schedule(rpca_batch_s* b, const BatchConfig& cfg) {
-  const int n = b->n;
-  const int C = b->sms * cfg.ctas_per_sm;
-  int L = std::max(1, std::min({cfg.lanes, n, C}));
+// The lanes of a schedule: the windows each lane runs, in order, and its CTAs.
+struct LanePlan {
+  std::vector<std::vector<int>> lw;
+  std::vector<int> nc;
+};
+
+// Windows go to lanes by longest-processing-time first on wload (equal loads
+// keep their index order); lane CTAs ~ (lane load)^alpha, at least one, at
+// most the largest wcap of the lane's windows, summing to at most C, the
+// fractional shares settled by largest remainders.  L = min(lanes, n, C).
+LanePlan plan_lanes(const std::vector<double>& wload, const std::vector<int>& wcap, int C, int lanes,
+                    double alpha) {
+  const int n = (int)wload.size();
+  const int L = std::max(1, std::min({lanes, n, C}));
   std::vector<int> order(n);
   std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int a, int c) { return window_load(b->p[a]) > window_load(b->p[c]); });
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return wload[a] > wload[c]; });
   std::vector<double> load(L, 0.0);
   std::vector<std::vector<int>> lw(L);
   for (int w : order) {
     int best = 0;
     for (int l = 1; l < L; ++l)
       if (load[l] < load[best]) best = l;
-    load[best] += window_load(b->p[w]);
+    load[best] += wload[w];
     lw[best].push_back(w);
   }
   // useful CTAs of a lane: its largest window's partial capacity
   std::vector<int> cap(L, 1);
   for (int l = 0; l < L; ++l)
-    for (int w : lw[l]) cap[l] = std::max(cap[l], b->views[w].max_grid);
+    for (int w : lw[l]) cap[l] = std::max(cap[l], wcap[w]);
   // CTAs ~ load^alpha, at least one, at most cap, summing to <= C
   std::vector<int> nc(L, 1);
   int left = C - L;
   std::vector<double> wgt(L);
-  for (int l = 0; l < L; ++l) wgt[l] = pow(std::max(load[l], 1.0), cfg.alpha);
+  for (int l = 0; l < L; ++l) wgt[l] = pow(std::max(load[l], 1.0), alpha);
   for (int pass = 0; pass < 4 && left > 0; ++pass) {
     double tot = 0;
     for (int l = 0; l < L; ++l)
@@ -173,6 +181,23 @@ void make_schedule(rpca_batch_s* b, const BatchConfig& cfg) {
     }
     if (given == 0) break;
   }
+  return {std::move(lw), std::move(nc)};
+}
+
+// Lanes, their CTAs and the window order for configuration cfg.
+void make_schedule(rpca_batch_s* b, const BatchConfig& cfg) {
+  const int n = b->n;
+  const int C = b->sms * cfg.ctas_per_sm;
+  std::vector<double> wload(n);
+  std::vector<int> wcap(n);
+  for (int w = 0; w < n; ++w) {
+    wload[w] = window_load(b->p[w]);
+    wcap[w] = b->views[w].max_grid;
+  }
+  const LanePlan lp = plan_lanes(wload, wcap, C, cfg.lanes, cfg.alpha);
+  const int L = (int)lp.nc.size();
+  const std::vector<std::vector<int>>& lw = lp.lw;
+  const std::vector<int>& nc = lp.nc;
   b->lanes.assign(L, LaneDesc{});
   b->slot_win.clear();
   b->win_slot.assign(n, 0);
@@ -516,6 +541,34 @@ rpca_status rpca_batch_tune(rpca_batch_t b, const rpca_window* win, void* stream
     g_tune_cache[b->signature] = best_cfg;
   }
   if (best_ms) *best_ms = best;
+  return RPCA_OK;
+}
+
+rpca_status rpca_batch_schedule(int32_t n, const int64_t* m, const int32_t* T, const int32_t* max_ctas,
+                                int32_t ctas, int32_t lanes, double alpha, int32_t* n_lanes, int32_t* lane_ctas,
+                                int32_t* order, int32_t* lane_end) {
+  if (n < 1 || !m || !T || !n_lanes || !lane_ctas || !order || !lane_end || ctas < 1 || lanes < 1 ||
+      !(alpha >= 0.0) || !isfinite(alpha))
+    return RPCA_ERR_ARG;
+  std::vector<double> wload(n);
+  std::vector<int> wcap(n);
+  for (int w = 0; w < n; ++w) {
+    if (m[w] < 1 || T[w] < 1 || (max_ctas && max_ctas[w] < 1)) return RPCA_ERR_ARG;
+    rpca_params p{};
+    p.m = m[w];
+    p.T = T[w];
+    wload[w] = window_load(p);
+    wcap[w] = max_ctas ? max_ctas[w] : ctas;
+  }
+  const LanePlan lp = plan_lanes(wload, wcap, ctas, lanes, alpha);
+  const int L = (int)lp.nc.size();
+  *n_lanes = L;
+  int k = 0;
+  for (int l = 0; l < L; ++l) {
+    lane_ctas[l] = lp.nc[l];
+    for (int w : lp.lw[l]) order[k++] = w;
+    lane_end[l] = k;
+  }
   return RPCA_OK;
 }
 

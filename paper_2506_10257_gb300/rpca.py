@@ -29,7 +29,7 @@ MAX_T_NARROW = 32
 EXPORTED = ["rpca_params_default", "rpca_workspace_size", "rpca_plan_create", "rpca_solve", "rpca_solve_host",
             "rpca_plan_result", "rpca_plan_destroy", "rpca_status_str", "rpca_gram", "rpca_eig",
             "rpca_gram_noalloc", "rpca_plan_timings", "rpca_batch_create", "rpca_batch_solve",
-            "rpca_batch_tune", "rpca_batch_info", "rpca_batch_window_ctas", "rpca_batch_destroy",
+            "rpca_batch_tune", "rpca_batch_info", "rpca_batch_window_ctas", "rpca_batch_destroy", "rpca_batch_schedule",
             "rpca_server_create", "rpca_server_set_warm", "rpca_submit", "rpca_poll", "rpca_server_wait",
             "rpca_server_stats", "rpca_server_destroy", "rpca_prefilter_scratch_bytes", "rpca_prefilter",
             "rpca_prefilter_highpass", "rpca_step_begin", "rpca_step_run", "rpca_step_sums", "rpca_step_done"]
@@ -114,6 +114,7 @@ def load(build_if_missing: bool = True):
     lib.rpca_batch_tune.argtypes = [vp, ctypes.POINTER(Window), vp, i32, ctypes.POINTER(ctypes.c_double)]
     lib.rpca_batch_info.argtypes = [vp, ctypes.POINTER(i32), i32]
     lib.rpca_batch_window_ctas.argtypes = [vp, ctypes.POINTER(i32), i32]
+    lib.rpca_batch_schedule.argtypes = [i32, vp, vp, vp, i32, i32, ctypes.c_double, ctypes.POINTER(i32), vp, vp, vp]
     lib.rpca_batch_destroy.argtypes = [vp]
     lib.rpca_batch_destroy.restype = None
     lib.rpca_server_create.argtypes = [ctypes.c_size_t, i32, ctypes.POINTER(vp)]
@@ -371,6 +372,30 @@ def prefilter(frames, corr_min: float = 0.8, window: int = 20, stream=None, wait
     torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
     K, n = (int(v) for v in count.cpu().tolist())
     return Y[:n], kept[:K], corr
+
+
+def batch_schedule(shapes, ctas: int, lanes: int, alpha: float = 1.0, max_ctas=None):
+    """The batch form's CTA schedule (rpca_batch_schedule, host only) for
+    windows of shapes [(m, T), ...] on `ctas` resident CTAs: a list of
+    (lane CTAs, [window indices in run order]) per lane."""
+    import numpy as np
+    n = len(shapes)
+    m = np.ascontiguousarray([s[0] for s in shapes], dtype=np.int64)
+    T = np.ascontiguousarray([s[1] for s in shapes], dtype=np.int32)
+    cap = None if max_ctas is None else np.ascontiguousarray(max_ctas, dtype=np.int32)
+    nl = ctypes.c_int32()
+    lc, order, end = (np.zeros(max(n, 1), dtype=np.int32) for _ in range(3))
+    st = load().rpca_batch_schedule(n, m.ctypes.data if n else None, T.ctypes.data if n else None,
+                                    cap.ctypes.data if cap is not None else None, int(ctas), int(lanes),
+                                    float(alpha), ctypes.byref(nl), lc.ctypes.data, order.ctypes.data,
+                                    end.ctypes.data)
+    if st != OK:
+        raise RpcaError(st, "rpca_batch_schedule")
+    out, k = [], 0
+    for l in range(nl.value):
+        out.append((int(lc[l]), [int(w) for w in order[k:end[l]]]))
+        k = int(end[l])
+    return out
 
 
 class Batch:
