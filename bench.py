@@ -3,7 +3,7 @@
 512x512-pixel x 20-frame windows (Casorati 262144 x 20, float32).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--form batch|plan|serve] [--precision fp32|tf32x3|bf16x3|tf32]
+                    [--form batch|plan|serve] [--precision fp32|tf32x3|bf16x3]
 
 Every solve is complete: init pass, every iteration until the relative
 residual is <= 1e-7, final L and mask, of seeded synthetic windows resident
@@ -61,39 +61,38 @@ def measured_peaks():
     return HBM_FALLBACK_GBS, "fallback"
 
 
-def ncu_traffic(kernel_src_hash: str):
-    """DRAM bytes per launch of the fused pass from the committed ncu summary,
-    or None when the summary was taken on a different kernel source."""
-    path = os.path.join(ROOT, "profiles", "fused_pass_w512x512_t20.md")
+def _ncu_entry(name: str, kernel_src_hash: str):
+    """Entry `name` of profiles/ncu_traffic.json (the machine-readable DRAM
+    traffic of the committed ncu captures), or None when it is missing or was
+    taken on a different kernel source."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
-    src_hash, traffic = None, None
-    for line in open(path):
-        if line.startswith("kernel_source_sha256:"):
-            src_hash = line.split(":", 1)[1].strip()
-        if line.startswith("dram_bytes_per_launch:"):
-            traffic = float(line.split(":", 1)[1].strip())
-    return traffic if src_hash == kernel_src_hash else None
+    with open(path) as f:
+        e = json.load(f).get(name)
+    if not e or e.get("kernel_source_sha256") != kernel_src_hash:
+        return None
+    return e
+
+
+def ncu_traffic(kernel_src_hash: str):
+    """DRAM bytes per launch of the fused pass (committed ncu capture)."""
+    e = _ncu_entry("fused_pass", kernel_src_hash)
+    return float(e["dram_bytes_per_launch"]) if e else None
 
 
 def ncu_batch_traffic(kernel_src_hash: str, iters):
     """DRAM bytes of one persistent batch launch, from the committed ncu
-    capture of the same kernel on 4 windows of this workload: its bytes per
-    window solve (32 iterations) scaled to these windows by their iteration
-    counts (traffic grows with the iterations run).  None for another kernel
-    source."""
-    path = os.path.join(ROOT, "profiles", "batch_kernel_4x262144x20.md")
-    if not os.path.exists(path):
+    capture of the same kernel on windows of this workload: its bytes per
+    window solve scaled to these windows by their iteration counts (a solve's
+    traffic grows with its iterations: the initial and final steps read and
+    write about 1 + 5 window arrays, each iteration 5).  None for another
+    kernel source."""
+    e = _ncu_entry("batch_kernel", kernel_src_hash)
+    if not e:
         return None
-    src_hash, per_window = None, None
-    for line in open(path):
-        if line.startswith("kernel_source_sha256:"):
-            src_hash = line.split(":", 1)[1].strip()
-        if line.startswith("dram_bytes_per_window_solve:"):
-            per_window = float(line.split(":", 1)[1].strip())
-    if src_hash != kernel_src_hash or per_window is None:
-        return None
-    return sum(per_window * (1 + 5 * it + 5) / (1 + 5 * 32 + 5) for it in iters)
+    per_window, it0 = float(e["dram_bytes_per_window_solve"]), int(e["iters_per_window"])
+    return sum(per_window * (1 + 5 * it + 5) / (1 + 5 * it0 + 5) for it in iters)
 
 
 def kernel_source_hash() -> str:
@@ -179,37 +178,39 @@ def window(seed: int, workload: str = WORKLOAD, complex_iq: bool = False):
 
 
 def run_reference(args):
-    """CPU FP64 oracle on bounded samples: a 32-row strip (16384 pixels x 20
-    frames) of the window per step; the 262144-pixel solve time is estimated
-    as 16x the strip (the oracle's per-iteration cost is linear in pixels)."""
+    """The reference arm: the CPU FP64 oracle (NumPy + LAPACK thin SVD per
+    iteration), as it stands, on the host cores.  Every timed step solves one
+    whole 262144 x 20 window of the GPU arm's workload (about 4 s on 16 Grace
+    cores), so value, ms_per_step and steps describe exactly what ran; the
+    untimed warm-up steps solve a 16384-pixel strip of it (they only bring up
+    the BLAS threads)."""
     rank, _, world = dist_env()
     if rank != 0:
         return 0
     import numpy as np
     from oracle import rpca_oracle as O
     w = window(1)
-    strip = 16384
-    F = np.ascontiguousarray(w.frames[:, :strip])
-    scale = w.m / strip
     for _ in range(args.warmup):
-        O.rpca_frames(F)
+        O.rpca_frames(np.ascontiguousarray(w.frames[:, :16384]))
     ts, its = [], []
+    t_run = time.perf_counter()
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        r = O.rpca_frames(F)
+        r = O.rpca_frames(w.frames)
         ts.append(time.perf_counter() - t0)
         its.append(r.iters)
-    est = statistics.mean(ts) * scale
-    val = 1.0 / est
+    wall = time.perf_counter() - t_run
+    ms_per_step = 1e3 * sum(ts) / len(ts)
+    val = 1e3 / ms_per_step
     line = {
         "impl": "reference", "metric": "solves/s", "value": val, "unit": "solves/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": est * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic (seeded microbubble window)",
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (seeded microbubble window, host memory)",
         "config": {"workload": WORKLOAD_DESC, "tol": 1e-7},
         "cpu_baseline": {"value": val, "unit": "solves/s", "cores": cores(), "kind": "oracle",
-                         "sample": f"first {strip} pixels (32 image rows) x 20 frames per step, "
-                                   f"time x{scale:.0f}; oracle iterations {its[0]}"},
+                         "sample": f"one whole {w.m}x{w.T} window per step (FP64, LAPACK SVD), "
+                                   f"oracle iterations {its[0]}; timed wall {wall:.1f} s"},
         "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -304,6 +305,15 @@ def _roofline(alg_bytes, seconds, kernel, timing, traffic=None):
             "peak_kind": peak_kind + " (hbm_gbs, burst copy)"}
 
 
+def _eig_desc() -> str:
+    """Arithmetic of the narrow eigen-step the library runs (its default, or the
+    FP32 opt-in selected by RPCA_EIG_FP32=1)."""
+    if os.environ.get("RPCA_EIG_FP32", "0") not in ("", "0"):
+        return "T x T Jacobi with FP32 rotations and basis (opt-in); FP64 Gram sums, sigma decision, mu, test"
+    return ("T x T cyclic Jacobi in FP64 (rotations, Gram sums, basis, Newton-Schulz, Wbar; "
+            "sigma decision, mu and convergence test FP64)")
+
+
 def _plan_pass_name(T, m, args):
     """The fused pass kernel a plan runs (the rule of the plan's kernel choice)."""
     if args.complex or T > 32:
@@ -316,11 +326,11 @@ def _plan_pass_name(T, m, args):
     return f"pass_kernel<{tb},FUSED>"
 
 
-def _solve_bytes(m, T, iters):
-    """Algorithmic HBM bytes of one solve: init pass reads X; each iteration
-    reads X, S, Y and writes S, Y; the final step reads X, S, Y_k, Y_k-1 and
-    writes L (plus the m-byte mask)."""
-    return 4 * m * T * (1 + 5 * iters + 5) + m
+def _solve_bytes(m, T, iters, b=4):
+    """Algorithmic HBM bytes of one solve (the method's own traffic, not the
+    kernels'): X read once at the start, X, S, Y read and S, Y written per
+    iteration (5 m T b), L written once at the end; b bytes per element."""
+    return b * m * T * (1 + 5 * iters + 1)
 
 
 def _plain_reference_rate(rpca, Xs, m, T, flush):
@@ -368,53 +378,32 @@ def run_batch(args):
     value = world * NB * args.steps / (total_ms * 1e-3)
     iters = [r["iters"] for r in res]
 
-    # end to end through the public API: every step uploads its windows from
-    # pinned host memory and downloads L, S and the masks; two device buffer
-    # sets and two copy streams let step k+1's upload and step k's download run
-    # beside the solves (a streaming pipeline; each step's copies stay inside
-    # the timed region, which ends when the last download has landed)
+    # end to end through the C ABI's host-buffer call (rpca_batch_solve_host):
+    # every step hands the library pinned host windows; the library uploads
+    # them, solves them in one persistent launch and downloads L, S and the
+    # masks into pinned host buffers.  Consecutive calls overlap one step's
+    # uploads and the previous step's downloads with the solves (the library's
+    # two staging sets and copy streams); every step's copies are inside the
+    # timed region, which ends when the last step's downloads have landed.
     Xh = [torch.from_numpy(w.frames).pin_memory() for w in ws]
     Lh = [torch.empty((T, m), dtype=torch.float32).pin_memory() for _ in ws]
     Sh = [torch.empty((T, m), dtype=torch.float32).pin_memory() for _ in ws]
     Mh = [torch.empty(m, dtype=torch.uint8).pin_memory() for _ in ws]
-    sets = [(Xs, Ls, Ss, masks),
-            ([torch.empty_like(x) for x in Xs], [torch.empty_like(x) for x in Xs],
-             [torch.empty_like(x) for x in Xs], [torch.empty_like(mk) for mk in masks])]
-    s_up, s_dn, s_cmp = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.current_stream()
 
     def e2e_run(nsteps):
-        done = []
         for k in range(nsteps):
-            Xb, Lb, Sb, Mb = sets[k % 2]
-            with torch.cuda.stream(s_up):
-                if k >= 2:
-                    s_up.wait_event(done[k - 2])          # this buffer set's last download has landed
-                for i in range(NB):
-                    Xb[i].copy_(Xh[i], non_blocking=True)
-                up = torch.cuda.Event()
-                up.record(s_up)
-            s_cmp.wait_event(up)
-            batch.solve(Xb, Lb, Sb, masks=Mb, thetas=thetas, wait=False)
-            solved = torch.cuda.Event()
-            solved.record(s_cmp)
-            with torch.cuda.stream(s_dn):
-                s_dn.wait_event(solved)
-                for i in range(NB):
-                    Lh[i].copy_(Lb[i], non_blocking=True)
-                    Sh[i].copy_(Sb[i], non_blocking=True)
-                    Mh[i].copy_(Mb[i], non_blocking=True)
-                dn = torch.cuda.Event()
-                dn.record(s_dn)
-                done.append(dn)
-        torch.cuda.synchronize()
+            r = batch.solve_host(Xh, Lh, Sh, masks=Mh, thetas=thetas, wait=(k == nsteps - 1))
+        return r
 
     e2e_run(2)
     e2e_steps = max(3, args.steps // 2)
     _barrier(world)
     t0 = time.perf_counter()
-    e2e_run(e2e_steps)
+    e2e_res = e2e_run(e2e_steps)
     e2e_s = _max_over_ranks(time.perf_counter() - t0, world)
     e2e_val = world * NB * e2e_steps / e2e_s
+    e2e_ok = all(r["status"] == rpca.OK for r in e2e_res) and \
+        bool(torch.equal(Lh[0], Ls[0].cpu())) and bool(torch.equal(Sh[0], Ss[0].cpu()))
 
     plain = _plain_reference_rate(rpca, Xs, m, T, flush)
     alg = sum(_solve_bytes(m, T, it) for it in iters)
@@ -425,7 +414,7 @@ def run_batch(args):
         "dtype": "f32", "data": "synthetic (seeded microbubble windows, in HBM)",
         "config": {"workload": WORKLOAD_DESC,
                    "form": f"batched persistent launch, {NB} windows per step (different seeds)",
-                   "precision": "fp32", "tol": 1e-7,
+                   "precision": "fp32", "tol": 1e-7, "eigensolve": _eig_desc(),
                    "l2": "flushed before every step (256 MB write, outside step events); "
                          "the step's windows (8 x 3 x 21 MB) exceed L2",
                    "schedule": info, "tuned_ms": tuned_ms,
@@ -444,8 +433,10 @@ def run_batch(args):
                               traffic=ncu_batch_traffic(kernel_source_hash(), iters)),
         "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": NB * m * T * 4,
                 "d2h_bytes_per_step": NB * (2 * m * T * 4 + m), "steps": e2e_steps,
-                "copies": "pinned host <-> device every step, on two copy streams beside the solves "
-                          "(two device buffer sets)"},
+                "api": "rpca_batch_solve_host (C ABI, pinned host buffers in and out)",
+                "copies": "inside the library: uploads and downloads on two copy streams beside the "
+                          "solves (two device staging sets)",
+                "outputs_equal_device_form": e2e_ok},
         "vs_plain_fp32": {"plain_solves_per_s": plain, "ratio": value / plain},
         "clocks": clocks,
         "kernel_source_sha256": kernel_source_hash(),
@@ -474,7 +465,7 @@ def run_serve(args):
     masks = [torch.zeros(m, dtype=torch.uint8, device="cuda") for _ in ws]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     prec = {"fp32": rpca.PREC_FP32, "tf32x3": rpca.PREC_TF32X3, "bf16x3": rpca.PREC_BF16X3,
-            "tf32": rpca.PREC_TF32}[args.precision]
+            }[args.precision]
     sv = rpca.Server(hbm_budget_bytes=120 * 10**9, max_slots=args.slots, warm=False)
     lat = []
 
@@ -505,7 +496,7 @@ def run_serve(args):
         "dtype": "f32", "data": "synthetic (seeded microbubble windows, in HBM)",
         "config": {"workload": WORKLOAD_DESC,
                    "form": f"served: {NB} probes submit one window each per step, {args.slots} slots, cold starts",
-                   "precision": args.precision, "tol": 1e-7,
+                   "precision": args.precision, "tol": 1e-7, "eigensolve": _eig_desc(),
                    "l2": "flushed before every step (256 MB write, outside step events)"},
         "ms_per_solve": ms_per_step / NB,
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
@@ -740,7 +731,7 @@ def run_uneven(args):
         "config": {"workload": f"{len(ws)} uneven windows: grids from 64x64, 128x256, 256x256, 512x512, "
                                "frames U{10..200}",
                    "form": "batched persistent launch (tiled bodies: the batch holds windows of > 32 frames)",
-                   "schedule": info, "tuned_ms": tuned_ms, "precision": "fp32", "tol": 1e-7,
+                   "schedule": info, "tuned_ms": tuned_ms, "precision": "fp32", "tol": 1e-7, "eigensolve": _eig_desc(),
                    "l2": "flushed before every step (256 MB write, outside step events)",
                    "frames": [w.T for w in ws], "pixels": [w.m for w in ws]},
         "iters": iters,
@@ -783,7 +774,7 @@ def run_stream(args):
                               n_free=max(8, int(800 * f)), speed=(0.5, 5.0))
         probes.append(dict(key=i, fps=fps, m=w.m, frames=torch.from_numpy(w.frames).cuda(), host=w))
     prec = {"fp32": rpca.PREC_FP32, "tf32x3": rpca.PREC_TF32X3, "bf16x3": rpca.PREC_BF16X3,
-            "tf32": rpca.PREC_TF32}[args.precision]
+            }[args.precision]
     # arrivals: per probe a Poisson process, merged
     events = []
     for pr in probes:
@@ -866,7 +857,7 @@ def run_stream(args):
         "config": {"workload": "8 probes, images 128x128 .. 768x512, 100-500 fps Poisson, 20-frame sliding windows",
                    "form": f"served: {args.slots} slots, warm start {not args.cold} (mu scale 0.1, "
                            f"cold every {args.cold_every}), budget 120 GB",
-                   "precision": args.precision, "duration_s": args.duration,
+                   "precision": args.precision, "eigensolve": _eig_desc(), "duration_s": args.duration,
                    "fps": [round(p["fps"], 1) for p in probes]},
         "offered_per_s": len(events) / args.duration,
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
@@ -892,7 +883,7 @@ def run_ours(args):
     T, m = w.frames.shape
     X = torch.from_numpy(w.frames).cuda()
     prec = {"fp32": rpca.PREC_FP32, "tf32x3": rpca.PREC_TF32X3, "bf16x3": rpca.PREC_BF16X3,
-            "tf32": rpca.PREC_TF32}[args.precision]
+            }[args.precision]
     drive = {"graph": rpca.DRIVE_GRAPH, "stream": rpca.DRIVE_STREAM, "host": rpca.DRIVE_HOST}[args.drive]
     plan = rpca.Plan(m, T, precision=prec, drive=drive, dtype=rpca.C64 if args.complex else rpca.R32)
     L = torch.empty_like(X)
@@ -938,7 +929,8 @@ def run_ours(args):
         "dtype": "c64" if args.complex else "f32", "data": "synthetic (seeded microbubble window, in HBM)",
         "config": {"workload": f"{wl} (Casorati {m}x{T}, {'complex64 IQ' if args.complex else 'fp32'})",
                    "form": "plan: one solve per step",
-                   "precision": args.precision,
+                   "precision": args.precision, "eigensolve": _eig_desc() if T <= 32 and not args.complex else
+                   "tiled path: T x T Jacobi with FP32 rotations; FP64 Gram sums and decisions",
                    "drive": {"graph": "cuda-graph device loop", "stream": "kernels launched one by one",
                              "host": "plain form: host loop, unfused passes"}[args.drive],
                    "tol": 1e-7, "l2": "flushed before every step (256 MB write, outside step events)",
@@ -975,7 +967,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp32", "tf32x3", "bf16x3", "tf32"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "tf32x3", "bf16x3"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--form", choices=["batch", "plan", "serve"], default="batch")
     ap.add_argument("--windows", type=int, default=8, help="windows per step (batch, serve)")

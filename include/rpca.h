@@ -60,7 +60,10 @@ typedef enum {
   RPCA_PREC_FP32 = 0,       /* FP32 CUDA-core FMA */
   RPCA_PREC_TF32X3 = 1,     /* tensor cores, TF32 hi/lo split, 3 products, FP32 accumulate */
   RPCA_PREC_BF16X3 = 2,     /* tensor cores, BF16 hi/lo split, 3 products, FP32 accumulate */
-  RPCA_PREC_TF32 = 3        /* tensor cores, plain TF32 */
+  RPCA_PREC_TF32 = 3        /* reserved: one plain TF32 product per contraction leaves L and S
+                               about 7e-4 from the FP64 solution (262144 x 20 window), outside
+                               the 1e-4 bound of the reduced precisions; plans reject it with
+                               RPCA_ERR_UNSUPPORTED */
 } rpca_precision;
 
 /* Penalty schedule.  IALM: mu_1 = mu0_scale/||X||_2, mu_{k+1} = min(rho mu_k,
@@ -210,7 +213,7 @@ typedef struct {
  * launch descriptor.  precision must be RPCA_PREC_FP32 (else
  * RPCA_ERR_UNSUPPORTED); drive is ignored.  The CTA schedule is the one tuned
  * before for the same window shapes in this process (rpca_batch_tune), else a
- * default (one lane per window, CTAs proportional to m*T). */
+ * default (paired lanes of two windows each, CTAs proportional to m*T). */
 rpca_status rpca_batch_create(const rpca_params* params, int32_t n, rpca_batch_t* out);
 
 /* Solves windows win[0..n) in one launch on `stream`.  With out != NULL
@@ -220,14 +223,25 @@ rpca_status rpca_batch_create(const rpca_params* params, int32_t n, rpca_batch_t
 rpca_status rpca_batch_solve(rpca_batch_t batch, const rpca_window* win, void* stream, rpca_result* out);
 
 /* Autotuner: times every candidate schedule (lanes, CTA share exponent, CTAs
- * per SM) on these windows, `reps` timed solves each (median), keeps the
+ * per SM, paired or not) on these windows, `reps` timed solves each (median), keeps the
  * fastest for this batch and for later batches of the same shapes in this
  * process.  *best_ms (nullable) gets its median time per solve.  Synchronous. */
 rpca_status rpca_batch_tune(rpca_batch_t batch, const rpca_window* win, void* stream, int32_t reps,
                             double* best_ms);
 
+/* Sets the schedule by hand (as rpca_batch_tune would pick one): `lanes`
+ * lanes (capped at the resident CTAs), lane CTAs ~ load^alpha, ctas_per_sm
+ * resident CTAs per SM (1 .. the kernel's maximum, info[4]), paired 0/1.
+ * Waits for the batch's launch in flight.  Errors: RPCA_ERR_ARG. */
+rpca_status rpca_batch_set_schedule(rpca_batch_t batch, int32_t lanes, double alpha, int32_t ctas_per_sm,
+                                    int32_t paired);
+
 /* Schedule in use: info[0..n) = {grid CTAs, lanes, CTAs per SM,
- * 1000 * share exponent, max resident CTAs per SM, graph captured (0/1)}. */
+ * 1000 * share exponent, max resident CTAs per SM, graph captured (0/1),
+ * paired lanes (0/1)}.  Paired lanes (the default for two or more windows):
+ * a lane of two or more windows runs them two at a time, its last CTA running
+ * every eigen-step (one window's) while its other CTAs run the other window's
+ * pass, so the one-CTA eigen-steps overlap the passes. */
 rpca_status rpca_batch_info(rpca_batch_t batch, int32_t* info, int32_t n);
 
 /* CTAs each window uses (n >= number of windows). */
@@ -251,6 +265,23 @@ rpca_status rpca_batch_window_ctas(rpca_batch_t batch, int32_t* ctas, int32_t n)
 rpca_status rpca_batch_schedule(int32_t n, const int64_t* m, const int32_t* T, const int32_t* max_ctas,
                                 int32_t ctas, int32_t lanes, double alpha, int32_t* n_lanes, int32_t* lane_ctas,
                                 int32_t* order, int32_t* lane_end);
+
+/* rpca_batch_solve with HOST buffers: win[i].X, L, S and mask are host
+ * pointers (pinned host memory, cudaHostAlloc, for full copy speed; mask may
+ * be NULL), laid out as the device buffers of rpca_solve.  The batch owns two
+ * device staging sets (one per call parity, allocated on the first call) and
+ * two copy streams: a call uploads every X into its set (after the downloads
+ * of the call two before it have landed), solves the set on `stream` in one
+ * persistent launch, and downloads L, S and the masks.  Consecutive calls
+ * therefore overlap one call's uploads and the previous call's downloads with
+ * the solves.  With out != NULL the call waits until its own downloads (and
+ * those of every earlier call) have landed and fills out[0..n) as
+ * rpca_batch_solve does, returning the worst status; with out == NULL it
+ * returns once enqueued, and the host buffers of every call made so far must
+ * stay untouched until a later call with out != NULL returns.  Errors:
+ * RPCA_ERR_ARG (null pointers), RPCA_ERR_NOMEM (staging allocation),
+ * RPCA_ERR_CUDA. */
+rpca_status rpca_batch_solve_host(rpca_batch_t batch, const rpca_window* win, void* stream, rpca_result* out);
 
 void rpca_batch_destroy(rpca_batch_t batch);
 
@@ -341,7 +372,7 @@ rpca_status rpca_eig(const double* G, int32_t T, double* evals, double* evecs, v
  * real float32 on the device; V row-major T x T float32 on the device or NULL
  * for the identity; G row-major T x T float64 on the device, written by the
  * call), but asynchronously on `stream` and with no cudaMalloc, cudaFree or
- * other allocating call: its scratch (about 2.2 MB: partial Grams of at most
+ * other allocating call: its scratch (about 2.4 MB: partial Grams of at most
  * 512 CTAs, reduction counters, control block) is a fixed array compiled into
  * the library, one copy on every GPU that loads it, held until the process
  * exits.  The caller still provides X, V and G.
@@ -349,7 +380,10 @@ rpca_status rpca_eig(const double* G, int32_t T, double* evals, double* evecs, v
  *     (the CTAs stride over the pixels).
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     before any stream capture.  The address is looked up again when the
+ *     device's current context has changed since (for instance after
+ *     cudaDeviceReset), so make the first call after such a change outside
+ *     stream capture too.
  *   - Every call shares the one array and clears its counters first; calls
  *     whose work overlaps on the GPU (other streams, other host threads) race
  *     on it and must be serialised by the caller.
@@ -362,7 +396,7 @@ rpca_status rpca_gram_noalloc(const float* X, int64_t m, int32_t T, const float*
  * eigen-decomposition of Z^T Z): with the pixel rows of one window spread over
  * several processes (one GPU each), every process runs the pass over its own
  * rows, the processes sum the Gram and the residual sums (an all-reduce of
- * T*32 floats and 2 doubles per iteration), and every process then runs the
+ * T*32 + 2 doubles per iteration), and every process then runs the
  * same eigen-step on the same sums, so the iteration is the one of the whole
  * window.  A plan created with params.sharded = 1 (real FP32, T <=
  * RPCA_MAX_T_NARROW, IALM schedule, no warm start; params.lambda set from the
@@ -376,8 +410,9 @@ rpca_status rpca_gram_noalloc(const float* X, int64_t m, int32_t T, const float*
  *                    RPCA_STEP_EIG (residual test, mu update, eigen-step),
  *                    RPCA_STEP_FINAL (L and the mask);
  *   rpca_step_sums   device pointers of the sums to reduce after RPCA_STEP_INIT and
- *                    RPCA_STEP_PASS: the Gram (T rows of 32 floats, row stride 32,
- *                    columns >= T zero) and {e2, l1} (2 doubles);
+ *                    RPCA_STEP_PASS: the Gram (T rows of 32 doubles, row stride 32,
+ *                    columns >= T zero; FP64 sums of the CTAs' FP32 partials) and
+ *                    {e2, l1} (2 doubles);
  *   rpca_step_done   synchronises `stream` and reports whether the solve has
  *                    ended (and its result, when `out` is not NULL).
  * Order: begin, INIT, reduce, EIG_INIT, then while not done: PASS, reduce, EIG;
@@ -394,7 +429,7 @@ typedef enum {
 rpca_status rpca_step_begin(rpca_plan_t plan, const float* X, float* L, float* S, uint8_t* mask, float theta,
                             void* stream);
 rpca_status rpca_step_run(rpca_plan_t plan, int32_t step, void* stream);
-rpca_status rpca_step_sums(rpca_plan_t plan, float** gram, double** sums);
+rpca_status rpca_step_sums(rpca_plan_t plan, double** gram, double** sums);
 rpca_status rpca_step_done(rpca_plan_t plan, int32_t* done, rpca_result* out, void* stream);
 
 /* ---- frame pre-filter of the in vivo reference ---------------------------- */

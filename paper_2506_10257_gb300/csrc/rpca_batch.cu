@@ -42,10 +42,11 @@ struct BatchConfig {
   int lanes;        // CTA ranges (<= windows)
   double alpha;     // lane CTAs ~ load^alpha
   int ctas_per_sm;  // resident CTAs per SM used by the grid
+  int paired;       // lanes of >= 2 windows run them two at a time beside an eigen-step CTA
 };
 
 bool operator==(const BatchConfig& a, const BatchConfig& b) {
-  return a.lanes == b.lanes && a.alpha == b.alpha && a.ctas_per_sm == b.ctas_per_sm;
+  return a.lanes == b.lanes && a.alpha == b.alpha && a.ctas_per_sm == b.ctas_per_sm && a.paired == b.paired;
 }
 
 std::mutex g_tune_mu;
@@ -111,6 +112,17 @@ struct rpca_batch_s {
   bool use_graph = true;
   cudaEvent_t last = nullptr;   // end of the last launch (guards h_desc reuse)
   bool pending = false;
+  // host-buffer form: two device staging sets (call parity), copy streams
+  struct Stage {
+    std::vector<void*> X, L, S;
+    std::vector<uint8_t*> M;
+    cudaEvent_t solved = nullptr, down = nullptr;
+    bool used = false;
+  };
+  Stage stage[2];
+  cudaStream_t s_up = nullptr, s_dn = nullptr;
+  cudaEvent_t up_done = nullptr;
+  long long host_calls = 0;
 };
 
 namespace {
@@ -192,7 +204,8 @@ void make_schedule(rpca_batch_s* b, const BatchConfig& cfg) {
   std::vector<int> wcap(n);
   for (int w = 0; w < n; ++w) {
     wload[w] = window_load(b->p[w]);
-    wcap[w] = b->views[w].max_grid;
+    // a paired lane's last CTA runs the eigen-steps beside the pass CTAs
+    wcap[w] = b->views[w].max_grid + (cfg.paired ? 1 : 0);
   }
   const LanePlan lp = plan_lanes(wload, wcap, C, cfg.lanes, cfg.alpha);
   const int L = (int)lp.nc.size();
@@ -208,13 +221,15 @@ void make_schedule(rpca_batch_s* b, const BatchConfig& cfg) {
     d.cta0 = cta;
     d.ncta = nc[l];
     d.w0 = (int)b->slot_win.size();
+    d.w1 = d.w0 + (int)lw[l].size();
+    const int pass_ctas = lane_is_paired(cfg.paired, d) ? nc[l] - 1 : nc[l];
     for (int w : lw[l]) {
       b->win_slot[w] = (int)b->slot_win.size();
       b->slot_win.push_back(w);
       const int64_t tiles = (b->p[w].m + b->views[w].tile - 1) / b->views[w].tile;
-      b->win_ncta[w] = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)nc[l], tiles, b->views[w].max_grid}));
+      b->win_ncta[w] =
+          (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)pass_ctas, tiles, b->views[w].max_grid}));
     }
-    d.w1 = (int)b->slot_win.size();
     cta += nc[l];
   }
   b->grid = cta;
@@ -290,6 +305,7 @@ void write_static_desc(rpca_batch_s* b) {
   BatchDesc* d = b->h_desc;
   d->nwin = b->n;
   d->nlanes = b->nlanes;
+  d->paired = b->cfg.paired;
   d->spin_limit = b->spin_limit;
   d->vrows = b->vrows;
   for (int l = 0; l < b->nlanes; ++l) d->lane[l] = b->lanes[l];
@@ -331,10 +347,13 @@ std::string make_signature(const rpca_batch_s* b) {
   return s;
 }
 
+// Default: lanes of two windows each, run paired beside an eigen-step CTA
+// (one window alone when the batch has one).
 BatchConfig default_config(const rpca_batch_s* b) {
   BatchConfig c;
   c.ctas_per_sm = b->occ_max;
-  c.lanes = std::min(b->n, b->sms * c.ctas_per_sm);
+  c.paired = b->n >= 2 ? 1 : 0;
+  c.lanes = std::min(c.paired ? (b->n + 1) / 2 : b->n, b->sms * c.ctas_per_sm);
   c.alpha = 1.0;
   return c;
 }
@@ -465,6 +484,7 @@ rpca_status rpca_batch_solve(rpca_batch_t b, const rpca_window* win, void* strea
     wd.mask = win[i].mask;
     wd.theta = win[i].theta;
     wd.gen = 0u;
+    wd.pdone = 0u;
   }
   cudaStream_t s = (cudaStream_t)stream;
   ensure_graph(b, s);
@@ -486,20 +506,125 @@ rpca_status rpca_batch_solve(rpca_batch_t b, const rpca_window* win, void* strea
   return (rpca_status)worst;
 }
 
+// Bytes of one window's X (and of L, S) in the batch.
+static size_t window_bytes(const rpca_params& p) {
+  return sizeof(float) * (size_t)p.m * (size_t)(p.dtype == RPCA_C64 ? 2 * p.T : p.T);
+}
+
+// Staging sets, copy streams and events of the host-buffer form (first call).
+static rpca_status host_stage_init(rpca_batch_t b) {
+  if (b->s_up) return RPCA_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&b->s_up, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->s_dn, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->up_done, cudaEventDisableTiming);
+  for (int j = 0; j < 2 && e == cudaSuccess; ++j) {
+    rpca_batch_s::Stage& st = b->stage[j];
+    e = cudaEventCreateWithFlags(&st.solved, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&st.down, cudaEventDisableTiming);
+    st.X.assign(b->n, nullptr);
+    st.L.assign(b->n, nullptr);
+    st.S.assign(b->n, nullptr);
+    st.M.assign(b->n, nullptr);
+    for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
+      const size_t nb = window_bytes(b->p[i]);
+      e = cudaMalloc(&st.X[i], nb);
+      if (e == cudaSuccess) e = cudaMalloc(&st.L[i], nb);
+      if (e == cudaSuccess) e = cudaMalloc(&st.S[i], nb);
+      if (e == cudaSuccess) e = cudaMalloc((void**)&st.M[i], (size_t)b->p[i].m);
+    }
+  }
+  return cuda_st(e);
+}
+
+static void host_stage_free(rpca_batch_t b) {
+  if (b->s_up) cudaStreamSynchronize(b->s_up);
+  if (b->s_dn) cudaStreamSynchronize(b->s_dn);
+  for (int j = 0; j < 2; ++j) {
+    rpca_batch_s::Stage& st = b->stage[j];
+    for (void* p : st.X) if (p) cudaFree(p);
+    for (void* p : st.L) if (p) cudaFree(p);
+    for (void* p : st.S) if (p) cudaFree(p);
+    for (uint8_t* p : st.M) if (p) cudaFree(p);
+    if (st.solved) cudaEventDestroy(st.solved);
+    if (st.down) cudaEventDestroy(st.down);
+  }
+  if (b->up_done) cudaEventDestroy(b->up_done);
+  if (b->s_up) cudaStreamDestroy(b->s_up);
+  if (b->s_dn) cudaStreamDestroy(b->s_dn);
+}
+
+rpca_status rpca_batch_solve_host(rpca_batch_t b, const rpca_window* win, void* stream, rpca_result* out) {
+  if (!b || !win) return RPCA_ERR_ARG;
+  for (int i = 0; i < b->n; ++i)
+    if (!win[i].X || !win[i].L || !win[i].S) return RPCA_ERR_ARG;
+  rpca_status st = host_stage_init(b);
+  if (st != RPCA_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int j = (int)(b->host_calls & 1);
+  rpca_batch_s::Stage& sg = b->stage[j];
+  // uploads into this set once the downloads of the call two before have landed
+  cudaError_t e = sg.used ? cudaStreamWaitEvent(b->s_up, sg.down, 0) : cudaSuccess;
+  for (int i = 0; i < b->n && e == cudaSuccess; ++i)
+    e = cudaMemcpyAsync(sg.X[i], win[i].X, window_bytes(b->p[i]), cudaMemcpyHostToDevice, b->s_up);
+  if (e == cudaSuccess) e = cudaEventRecord(b->up_done, b->s_up);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->up_done, 0);
+  if (e != cudaSuccess) return cuda_st(e);
+  std::vector<rpca_window> dw(b->n);
+  for (int i = 0; i < b->n; ++i) {
+    dw[i] = win[i];
+    dw[i].X = sg.X[i];
+    dw[i].L = sg.L[i];
+    dw[i].S = sg.S[i];
+    dw[i].mask = win[i].mask ? sg.M[i] : nullptr;
+  }
+  st = rpca_batch_solve(b, dw.data(), stream, nullptr);
+  if (st != RPCA_OK) return st;
+  e = cudaEventRecord(sg.solved, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(b->s_dn, sg.solved, 0);
+  for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
+    const size_t nb = window_bytes(b->p[i]);
+    e = cudaMemcpyAsync(win[i].L, sg.L[i], nb, cudaMemcpyDeviceToHost, b->s_dn);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(win[i].S, sg.S[i], nb, cudaMemcpyDeviceToHost, b->s_dn);
+    if (e == cudaSuccess && win[i].mask)
+      e = cudaMemcpyAsync(win[i].mask, sg.M[i], (size_t)b->p[i].m, cudaMemcpyDeviceToHost, b->s_dn);
+  }
+  if (e == cudaSuccess && out)
+    e = cudaMemcpyAsync(b->h_ctrl, b->d_ctrl, sizeof(Ctrl) * b->n, cudaMemcpyDeviceToHost, b->s_dn);
+  if (e == cudaSuccess) e = cudaEventRecord(sg.down, b->s_dn);
+  if (e != cudaSuccess) return cuda_st(e);
+  sg.used = true;
+  ++b->host_calls;
+  if (!out) return RPCA_OK;
+  e = cudaEventSynchronize(sg.down);
+  if (e != cudaSuccess) return cuda_st(e);
+  b->pending = false;
+  int worst = RPCA_OK;
+  for (int i = 0; i < b->n; ++i) {
+    result_from_ctrl(b->views[i].lambda, b->h_ctrl[b->win_slot[i]], &out[i], b->views[i].cplx);
+    if (out[i].status < 0) worst = out[i].status;
+    else if (worst == RPCA_OK && out[i].status != RPCA_OK) worst = out[i].status;
+  }
+  return (rpca_status)worst;
+}
+
 rpca_status rpca_batch_tune(rpca_batch_t b, const rpca_window* win, void* stream, int32_t reps, double* best_ms) {
   if (!b || !win || reps < 1) return RPCA_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   std::vector<BatchConfig> cands;
   std::vector<int> lane_opts;
-  for (int div : {1, 2, 4, 8}) lane_opts.push_back(std::max(1, (b->n + div - 1) / div));
+  for (int div : {1, 2, 4, 8})
+    if (std::find(lane_opts.begin(), lane_opts.end(), std::max(1, (b->n + div - 1) / div)) == lane_opts.end())
+      lane_opts.push_back(std::max(1, (b->n + div - 1) / div));
   std::vector<int> occ_opts = {1};
   if (b->occ_max > 1) occ_opts.push_back(b->occ_max);
   for (int occ : occ_opts)
     for (int L : lane_opts)
-      for (double a : {1.0, 0.5}) {
-        BatchConfig c{std::min(L, b->sms * occ), a, occ};
-        if (std::find(cands.begin(), cands.end(), c) == cands.end()) cands.push_back(c);
-      }
+      for (double a : {1.0, 0.5})
+        for (int pr : {0, 1}) {
+          if (pr && b->n < 2 * L) continue;  // a paired lane needs two windows
+          BatchConfig c{std::min(L, b->sms * occ), a, occ, pr};
+          if (std::find(cands.begin(), cands.end(), c) == cands.end()) cands.push_back(c);
+        }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -572,11 +697,20 @@ rpca_status rpca_batch_schedule(int32_t n, const int64_t* m, const int32_t* T, c
   return RPCA_OK;
 }
 
+rpca_status rpca_batch_set_schedule(rpca_batch_t b, int32_t lanes, double alpha, int32_t ctas_per_sm,
+                                    int32_t paired) {
+  if (!b || lanes < 1 || !(alpha >= 0.0) || !isfinite(alpha) || ctas_per_sm < 1 || ctas_per_sm > b->occ_max ||
+      (paired != 0 && paired != 1))
+    return RPCA_ERR_ARG;
+  BatchConfig c{std::min(lanes, b->sms * ctas_per_sm), alpha, ctas_per_sm, paired};
+  return apply_config(b, c);
+}
+
 rpca_status rpca_batch_info(rpca_batch_t b, int32_t* info, int32_t n) {
   if (!b || !info || n < 0) return RPCA_ERR_ARG;
-  const int32_t v[6] = {b->grid, b->nlanes, b->cfg.ctas_per_sm, (int32_t)lround(b->cfg.alpha * 1000.0),
-                        b->occ_max, b->exec ? 1 : 0};
-  for (int i = 0; i < n && i < 6; ++i) info[i] = v[i];
+  const int32_t v[7] = {b->grid, b->nlanes, b->cfg.ctas_per_sm, (int32_t)lround(b->cfg.alpha * 1000.0),
+                        b->occ_max, b->exec ? 1 : 0, b->cfg.paired};
+  for (int i = 0; i < n && i < 7; ++i) info[i] = v[i];
   return RPCA_OK;
 }
 
@@ -589,6 +723,7 @@ rpca_status rpca_batch_window_ctas(rpca_batch_t b, int32_t* ctas, int32_t n) {
 void rpca_batch_destroy(rpca_batch_t b) {
   if (!b) return;
   if (b->pending && b->last) cudaEventSynchronize(b->last);
+  host_stage_free(b);
   drop_graph(b);
   for (rpca_plan_t pl : b->plans) rpca_plan_destroy(pl);
   if (b->h_desc) cudaFreeHost(b->h_desc);

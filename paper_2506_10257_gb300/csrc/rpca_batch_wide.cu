@@ -34,6 +34,26 @@ struct WideBody {
   }
 };
 
+// The tiled steps of a window by its columns per warp (TB of the descriptor).
+template <bool CPLX>
+struct WideDisp {
+  static __device__ bool pass(WinDesc& wd, bool init, int lc, int nc, unsigned char* dsm) {
+    switch (wd.TB) {
+      case 4: return WideBody<4, CPLX>::pass(wd.b, init, lc, nc, dsm);
+      case 8: return WideBody<8, CPLX>::pass(wd.b, init, lc, nc, dsm);
+      case 12: return WideBody<12, CPLX>::pass(wd.b, init, lc, nc, dsm);
+      case 16: return WideBody<16, CPLX>::pass(wd.b, init, lc, nc, dsm);
+      case 20: return WideBody<20, CPLX>::pass(wd.b, init, lc, nc, dsm);
+      case 24: return WideBody<24, CPLX>::pass(wd.b, init, lc, nc, dsm);
+      case 28: return WideBody<28, CPLX>::pass(wd.b, init, lc, nc, dsm);
+      default: return false;
+    }
+  }
+  static __device__ void eig(WinDesc& wd, int flags, unsigned char* dsm, int vrows) {
+    wide_eig_call(wd.b, flags, reinterpret_cast<float*>(dsm), vrows);
+  }
+};
+
 // Batches holding a wide or complex window: every window runs the tiled
 // bodies (TB of a window = its columns per warp, CW).
 template <bool CPLX>
@@ -47,6 +67,10 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel_wide(BatchDesc*
   if (lc < 0 || lc >= ld.ncta) return;
   const unsigned long long limit = bd->spin_limit;
   const int vrows = bd->vrows;
+  if (lane_is_paired(bd->paired, ld)) {
+    run_lane_paired<WideDisp<CPLX>>(bd, ld, lc, batch_dsm, limit, &bd->stop, vrows);
+    return;
+  }
   for (int w = ld.w0; w < ld.w1; ++w) {
     WinDesc& wd = bd->w[w];
     switch (wd.TB) {

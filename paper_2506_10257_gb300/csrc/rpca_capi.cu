@@ -27,10 +27,11 @@ struct KernelSet {
   size_t pass_ws_smem[4];
   void* pass_fs[4];        // CUDA-core FP32 passes fed by TMA, by mode (needs m % 4 == 0)
   size_t pass_fs_smem;
-  void* eig32;       // smem Jacobi, FP32 rotations (reference form)
-  void* eig64;       // smem Jacobi, FP64 rotations
-  void* eig_fast;    // FP32 rotations, logged and accumulated once
+  void* eig64;       // plain smem Jacobi, FP64 rotations (rpca_eig on an external matrix)
+  void* eig_fast;    // the plans' eigen-step: FP64 rotations, logged and accumulated once
   size_t eig_fast_smem;
+  void* eig_fast32;  // the same with FP32 rotations and basis arithmetic (RPCA_EIG_FP32=1)
+  size_t eig_fast32_smem;
   int TB;
   int eig_threads;
 };
@@ -48,10 +49,11 @@ KernelSet make_set() {
   k.pass_fs[PM_UPDATE] = (void*)pass_fs_kernel<TB, PM_UPDATE>;
   k.pass_fs[PM_GRAM] = (void*)pass_fs_kernel<TB, PM_GRAM>;
   k.pass_fs_smem = FsShape<TB>::SMEM;
-  k.eig32 = (void*)eig_kernel<TB, float>;
   k.eig64 = (void*)eig_kernel<TB, double>;
-  k.eig_fast = (void*)eig_fast_kernel<TB>;
-  k.eig_fast_smem = sizeof(EigFastSmem<TB>);
+  k.eig_fast = (void*)eig64_kernel<TB>;
+  k.eig_fast_smem = sizeof(Eig64Smem<TB>);
+  k.eig_fast32 = (void*)eig_fast_kernel<TB, float>;
+  k.eig_fast32_smem = sizeof(EigFastSmem<TB, float>);
   k.TB = TB;
   k.eig_threads = TB > 20 ? 512 : 256;
   return k;
@@ -76,16 +78,16 @@ void add_tc(KernelSet& k) {
   k.pass_tc_smem[RPCA_PREC_TF32X3] = pass_tc_smem<TB, KP, false>();
   k.pass_tc[RPCA_PREC_BF16X3] = (void*)pass_tc_kernel<TB, KP, true, true>;
   k.pass_tc_smem[RPCA_PREC_BF16X3] = pass_tc_smem<TB, KP, true>();
-  k.pass_tc[RPCA_PREC_TF32] = (void*)pass_tc_kernel<TB, KP, false, false>;
-  k.pass_tc_smem[RPCA_PREC_TF32] = pass_tc_smem<TB, KP, false>();
+  k.pass_tc[RPCA_PREC_TF32] = nullptr;  // plain TF32 is not offered (validate)
+  k.pass_tc_smem[RPCA_PREC_TF32] = 0;
   k.pass_ws[RPCA_PREC_FP32] = nullptr;
   k.pass_ws_smem[RPCA_PREC_FP32] = 0;
   k.pass_ws[RPCA_PREC_TF32X3] = (void*)pass_ws_kernel<TB, KP, false, true>;
   k.pass_ws_smem[RPCA_PREC_TF32X3] = pass_ws_smem<TB, KP, false>();
   k.pass_ws[RPCA_PREC_BF16X3] = (void*)pass_ws_kernel<TB, KP, true, true>;
   k.pass_ws_smem[RPCA_PREC_BF16X3] = pass_ws_smem<TB, KP, true>();
-  k.pass_ws[RPCA_PREC_TF32] = (void*)pass_ws_kernel<TB, KP, false, false>;
-  k.pass_ws_smem[RPCA_PREC_TF32] = pass_ws_smem<TB, KP, false>();
+  k.pass_ws[RPCA_PREC_TF32] = nullptr;
+  k.pass_ws_smem[RPCA_PREC_TF32] = 0;
 }
 
 // Tensor-core pass buckets: T <= 16, 20, 32.
@@ -147,7 +149,7 @@ Layout make_layout(int64_t m, int T, int sms, bool wide) {
   L.red = take(sizeof(RedState));
   L.job = take(sizeof(Job));
   const size_t tw = wide ? (size_t)T * T : 1;   // wide-path Gram, Wbar, V
-  L.gw = take(sizeof(float) * tw);
+  L.gw = take(sizeof(double) * tw);
   L.ww = take(sizeof(float) * tw);
   L.vw = take(sizeof(float) * tw);
   L.evw = take(sizeof(double) * (size_t)T);
@@ -158,7 +160,7 @@ Layout make_layout(int64_t m, int T, int sms, bool wide) {
   L.rk = take(sizeof(int) * nrounds * npairs);
   L.rrnd = take(sizeof(int) * 2 * nrounds);
   L.gram_part = take(sizeof(float) * (size_t)maxgrid * T * T);
-  L.group_part = take(sizeof(float) * (size_t)L.ngroups * T * T);
+  L.group_part = take(sizeof(double) * (size_t)L.ngroups * T * T);
   L.scal_part = take(sizeof(double) * 2 * (size_t)maxgrid);
   L.gscal_part = take(sizeof(double) * 2 * (size_t)L.ngroups);
   L.ybuf = take(sizeof(float) * (size_t)m * T);
@@ -185,6 +187,10 @@ rpca_status validate(const rpca_params* p) {
   if (p->dtype != RPCA_R32 && p->dtype != RPCA_C64) return RPCA_ERR_ARG;
   if (p->dtype == RPCA_C64 && (2 * p->T > kMaxTW || p->precision != RPCA_PREC_FP32)) return RPCA_ERR_UNSUPPORTED;
   if (p->precision < RPCA_PREC_FP32 || p->precision > RPCA_PREC_TF32) return RPCA_ERR_ARG;
+  // one TF32 product per contraction (10-bit mantissa) leaves L and S about
+  // 7e-4 from the FP64 solution on the 262144 x 20 window, outside the 1e-4
+  // bound of the reduced precisions, so it is not offered
+  if (p->precision == RPCA_PREC_TF32) return RPCA_ERR_UNSUPPORTED;
   if (p->precision != RPCA_PREC_FP32 && p->drive == RPCA_DRIVE_HOST) return RPCA_ERR_UNSUPPORTED;
   if (p->precision != RPCA_PREC_FP32 && p->T > kMaxT) return RPCA_ERR_UNSUPPORTED;  // wide path is FP32
   if (p->m * (int64_t)p->T > (int64_t)1 << 40) return RPCA_ERR_ARG;
@@ -210,7 +216,7 @@ struct rpca_plan_s {
   char* ws;
   bool own_ws;
   double lambda;
-  int eig_fp64;
+  int eig_fp32;       // opt-in FP32 rotations in the narrow eigen-step (RPCA_EIG_FP32=1)
   cudaGraph_t graph;
   cudaGraphExec_t exec;
   Ctrl* ctrl_host;  // pinned
@@ -266,21 +272,21 @@ static cudaError_t launch(void* fn, dim3 g, dim3 blk, void** args, cudaStream_t 
   return cudaLaunchKernel(fn, g, blk, args, smem, s);
 }
 
-// Eigen-step kernel of a plan: FP64 rotations when RPCA_EIG_FP64 is set, else
-// the fast FP32 form.  Both take (Bufs, flags, handle, use_cond, ...); the
-// extra pointer arguments only exist in the smem form and are ignored by the
-// fast one.
+// Eigen-step kernel of a plan: FP64 Jacobi rotations and basis arithmetic,
+// or FP32 ones when RPCA_EIG_FP32 is set.  Both take (Bufs, flags, handle,
+// use_cond, ...); the extra pointer arguments of the argument lists below
+// are ignored.
 static void* eig_fn(const rpca_plan_s* pl) {
   if (pl->wide) return pl->wk.eig;
-  return pl->eig_fp64 ? pl->ks.eig64 : pl->ks.eig_fast;
+  return pl->eig_fp32 ? pl->ks.eig_fast32 : pl->ks.eig_fast;
 }
 static size_t eig_smem(const rpca_plan_s* pl) {
   if (pl->wide) return pl->wk.eig_smem;
-  return pl->eig_fp64 ? 0 : pl->ks.eig_fast_smem;
+  return pl->eig_fp32 ? pl->ks.eig_fast32_smem : pl->ks.eig_fast_smem;
 }
 static dim3 eig_block(const rpca_plan_s* pl) {
   if (pl->wide) return dim3(pl->wk.eig_threads);
-  return dim3(pl->eig_fp64 ? pl->ks.eig_threads : kEigThreads);
+  return dim3(kEigThreads);
 }
 // CUDA-core FP32 passes by mode (narrow: one pixel row per thread, TMA-fed when
 // the plan has tensor maps; wide: tiles).
@@ -526,15 +532,18 @@ static rpca_status plan_create_impl(const rpca_params* p, void* workspace, size_
     }
   }
   pl->lay = make_layout(p->m, Tr, sms, pl->wide);
-  if (!pl->wide && pl->ks.eig_fast_smem > 48 * 1024) {
+  if (!pl->wide) {
     cudaError_t ea = cudaFuncSetAttribute(pl->ks.eig_fast, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)pl->ks.eig_fast_smem);
+    if (ea == cudaSuccess)
+      ea = cudaFuncSetAttribute(pl->ks.eig_fast32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)pl->ks.eig_fast32_smem);
     if (ea != cudaSuccess) {
       delete pl;
       return cuda_status(ea);
     }
   }
-  pl->eig_fp64 = (getenv("RPCA_EIG_FP64") && atoi(getenv("RPCA_EIG_FP64")) != 0) ? 1 : 0;
+  pl->eig_fp32 = (getenv("RPCA_EIG_FP32") && atoi(getenv("RPCA_EIG_FP32")) != 0) ? 1 : 0;
   if (workspace) {
     if (workspace_bytes < pl->lay.total || ((uintptr_t)workspace & 255u)) {
       delete pl;
@@ -556,10 +565,10 @@ static rpca_status plan_create_impl(const rpca_params* p, void* workspace, size_
   b.red = (RedState*)(pl->ws + pl->lay.red);
   b.job = (Job*)(pl->ws + pl->lay.job);
   b.gram_part = (float*)(pl->ws + pl->lay.gram_part);
-  b.group_part = (float*)(pl->ws + pl->lay.group_part);
+  b.group_part = (double*)(pl->ws + pl->lay.group_part);
   b.scal_part = (double*)(pl->ws + pl->lay.scal_part);
   b.gscal_part = (double*)(pl->ws + pl->lay.gscal_part);
-  b.Gw = (float*)(pl->ws + pl->lay.gw);
+  b.Gw = (double*)(pl->ws + pl->lay.gw);
   b.Ww = (float*)(pl->ws + pl->lay.ww);
   b.Vw = (float*)(pl->ws + pl->lay.vw);
   b.evw = (double*)(pl->ws + pl->lay.evw);
@@ -575,6 +584,7 @@ static rpca_status plan_create_impl(const rpca_params* p, void* workspace, size_
   // a sharded plan's passes finish their reduction themselves, so the summed
   // Gram and residual sums sit in the reduction record between the steps
   b.finalize = p->sharded ? 1 : 0;
+  b.eig64 = pl->wide ? 0 : (pl->eig_fp32 ? 0 : 1);
 
   const int mT = (int)std::max<int64_t>(p->m, p->T);
   pl->lambda = p->lambda > 0 ? p->lambda : 1.0 / sqrt((double)mT);
@@ -587,7 +597,9 @@ static rpca_status plan_create_impl(const rpca_params* p, void* workspace, size_
   c.mu0_scale = p->mu0_scale;
   c.mu_max_factor = p->mu_max_factor;
   c.tol = p->tol;
-  c.jacobi_eps = pl->eig_fp64 ? 1e-12 : 1e-6;
+  // Jacobi threshold: an off-diagonal pair rotates while |g_pq| > eps sqrt(g_pp g_qq);
+  // FP64 rotations stop 1e2 below the FP32 rounding of the passes' Gram entries
+  c.jacobi_eps = (b.eig64 ? 1e-9 : 1e-6);
   c.warm_sweeps = 4;
   c.cold_sweeps = 30;
   c.warm = p->warm_start;
@@ -855,7 +867,7 @@ rpca_status rpca_gram(const float* X, int64_t m, int32_t T, const float* V, doub
   c.k = 0;
   c.done = 0;
   c.f_inv_mu = 1.f;
-  std::vector<float> gred(kMaxT * kMaxT);
+  std::vector<double> gred(kMaxT * kMaxT);
   if (e == cudaSuccess) e = cudaMemcpy(b.ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(b.job, &j, sizeof(Job), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(b.eig->V32, v32.data(), sizeof(float) * kMaxT * kMaxT, cudaMemcpyHostToDevice);
@@ -863,7 +875,7 @@ rpca_status rpca_gram(const float* X, int64_t m, int32_t T, const float* V, doub
   if (e == cudaSuccess)
     e = launch(pl->ks.pass[PM_GRAM], dim3(pl->lay.grid), dim3(kPassThreads), a_pass, s, pl->ks.pass_smem);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e == cudaSuccess) e = cudaMemcpy(gred.data(), b.red->G, sizeof(float) * kMaxT * kMaxT, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(gred.data(), b.red->G, sizeof(double) * kMaxT * kMaxT, cudaMemcpyDeviceToHost);
   std::vector<double> gh((size_t)T * T);
   for (int r = 0; r < T; ++r)
     for (int cc = 0; cc < T; ++cc) gh[r * T + cc] = gred[r * kMaxT + cc];
@@ -980,7 +992,7 @@ rpca_status rpca_step_run(rpca_plan_t pl, int32_t step, void* stream) {
   }
 }
 
-rpca_status rpca_step_sums(rpca_plan_t pl, float** gram, double** sums) {
+rpca_status rpca_step_sums(rpca_plan_t pl, double** gram, double** sums) {
   if (!pl || !pl->p.sharded || !gram || !sums) return RPCA_ERR_ARG;
   *gram = pl->bufs.red->G;
   *sums = &pl->bufs.red->e2;

@@ -91,7 +91,7 @@ struct EigState {
 
 // Cross-CTA reduction state (two levels, last-arriving CTA reduces).
 struct RedState {
-  float G[kMaxT * kMaxT];      // final Gram (row-major), written by the last CTA
+  double G[kMaxT * kMaxT];     // final Gram (row-major, FP64 sums of the CTAs' FP32 partials)
   double e2;                   // sum of E^2 (or ||X||_F^2 in the init pass)
   double l1;                   // sum |X| (init pass)
   unsigned long long t_start;  // earliest CTA start of the last pass (globaltimer)
@@ -131,8 +131,8 @@ struct Bufs {
   EigState* eig;
   RedState* red;
   Job* job;
-  float* gram_part;    // [grid][T*T]
-  float* group_part;   // [ngroups][T*T]
+  float* gram_part;    // [grid][T*T] FP32 partial Gram of each CTA
+  double* group_part;  // [ngroups][T*T] FP64 sums of the partials of each group of CTAs
   double* scal_part;   // [grid][2]
   double* gscal_part;  // [ngroups][2]
   int64_t m;
@@ -143,9 +143,10 @@ struct Bufs {
   int wide;            // tiled path: the reduced Gram goes to Gw (T x T), else to red->G (kMaxT stride)
   int finalize;        // 1: the pass itself sums the group partials into red->G, e2, l1;
                        // 0: the next eigen-step does (saves a serial reduction level)
+  int eig64;           // narrow eigen-step: 1 FP64 Jacobi rotations and basis arithmetic, 0 FP32
   // T > kMaxT ("wide" windows): the reduced Gram, Wbar and V live in these
   // T x T row-major arrays of the workspace instead of red->G and EigState.
-  float* Gw;
+  double* Gw;          // FP64 sums of the partial Grams (also scratch of the eigen-step)
   float* Ww;
   float* Vw;
   double* evw;

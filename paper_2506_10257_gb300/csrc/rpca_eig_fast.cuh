@@ -1,10 +1,11 @@
-// rpca_eig_fast.cuh -- eigen-step with FP32 Jacobi rotations (included inside
+// rpca_eig_fast.cuh -- the narrow eigen-step (T <= 32): cyclic Jacobi on the
+// rotated Gram, in FP64 (default) or FP32 rotations (included inside
 // namespace rpca by rpca_kernels.cuh).
 //
 // The rotated Gram G~ = V^T Z^T Z V of the next iteration arrives nearly
-// diagonal, so a few cyclic Jacobi sweeps in FP32 diagonalise it to the
-// accuracy of its FP32 entries.  Each round of a sweep annihilates T/2
-// disjoint (p, q) pairs (round-robin order):
+// diagonal (V is the basis the pass rotated Z into), so a few cyclic Jacobi
+// sweeps diagonalise it.  Each round of a sweep annihilates T/2 disjoint
+// (p, q) pairs (round-robin order):
 //   phase A  T/2 threads compute the rotations (GVL sym.schur2) and the exact
 //            new diagonal entries, and log them;
 //   phase B  one thread per upper-triangle entry forms (J^T G J)_ab from four
@@ -12,38 +13,54 @@
 // The eigenvector update is not done per round: after the sweeps every row of
 // Q (the product of the logged rotations) is accumulated in registers by one
 // thread, with the (p, q) indices of each round known at compile time.  Then
-// V_new = V_old Q, one Newton-Schulz step keeps it orthonormal, and the FP64
-// part follows: sigma = sqrt(lambda), the sigma > tau = 1/mu decision and
+// V_new = V Q with V the basis the pass used, one Newton-Schulz step
+// V <- V (3I - V^T V)/2 makes it orthonormal (to first order this also
+// removes the departure of the FP32-rounded V from orthonormality), and the
+// decisions follow in FP64: sigma = sqrt(lambda), sigma > tau = 1/mu and
 // g = min(1, tau/sigma), with Wbar = V diag(g) V^T (Eq. 4 through the Gram).
+// Real = double does all of that in FP64 (the Gram arrives as FP64 sums) and
+// rounds Wbar and V to FP32 once for the passes; Real = float is the faster
+// opt-in with FP32 rotations and basis arithmetic.
 #pragma once
 
 constexpr int kEigLogSweeps = 10;  // sweeps one eigen-step may take (and log)
 constexpr int kEigThreads = 256;   // threads of the eigen-step CTA
 
-template <int TB>
+template <typename Real>
+struct Pair2 {
+  Real x, y;
+};
+
+template <int TB, typename Real>
 struct EigFastSmem {
-  float G[2][TB * (TB + 1)];
-  float2 log[kEigLogSweeps][TB - 1][TB / 2];
+  Real G[2][TB * (TB + 1)];
+  Pair2<Real> log[kEigLogSweeps][TB - 1][TB / 2];
   int ran[kEigLogSweeps][TB - 1];
-  float2 cs[2][TB / 2];       // rotations of the current round and of the next (by round parity)
+  Pair2<Real> cs[2][TB / 2];  // rotations of the current round and of the next (by round parity)
   int2 pq[TB - 1][TB / 2];   // (p, q), p < q, of every pair of every round (fixed order)
   int2 pinfo[TB - 1][TB];    // (pair index, slot) of every index in every round
-  float dnew[2][TB];          // new diagonal entries, same double buffering
-  float A[TB * (TB + 1)];
+  Real dnew[2][TB];           // new diagonal entries, same double buffering
+  Real A[TB * (TB + 1)];
   double ev[TB];
-  float g[TB];
+  Real g[TB];
 };
+
+__device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_r(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float recip_r(float x) { return __fdividef(1.f, x); }
+__device__ __forceinline__ double recip_r(double x) { return 1.0 / x; }
 
 // The eigen-step on one CTA of kEigThreads threads; `dsm` holds
 // sizeof(EigFastSmem<TB>) bytes of shared memory.
-template <int TB>
+template <int TB, typename Real>
 __device__ void eig_fast_body(Bufs b, int flags, cudaGraphConditionalHandle h, int use_cond, unsigned char* dsm) {
   constexpr int K = TB / 2;
   constexpr int NR = TB - 1;
   constexpr int LD = TB + 1;
   constexpr int NE = TB * (TB + 1) / 2;
   constexpr int EPT = (NE + kEigThreads - 1) / kEigThreads;  // upper-triangle entries per thread
-  EigFastSmem<TB>& S = *reinterpret_cast<EigFastSmem<TB>*>(dsm);
+  using P2 = Pair2<Real>;
+  EigFastSmem<TB, Real>& S = *reinterpret_cast<EigFastSmem<TB, Real>*>(dsm);
   __shared__ int sFlag;
   __shared__ double sTau;
 
@@ -56,7 +73,7 @@ __device__ void eig_fast_body(Bufs b, int flags, cudaGraphConditionalHandle h, i
 
   for (int i = tid; i < TB * TB; i += nthr) {
     const int r = i / TB, c = i % TB;
-    S.G[0][r * LD + c] = (r < T && c < T) ? b.red->G[r * kMaxT + c] : 0.f;
+    S.G[0][r * LD + c] = (r < T && c < T) ? (Real)b.red->G[r * kMaxT + c] : (Real)0;
   }
   for (int i = tid; i < NR * K; i += nthr) {
     const int r = i / K, k = i % K;
@@ -71,8 +88,8 @@ __device__ void eig_fast_body(Bufs b, int flags, cudaGraphConditionalHandle h, i
   const unsigned long long t1 = gtimer();
   int rounds_run = 0;
 
-  const float eps = (float)ctrl->jacobi_eps;
-  const float eps2 = eps * eps;
+  const Real eps = (Real)ctrl->jacobi_eps;
+  const Real eps2 = eps * eps;
   int max_sweeps = (cold || (flags & EF_FULL)) ? ctrl->cold_sweeps : ctrl->warm_sweeps;
   if (max_sweeps > kEigLogSweeps) max_sweeps = kEigLogSweeps;
   // upper-triangle entries owned by this thread
@@ -93,42 +110,44 @@ __device__ void eig_fast_body(Bufs b, int flags, cudaGraphConditionalHandle h, i
   }
   // Entry (a, c), a <= c, of J^T G J for round rnd's rotations (buffers cb):
   // pairs not rotated have c = 1, s = 0; a rotated pair's own entry is 0.
-  auto rotated_entry = [&](int rnd, int cb, int cur, int a, int c) -> float {
+  auto rotated_entry = [&](int rnd, int cb, int cur, int a, int c) -> Real {
     if (a == c) return S.dnew[cb][a];
     const int2 ia = S.pinfo[rnd][a], ic = S.pinfo[rnd][c];
     if (ia.x == ic.x) {
-      const float2 r = S.cs[cb][ia.x];
-      return (r.y != 0.f) ? 0.f : S.G[cur][a * LD + c];  // annihilated when rotated
+      const P2 r = S.cs[cb][ia.x];
+      return (r.y != (Real)0) ? (Real)0 : S.G[cur][a * LD + c];  // annihilated when rotated
     }
     const int2 pa2 = S.pq[rnd][ia.x], pc2 = S.pq[rnd][ic.x];
-    const float2 ra = S.cs[cb][ia.x], rc = S.cs[cb][ic.x];
+    const P2 ra = S.cs[cb][ia.x], rc = S.cs[cb][ic.x];
+    // pairs not rotated this round keep their entries (c = 1, s = 0)
+    if (ra.y == (Real)0 && rc.y == (Real)0) return S.G[cur][a * LD + c];
     // column a of J: slot 0 (c, -s) at (p, q); slot 1 (s, c)
-    const float wa0 = ia.y ? ra.y : ra.x, wa1 = ia.y ? ra.x : -ra.y;
-    const float wc0 = ic.y ? rc.y : rc.x, wc1 = ic.y ? rc.x : -rc.y;
-    const float* g0 = &S.G[cur][pa2.x * LD];
-    const float* g1 = &S.G[cur][pa2.y * LD];
+    const Real wa0 = ia.y ? ra.y : ra.x, wa1 = ia.y ? ra.x : -ra.y;
+    const Real wc0 = ic.y ? rc.y : rc.x, wc1 = ic.y ? rc.x : -rc.y;
+    const Real* g0 = &S.G[cur][pa2.x * LD];
+    const Real* g1 = &S.G[cur][pa2.y * LD];
     return wa0 * (wc0 * g0[pc2.x] + wc1 * g0[pc2.y]) + wa1 * (wc0 * g1[pc2.x] + wc1 * g1[pc2.y]);
   };
   // Rotation of pair k of round rnd from (app, aqq, apq) into buffers cb (GVL
   // sym.schur2: t = 2 apq sgn(d) / (|d| + sqrt(d^2 + 4 apq^2)), d = aqq - app);
   // returns whether the pair rotates.
-  auto make_rotation = [&](int rnd, int cb, int sw, int k, float app, float aqq, float apq) -> int {
+  auto make_rotation = [&](int rnd, int cb, int sw, int k, Real app, Real aqq, Real apq) -> int {
     const int2 pq = S.pq[rnd][k];
-    float c = 1.f, s = 0.f, dp = app, dq = aqq;
+    Real c = 1, s = 0, dp = app, dq = aqq;
     int act = 0;
-    if (apq != 0.f && apq * apq > eps2 * fabsf(app * aqq)) {
+    if (apq != (Real)0 && apq * apq > eps2 * fabs(app * aqq)) {
       act = 1;
-      const float dd = aqq - app;
-      const float r2 = fmaf(dd, dd, 4.f * apq * apq);
-      const float den = fabsf(dd) + r2 * rsqrtf(r2);
-      const float t = copysignf(1.f, dd) * (2.f * apq) * __fdividef(1.f, den);
-      c = rsqrtf(fmaf(t, t, 1.f));
+      const Real dd = aqq - app;
+      const Real r2 = fma(dd, dd, (Real)4 * apq * apq);
+      const Real den = fabs(dd) + sqrt(r2);
+      const Real t = copysign((Real)1, dd) * ((Real)2 * apq) * recip_r(den);
+      c = rsqrt_r(fma(t, t, (Real)1));
       s = t * c;
       dp = app - t * apq;
       dq = aqq + t * apq;
     }
-    S.cs[cb][k] = make_float2(c, s);
-    S.log[sw][rnd][k] = make_float2(c, s);
+    S.cs[cb][k] = P2{c, s};
+    S.log[sw][rnd][k] = P2{c, s};
     S.dnew[cb][pq.x] = dp;
     S.dnew[cb][pq.y] = dq;
     return act;
@@ -145,8 +164,8 @@ __device__ void eig_fast_body(Bufs b, int flags, cudaGraphConditionalHandle h, i
     for (int u = 0; u < EPT; ++u) {
       const int a = ea[u], c = ec[u];
       if (a >= 0 && a < c) {
-        const float apq = S.G[cur][a * LD + c];
-        if (apq != 0.f && apq * apq > eps2 * fabsf(S.G[cur][a * LD + a] * S.G[cur][c * LD + c])) need = 1;
+        const Real apq = S.G[cur][a * LD + c];
+        if (apq != (Real)0 && apq * apq > eps2 * fabs(S.G[cur][a * LD + a] * S.G[cur][c * LD + c])) need = 1;
       }
     }
     if (!__syncthreads_or(need)) break;
@@ -167,7 +186,7 @@ __device__ void eig_fast_body(Bufs b, int flags, cudaGraphConditionalHandle h, i
         for (int u = 0; u < EPT; ++u) {
           const int a = ea[u], c = ec[u];
           if (a < 0) continue;
-          const float v = rotated_entry(rnd, cb, cur, a, c);
+          const Real v = rotated_entry(rnd, cb, cur, a, c);
           S.G[nxt][a * LD + c] = v;
           S.G[nxt][c * LD + a] = v;
         }
@@ -176,7 +195,7 @@ __device__ void eig_fast_body(Bufs b, int flags, cudaGraphConditionalHandle h, i
       if (pk >= 0 && rnd + 1 < NR) {
         // the entries (p, p), (q, q), (p, q) of the next round's pair after this round
         const int2 pq = S.pq[rnd + 1][pk];
-        float app, aqq, apq;
+        Real app, aqq, apq;
         if (any) {
           app = S.dnew[cb][pq.x];
           aqq = S.dnew[cb][pq.y];
@@ -199,9 +218,9 @@ __device__ void eig_fast_body(Bufs b, int flags, cudaGraphConditionalHandle h, i
   if (tid < TB) S.ev[tid] = (double)S.G[cur][tid * LD + tid];
   const int qb = cur ^ 1;  // Q goes to the other G buffer
   if (tid < TB) {
-    float qr[TB];
+    Real qr[TB];
 #pragma unroll
-    for (int j = 0; j < TB; ++j) qr[j] = (j == tid) ? 1.f : 0.f;
+    for (int j = 0; j < TB; ++j) qr[j] = (j == tid) ? (Real)1 : (Real)0;
     for (int sw = 0; sw < sweeps; ++sw) {
 #pragma unroll
       for (int rnd = 0; rnd < NR; ++rnd) {
@@ -211,8 +230,9 @@ __device__ void eig_fast_body(Bufs b, int flags, cudaGraphConditionalHandle h, i
           int pa, pb;
           rr_pair(rnd, k, TB, pa, pb);
           const int p = pa < pb ? pa : pb, q = pa < pb ? pb : pa;
-          const float2 r = S.log[sw][rnd][k];
-          const float xp = qr[p], xq = qr[q];
+          const P2 r = S.log[sw][rnd][k];
+          if (r.y == (Real)0) continue;  // not rotated
+          const Real xp = qr[p], xq = qr[q];
           qr[p] = r.x * xp - r.y * xq;
           qr[q] = r.y * xp + r.x * xq;
         }
@@ -223,37 +243,47 @@ __device__ void eig_fast_body(Bufs b, int flags, cudaGraphConditionalHandle h, i
   }
   __syncthreads();
   const unsigned long long t3 = gtimer();
-  // old basis -> S.A
+  // the basis the pass used (V32, exact in FP64) -> S.A
   for (int i = tid; i < TB * TB; i += nthr) {
     const int r = i / TB, c = i % TB;
-    float v = (r == c) ? 1.f : 0.f;
-    if (!cold && r < T && c < T) v = b.eig->V32[r * kMaxT + c];
+    Real v = (r == c) ? (Real)1 : (Real)0;
+    if (!cold && r < T && c < T) v = (Real)b.eig->V32[r * kMaxT + c];
     S.A[r * LD + c] = v;
   }
   __syncthreads();
-  // V_new = V_old Q  -> S.G[cur]
+  // V_new = V_old Q  -> S.G[cur] (rows and columns past T stay zero)
   for (int i = tid; i < TB * TB; i += nthr) {
     const int r = i / TB, c = i % TB;
-    float acc = 0.f;
+    Real acc = 0;
+    if (r < T && c < T) {
 #pragma unroll 4
-    for (int j = 0; j < TB; ++j) acc = fmaf(S.A[r * LD + j], S.G[qb][j * LD + c], acc);
+      for (int j = 0; j < T; ++j) acc = fma(S.A[r * LD + j], S.G[qb][j * LD + c], acc);
+    }
     S.G[cur][r * LD + c] = acc;
   }
   __syncthreads();
-  // Newton-Schulz: P = 1.5 I - 0.5 V^T V -> S.A ; V <- V P -> S.G[qb]
+  // Newton-Schulz: P = 1.5 I - 0.5 V^T V -> S.A (symmetric: upper triangle
+  // computed, mirrored); V <- V P -> S.G[qb]
   for (int i = tid; i < TB * TB; i += nthr) {
     const int a = i / TB, c = i % TB;
-    float acc = 0.f;
+    if (a > c) continue;
+    Real acc = 0;
+    if (c < T) {
 #pragma unroll 4
-    for (int r = 0; r < TB; ++r) acc = fmaf(S.G[cur][r * LD + a], S.G[cur][r * LD + c], acc);
-    S.A[a * LD + c] = (a == c ? 1.5f : 0.f) - 0.5f * acc;
+      for (int r = 0; r < T; ++r) acc = fma(S.G[cur][r * LD + a], S.G[cur][r * LD + c], acc);
+    }
+    const Real v = (a == c ? (Real)1.5 : (Real)0) - (Real)0.5 * acc;
+    S.A[a * LD + c] = v;
+    S.A[c * LD + a] = v;
   }
   __syncthreads();
   for (int i = tid; i < TB * TB; i += nthr) {
     const int r = i / TB, c = i % TB;
-    float acc = 0.f;
+    Real acc = 0;
+    if (r < T && c < T) {
 #pragma unroll 4
-    for (int a = 0; a < TB; ++a) acc = fmaf(S.G[cur][r * LD + a], S.A[a * LD + c], acc);
+      for (int a = 0; a < T; ++a) acc = fma(S.G[cur][r * LD + a], S.A[a * LD + c], acc);
+    }
     S.G[qb][r * LD + c] = acc;
   }
 
@@ -271,17 +301,21 @@ __device__ void eig_fast_body(Bufs b, int flags, cudaGraphConditionalHandle h, i
   if (tid < TB) {
     const double sig = sqrt(fmax(S.ev[tid], 0.0));
     keep = (tid < T) && (sig > sTau);
-    S.g[tid] = keep ? (float)(sTau / sig) : 1.f;
+    S.g[tid] = keep ? (Real)(sTau / sig) : (Real)1;
   }
   const int rank = __syncthreads_count(keep);
 
-  const float* Vn = S.G[qb];
+  // Wbar = V diag(g) V^T (symmetric: upper triangle, mirrored), rounded to
+  // FP32 once; V rounded to FP32 for the next pass
+  const Real* Vn = S.G[qb];
   for (int i = tid; i < T * T; i += nthr) {
     const int a = i / T, c = i % T;
-    float acc = 0.f;
-    for (int j = 0; j < T; ++j) acc = fmaf(Vn[a * LD + j] * S.g[j], Vn[c * LD + j], acc);
-    b.eig->Wbar[a * kMaxT + c] = acc;
-    b.eig->V32[a * kMaxT + c] = Vn[a * LD + c];
+    b.eig->V32[a * kMaxT + c] = (float)Vn[a * LD + c];
+    if (a > c) continue;
+    Real acc = 0;
+    for (int j = 0; j < T; ++j) acc = fma(Vn[a * LD + j] * S.g[j], Vn[c * LD + j], acc);
+    b.eig->Wbar[a * kMaxT + c] = (float)acc;
+    b.eig->Wbar[c * kMaxT + a] = (float)acc;
   }
   if (tid < T) b.eig->evals[tid] = S.ev[tid];
   if (tid == 0) {
@@ -300,9 +334,9 @@ __device__ void eig_fast_body(Bufs b, int flags, cudaGraphConditionalHandle h, i
   }
 }
 
-template <int TB>
+template <int TB, typename Real>
 __global__ void __launch_bounds__(kEigThreads) eig_fast_kernel(Bufs b, int flags, cudaGraphConditionalHandle h,
                                                                int use_cond) {
   extern __shared__ __align__(16) unsigned char eig_smem_raw[];
-  eig_fast_body<TB>(b, flags, h, use_cond, eig_smem_raw);
+  eig_fast_body<TB, Real>(b, flags, h, use_cond, eig_smem_raw);
 }

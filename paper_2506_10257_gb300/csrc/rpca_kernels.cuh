@@ -17,6 +17,17 @@ __device__ __forceinline__ float form_z(float x, float s, float y, float inv_mu)
   return (x - s) + y * inv_mu;
 }
 
+// Whether the solve has ended, as one value for the whole CTA (thread 0
+// reads the flag): in a persistent launch another CTA may mark a window
+// failed at any time, and every thread must take the same branch around the
+// barriers that follow.
+__device__ __forceinline__ bool solve_done_uniform(const Ctrl* ctrl) {
+  __shared__ int sDoneFlag;
+  if (threadIdx.x == 0) sDoneFlag = __ldcg(&ctrl->done);
+  __syncthreads();
+  return sDoneFlag != 0;
+}
+
 // Jacobi round-robin pairing (circle method) on n indices, round r in [0, n-1).
 __device__ __forceinline__ void rr_pair(int r, int i, int n, int& a, int& b) {
   const int k = n - 1;
@@ -106,49 +117,43 @@ __device__ __forceinline__ void vec_mat(const float (&z)[TB], const float* M, fl
   }
 }
 
-__device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
-  const float y = v - c;
-  const float t = s + y;
-  c = (t - s) - y;
-  s = t;
-}
-
-// Sums rows [r0, r1) of a row-major [rows][TT] float array entry by entry in a
-// fixed order (Kahan), calling out(e, sum) for every entry; each thread takes
-// entries tid, tid + blockDim, ... and issues its loads in batches of 16 so
-// that their L2 latencies overlap.
-template <int W = 1, typename Out>
-__device__ __forceinline__ void sum_rows(const float* src, int r0, int r1, int TT, Out out) {
+// Sums rows [r0, r1) of a row-major [rows][TT] array (float partials of the
+// CTAs, or double group sums) entry by entry in FP64 in a fixed row order,
+// calling out(e, sum) for every entry; each thread takes entries tid,
+// tid + blockDim, ... and issues its loads in batches of 16 so that their L2
+// latencies overlap.  Sums of FP32 products in FP64 are exact to about 2^-53
+// of their magnitude, so the reduced Gram carries only the rounding of the
+// CTAs' own FP32 accumulations.
+template <int W = 1, typename Src, typename Out>
+__device__ __forceinline__ void sum_rows(const Src* src, int r0, int r1, int TT, Out out) {
   // W = 4: four entries per step (T x T Grams of wide windows), so that 64
   // loads are in flight per thread
   int e = threadIdx.x;
   for (; W == 4 && e + 3 * (int)blockDim.x < TT; e += 4 * blockDim.x) {
-    float s[4] = {0.f, 0.f, 0.f, 0.f}, comp[4] = {0.f, 0.f, 0.f, 0.f};
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
     for (int rb = r0; rb < r1; rb += 16) {
-      float v[4][16];
+      Src v[4][16];
 #pragma unroll
       for (int q = 0; q < 4; ++q)
 #pragma unroll
         for (int u = 0; u < 16; ++u)
-          v[q][u] = (rb + u < r1) ? __ldcg(&src[(int64_t)(rb + u) * TT + e + q * blockDim.x]) : 0.f;
+          v[q][u] = (rb + u < r1) ? __ldcg(&src[(int64_t)(rb + u) * TT + e + q * blockDim.x]) : (Src)0;
 #pragma unroll
       for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int u = 0; u < 16; ++u)
-          if (rb + u < r1) kahan_add(s[q], comp[q], v[q][u]);
+        for (int u = 0; u < 16; ++u) s[q] += (double)v[q][u];
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) out(e + q * blockDim.x, s[q]);
   }
   for (; e < TT; e += blockDim.x) {
-    float s = 0.f, comp = 0.f;
+    double s = 0.0;
     for (int rb = r0; rb < r1; rb += 16) {
-      float v[16];
+      Src v[16];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) v[u] = (rb + u < r1) ? __ldcg(&src[(int64_t)(rb + u) * TT + e]) : 0.f;
+      for (int u = 0; u < 16; ++u) v[u] = (rb + u < r1) ? __ldcg(&src[(int64_t)(rb + u) * TT + e]) : (Src)0;
 #pragma unroll
-      for (int u = 0; u < 16; ++u)
-        if (rb + u < r1) kahan_add(s, comp, v[u]);
+      for (int u = 0; u < 16; ++u) s += (double)v[u];
     }
     out(e, s);
   }
@@ -211,8 +216,8 @@ static __device__ __noinline__ bool cross_cta_reduce(Bufs b, bool kGram, double*
   if (!sLast) return false;
   __threadfence();
   if (kGram) {
-    float* gp = b.group_part + (int64_t)grp * TT;
-    sum_rows<W>(b.gram_part, c0, c1, TT, [&](int e, float v) { gp[e] = v; });
+    double* gp = b.group_part + (int64_t)grp * TT;
+    sum_rows<W>(b.gram_part, c0, c1, TT, [&](int e, double v) { gp[e] = v; });
   }
   sum_scalars(b.scal_part, c0, c1, sScal, [&](double s0, double s1) {
     b.gscal_part[2 * grp] = s0;
@@ -242,11 +247,11 @@ static __device__ __noinline__ bool cross_cta_reduce(Bufs b, bool kGram, double*
   __threadfence();
   if (kGram) {
     if (b.wide) {
-      float* G = b.Gw;
-      sum_rows<W>(b.group_part, 0, ngroups, TT, [&](int e, float v) { G[e] = v; });
+      double* G = b.Gw;
+      sum_rows<W>(b.group_part, 0, ngroups, TT, [&](int e, double v) { G[e] = v; });
     } else {
-      float* G = b.red->G;
-      sum_rows(b.group_part, 0, ngroups, TT, [&](int e, float v) { G[(e / T) * kMaxT + e % T] = v; });
+      double* G = b.red->G;
+      sum_rows(b.group_part, 0, ngroups, TT, [&](int e, double v) { G[(e / T) * kMaxT + e % T] = v; });
     }
   }
   sum_scalars(b.gscal_part, 0, ngroups, sScal, [&](double s0, double s1) {
@@ -395,7 +400,7 @@ __device__ bool pass_body(Bufs b, int lc, int nc, unsigned char* dsm) {
   __shared__ int sLast;
 
   const Ctrl* ctrl = b.ctrl;
-  if (__ldcg(&ctrl->done)) return false;
+  if (solve_done_uniform(ctrl)) return false;
   const int tid = threadIdx.x;
   if (tid == 0) atomicMin(&b.red->t_start, gtimer());
   const int T = b.T;
@@ -571,11 +576,11 @@ static __device__ void finalize_sums(Bufs b, double* sh) {
   const int ng = b.red->ngroups_last;
   if (b.red->gram_last) {
     if (b.wide) {
-      float* G = b.Gw;
-      sum_rows<4>(b.group_part, 0, ng, TT, [&](int e, float v) { G[e] = v; });
+      double* G = b.Gw;
+      sum_rows<4>(b.group_part, 0, ng, TT, [&](int e, double v) { G[e] = v; });
     } else {
-      float* G = b.red->G;
-      sum_rows(b.group_part, 0, ng, TT, [&](int e, float v) { G[(e / T) * kMaxT + e % T] = v; });
+      double* G = b.red->G;
+      sum_rows(b.group_part, 0, ng, TT, [&](int e, double v) { G[(e / T) * kMaxT + e % T] = v; });
     }
   }
   sum_scalars(b.gscal_part, 0, ng, sh, [&](double s0, double s1) {
@@ -988,5 +993,6 @@ static __global__ void begin_kernel(Bufs b, const float* X, float* L, float* S, 
 #include "rpca_pass_ws.cuh"
 #include "rpca_pass_fs.cuh"
 #include "rpca_eig_fast.cuh"
+#include "rpca_eig64.cuh"
 
 }  // namespace rpca

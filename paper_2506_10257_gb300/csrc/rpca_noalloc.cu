@@ -39,29 +39,54 @@ constexpr size_t kNaJob = na_align(kNaRed + sizeof(RedState));
 constexpr size_t kNaHeader = na_align(kNaJob + sizeof(Job));      // zeroed by every call
 constexpr size_t kNaGram = kNaHeader;
 constexpr size_t kNaGroup = na_align(kNaGram + sizeof(float) * kNaMaxGrid * kMaxT * kMaxT);
-constexpr size_t kNaScal = na_align(kNaGroup + sizeof(float) * kNaMaxGroups * kMaxT * kMaxT);
+constexpr size_t kNaScal = na_align(kNaGroup + sizeof(double) * kNaMaxGroups * kMaxT * kMaxT);
 constexpr size_t kNaGscal = na_align(kNaScal + sizeof(double) * 2 * kNaMaxGrid);
-constexpr size_t kNaBytes = na_align(kNaGscal + sizeof(double) * 2 * kNaMaxGroups);  // about 2.2 MB
+constexpr size_t kNaBytes = na_align(kNaGscal + sizeof(double) * 2 * kNaMaxGroups);  // about 2.4 MB
 
 // The scratch: one copy per GPU that loads the library, held until the process exits.
 static __device__ __align__(256) unsigned char g_rpca_noalloc_scratch[kNaBytes];
 
 constexpr int kNaMaxDevices = 64;
 std::mutex g_na_mu;
-void* g_na_ptr[kNaMaxDevices];  // device address of the scratch, per device
+void* g_na_ptr[kNaMaxDevices];   // device address of the scratch, per device ...
+void* g_na_ctx[kNaMaxDevices];   // ... and the context it was looked up in
 
-// Device address of the scratch on the current device (set up once per device).
+// The calling thread's current CUDA context (driver cuCtxGetCurrent, looked
+// up once through the runtime), or NULL when it cannot be had.
+void* current_context() {
+  typedef int (*CtxGetCurrent)(void**);
+  static CtxGetCurrent fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (CtxGetCurrent)f;
+  }
+  void* ctx = nullptr;
+  if (!fn || fn(&ctx) != 0) return nullptr;
+  return ctx;
+}
+
+// Device address of the scratch on the current device: looked up the first
+// time a device is used, and again whenever the device's current context is
+// another one than at the last lookup (after cudaDeviceReset the primary
+// context, and with it the array's address, is new).
 cudaError_t na_scratch(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kNaMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lk(g_na_mu);
-  if (!g_na_ptr[dev]) {
+  void* ctx = current_context();
+  if (!g_na_ptr[dev] || !ctx || ctx != g_na_ctx[dev]) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_rpca_noalloc_scratch);
     if (e != cudaSuccess) return e;
     g_na_ptr[dev] = p;
+    g_na_ctx[dev] = current_context();  // (the lookup makes the primary context current)
   }
   *out = g_na_ptr[dev];
   return cudaSuccess;
@@ -87,7 +112,7 @@ __global__ void na_setup_kernel(Bufs b, const float* X, const float* V, int T) {
 
 // G (row-major T x T, float64) from the reduced Gram.
 __global__ void na_store_kernel(Bufs b, double* G, int T) {
-  for (int i = threadIdx.x; i < T * T; i += blockDim.x) G[i] = (double)b.red->G[(i / T) * kMaxT + i % T];
+  for (int i = threadIdx.x; i < T * T; i += blockDim.x) G[i] = b.red->G[(i / T) * kMaxT + i % T];
 }
 
 void* na_pass_fn(int T) {
@@ -139,7 +164,7 @@ extern "C" rpca_status rpca_gram_noalloc(const float* X, int64_t m, int32_t T, c
   b.red = (RedState*)(s0 + kNaRed);
   b.job = (Job*)(s0 + kNaJob);
   b.gram_part = (float*)(s0 + kNaGram);
-  b.group_part = (float*)(s0 + kNaGroup);
+  b.group_part = (double*)(s0 + kNaGroup);
   b.scal_part = (double*)(s0 + kNaScal);
   b.gscal_part = (double*)(s0 + kNaGscal);
   b.m = m;

@@ -81,7 +81,7 @@ __device__ bool pass_fs_body(Bufs b, int lc, int nc, unsigned char* dsm) {
   __shared__ int sLast;
 
   const Ctrl* ctrl = b.ctrl;
-  if (__ldcg(&ctrl->done)) return false;
+  if (solve_done_uniform(ctrl)) return false;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) atomicMin(&b.red->t_start, gtimer());
   const int T = b.T;

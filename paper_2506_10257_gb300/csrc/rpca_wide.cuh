@@ -135,7 +135,7 @@ __device__ bool pass_wide_body(Bufs b, int lc, int nc, float* wide_smem) {
   __shared__ int sLast;
 
   const Ctrl* ctrl = b.ctrl;
-  if (__ldcg(&ctrl->done)) return false;
+  if (solve_done_uniform(ctrl)) return false;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   if (tid == 0) atomicMin(&b.red->t_start, gtimer());
   const int T = b.T;
@@ -449,7 +449,7 @@ __device__ bool pass_res_body(Bufs b, int lc, int nc, float* smem) {
   __shared__ int sLast;
 
   const Ctrl* ctrl = b.ctrl;
-  if (__ldcg(&ctrl->done)) return false;
+  if (solve_done_uniform(ctrl)) return false;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int tx = tid & 15, ty = tid >> 4;     // column group, pixel group
   const int c0 = tx * CPT, p0 = 4 * ty;

@@ -29,7 +29,7 @@ MAX_T_NARROW = 32
 EXPORTED = ["rpca_params_default", "rpca_workspace_size", "rpca_plan_create", "rpca_solve", "rpca_solve_host",
             "rpca_plan_result", "rpca_plan_destroy", "rpca_status_str", "rpca_gram", "rpca_eig",
             "rpca_gram_noalloc", "rpca_plan_timings", "rpca_batch_create", "rpca_batch_solve",
-            "rpca_batch_tune", "rpca_batch_info", "rpca_batch_window_ctas", "rpca_batch_destroy", "rpca_batch_schedule",
+            "rpca_batch_solve_host", "rpca_batch_tune", "rpca_batch_set_schedule", "rpca_batch_info", "rpca_batch_window_ctas", "rpca_batch_destroy", "rpca_batch_schedule",
             "rpca_server_create", "rpca_server_set_warm", "rpca_submit", "rpca_poll", "rpca_server_wait",
             "rpca_server_stats", "rpca_server_destroy", "rpca_prefilter_scratch_bytes", "rpca_prefilter",
             "rpca_prefilter_highpass", "rpca_step_begin", "rpca_step_run", "rpca_step_sums", "rpca_step_done"]
@@ -101,7 +101,7 @@ def load(build_if_missing: bool = True):
     lib.rpca_gram_noalloc.argtypes = [vp, i64, i32, vp, vp, vp]
     lib.rpca_step_begin.argtypes = [vp, vp, vp, vp, vp, f32, vp]
     lib.rpca_step_run.argtypes = [vp, i32, vp]
-    lib.rpca_step_sums.argtypes = [vp, ctypes.POINTER(ctypes.POINTER(ctypes.c_float)),
+    lib.rpca_step_sums.argtypes = [vp, ctypes.POINTER(ctypes.POINTER(ctypes.c_double)),
                                    ctypes.POINTER(ctypes.POINTER(ctypes.c_double))]
     lib.rpca_step_done.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(Result), vp]
     lib.rpca_prefilter_scratch_bytes.argtypes = [i64, i32]
@@ -111,7 +111,9 @@ def load(build_if_missing: bool = True):
     lib.rpca_plan_timings.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i32]
     lib.rpca_batch_create.argtypes = [ctypes.POINTER(Params), i32, ctypes.POINTER(vp)]
     lib.rpca_batch_solve.argtypes = [vp, ctypes.POINTER(Window), vp, ctypes.POINTER(Result)]
+    lib.rpca_batch_solve_host.argtypes = [vp, ctypes.POINTER(Window), vp, ctypes.POINTER(Result)]
     lib.rpca_batch_tune.argtypes = [vp, ctypes.POINTER(Window), vp, i32, ctypes.POINTER(ctypes.c_double)]
+    lib.rpca_batch_set_schedule.argtypes = [vp, i32, ctypes.c_double, i32, i32]
     lib.rpca_batch_info.argtypes = [vp, ctypes.POINTER(i32), i32]
     lib.rpca_batch_window_ctas.argtypes = [vp, ctypes.POINTER(i32), i32]
     lib.rpca_batch_schedule.argtypes = [i32, vp, vp, vp, i32, i32, ctypes.c_double, ctypes.POINTER(i32), vp, vp, vp]
@@ -313,17 +315,24 @@ def eig(G):
 def gram_noalloc(frames, V=None, G=None, stream=None):
     """Same Gram as ``gram`` through rpca_gram_noalloc, which allocates no device
     memory (its scratch is a fixed array inside the library).  The output G
-    (T, T) float64 is allocated here by the caller side unless given."""
+    (T, T) float64 is allocated here by the caller side unless given.  The call
+    is asynchronous on `stream` (default: the current stream)."""
     torch = _torch()
     T, m = frames.shape
+    s = stream if stream is not None else torch.cuda.current_stream()
     if G is None:
         G = torch.empty((T, T), dtype=torch.float64, device="cuda")
     vptr = 0
     if V is not None:
-        V = V.to(device="cuda", dtype=torch.float32).contiguous()
+        V2 = V.to(device="cuda", dtype=torch.float32).contiguous()
+        if V2.data_ptr() != V.data_ptr() and s != torch.cuda.current_stream():
+            # a converted copy lives in the current stream's pool: keep it from
+            # being reused before the kernels on `s` have read it
+            V2.record_stream(s)
+        V = V2
         vptr = V.data_ptr()
     st = load().rpca_gram_noalloc(ctypes.c_void_p(frames.data_ptr()), m, T, ctypes.c_void_p(vptr),
-                                  ctypes.c_void_p(G.data_ptr()), _stream_handle(stream))
+                                  ctypes.c_void_p(G.data_ptr()), ctypes.c_void_p(s.cuda_stream))
     if st != OK:
         raise RpcaError(st, "rpca_gram_noalloc")
     return G
@@ -468,6 +477,39 @@ class Batch:
         self._keep = (frames, Ls, Ss, masks)
         return Ls, Ss, ([r.as_dict() for r in res] if wait else None)
 
+    def solve_host(self, frames, Ls, Ss, masks=None, thetas=None, stream=None, wait: bool = True):
+        """Solve windows held in HOST memory through rpca_batch_solve_host.
+
+        frames, Ls, Ss (and masks): per window a contiguous CPU tensor (pinned
+        for full copy speed) of the window's shape, (T, m) float32 or complex64
+        (masks: (m,) uint8).  The library uploads, solves in one persistent
+        launch and downloads into Ls, Ss, masks.  With wait=False the call
+        returns once enqueued (the buffers must stay untouched until a later
+        call with wait=True returns) and results is None."""
+        import torch
+        if len(frames) != self.n:
+            raise ValueError(f"expected {self.n} windows, got {len(frames)}")
+        w = (Window * self.n)()
+        for i, F in enumerate(frames):
+            m, T = self.shapes[i]
+            for name, t in (("frames", F), ("L", Ls[i]), ("S", Ss[i])):
+                if (t.device.type != "cpu" or not t.is_contiguous() or tuple(t.shape) != (T, m)
+                        or t.dtype not in (torch.float32, torch.complex64) or t.dtype != F.dtype):
+                    raise ValueError(f"window {i}: {name} must be a contiguous CPU tensor of shape {(T, m)}")
+            w[i].X = F.data_ptr()
+            w[i].L = Ls[i].data_ptr()
+            w[i].S = Ss[i].data_ptr()
+            if masks is not None and masks[i] is not None:
+                if masks[i].device.type != "cpu" or masks[i].numel() != m or masks[i].dtype != torch.uint8:
+                    raise ValueError(f"window {i}: mask must be a ({m},) uint8 CPU tensor")
+                w[i].mask = masks[i].data_ptr()
+            w[i].theta = float(thetas[i]) if thetas is not None else 0.0
+        res = (Result * self.n)()
+        st = self.lib.rpca_batch_solve_host(self.handle, w, _stream_handle(stream), res if wait else None)
+        if st < 0:
+            raise RpcaError(st, "rpca_batch_solve_host")
+        return [r.as_dict() for r in res] if wait else None
+
     def tune(self, frames, reps: int = 3, stream=None) -> float:
         """Autotune the CTA schedule on these windows; returns the best median ms per batch solve."""
         torch = _torch()
@@ -480,12 +522,18 @@ class Batch:
             raise RpcaError(st, "rpca_batch_tune")
         return best.value
 
+    def set_schedule(self, lanes: int, alpha: float = 1.0, ctas_per_sm: int = 1, paired: bool = True):
+        """Set the CTA schedule by hand (rpca_batch_set_schedule)."""
+        st = self.lib.rpca_batch_set_schedule(self.handle, int(lanes), float(alpha), int(ctas_per_sm), int(bool(paired)))
+        if st != OK:
+            raise RpcaError(st, "rpca_batch_set_schedule")
+
     def info(self) -> dict:
-        buf = (ctypes.c_int32 * 6)()
-        st = self.lib.rpca_batch_info(self.handle, buf, 6)
+        buf = (ctypes.c_int32 * 7)()
+        st = self.lib.rpca_batch_info(self.handle, buf, 7)
         if st != OK:
             raise RpcaError(st, "rpca_batch_info")
-        keys = ["grid", "lanes", "ctas_per_sm", "alpha_milli", "occ_max", "graph"]
+        keys = ["grid", "lanes", "ctas_per_sm", "alpha_milli", "occ_max", "graph", "paired"]
         out = dict(zip(keys, list(buf)))
         ctas = (ctypes.c_int32 * self.n)()
         if self.lib.rpca_batch_window_ctas(self.handle, ctas, self.n) == OK:

@@ -5,8 +5,7 @@ Gram Z^T Z (the SVD of Eq. 4 is taken through its eigen-decomposition) and
 through the residual and norm sums of the stopping test.  With the pixel rows
 of one window spread over the processes of a torch.distributed group, every
 process runs the fused pass over its own rows, the processes sum the Gram and
-the two scalar sums (one all-reduce of T*32 floats and 2 doubles per
-iteration), and every process runs the same eigen-step on the same sums, so
+the two scalar sums (one all-reduce of T*32 + 2 doubles per iteration), and every process runs the same eigen-step on the same sums, so
 all of them follow the iteration of the whole window and stop together.
 
 ``solve_sharded`` drives any engine with the step interface below;
@@ -40,13 +39,13 @@ class PlanSteps:
         lam = kw.pop("lambda_", None) or 1.0 / math.sqrt(max(int(m_total), int(T)))
         self.plan = rpca.Plan(m_local, T, sharded=1, lambda_=lam, **kw)
         self.lib = self.plan.lib
-        g, s = ctypes.POINTER(ctypes.c_float)(), ctypes.POINTER(ctypes.c_double)()
+        g, s = ctypes.POINTER(ctypes.c_double)(), ctypes.POINTER(ctypes.c_double)()
         st = self.lib.rpca_step_sums(self.plan.handle, ctypes.byref(g), ctypes.byref(s))
         if st != rpca.OK:
             raise rpca.RpcaError(st, "rpca_step_sums")
         gp = ctypes.cast(g, ctypes.c_void_p).value
         sp = ctypes.cast(s, ctypes.c_void_p).value
-        self._gram = torch.as_tensor(_DeviceArray(gp, (T, 32), "<f4"), device="cuda")
+        self._gram = torch.as_tensor(_DeviceArray(gp, (T, 32), "<f8"), device="cuda")
         self._sums = torch.as_tensor(_DeviceArray(sp, (2,), "<f8"), device="cuda")
         self.m, self.T = int(m_local), int(T)
 
@@ -65,7 +64,7 @@ class PlanSteps:
             raise rpca.RpcaError(st, "rpca_step_run")
 
     def sums(self):
-        """The buffers to sum across the processes: the Gram (T x 32 float32;
+        """The buffers to sum across the processes: the Gram (T x 32 float64;
         columns >= T unused) and (e2, l1) float64, both on the device."""
         return [self._gram, self._sums]
 

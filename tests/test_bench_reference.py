@@ -41,6 +41,9 @@ def test_reference_arm_prints_one_contract_line():
     assert d["config"]["workload"] == b.WORKLOAD_DESC
     assert d["steps"] == 1 and d["warmup"] == 3 and d["value"] > 0
     assert abs(d["ms_per_step"] - 1000.0 / d["value"]) <= 1e-9 * d["ms_per_step"]
+    # every timed step solved a whole window: the steps fit in the timed wall time
+    wall = float(d["cpu_baseline"]["sample"].rsplit("timed wall ", 1)[1].split()[0])
+    assert d["steps"] * d["ms_per_step"] <= 1e3 * wall + 100.0
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

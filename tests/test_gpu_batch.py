@@ -44,9 +44,11 @@ def windows(shapes, seed0=100):
     return out
 
 
-def run_batch(rp, wins, thetas=None, tune=False, **kw):
+def run_batch(rp, wins, thetas=None, tune=False, schedule=None, **kw):
     shapes = [(w.m, w.T) for w in wins]
     b = rp.Batch(shapes, **kw)
+    if schedule is not None:
+        b.set_schedule(**schedule)
     X = [torch.from_numpy(np.ascontiguousarray(w.frames, dtype=np.float32)).cuda() for w in wins]
     masks = [torch.zeros(w.m, dtype=torch.uint8, device="cuda") for w in wins] if thetas is not None else None
     if tune:
@@ -76,7 +78,8 @@ def test_batch_matches_single_solves_and_oracle(rp):
     refs = [O.rpca_frames(w.frames) for w in wins]
     thetas = [O.mask_threshold(O.temporal_mean_abs(r.L), w.bound_mask_gt) for r, w in zip(refs, wins)]
     got, info = run_batch(rp, wins, thetas=thetas)
-    assert info["grid"] >= len(wins) and info["lanes"] == len(wins)
+    # default schedule: lanes of two windows, run paired beside an eigen-step CTA
+    assert info["grid"] >= len(wins) and info["lanes"] == (len(wins) + 1) // 2 and info["paired"] == 1
     rows = []
     for w, r, g, th in zip(wins, refs, got, thetas):
         s = single(rp, w)
@@ -94,6 +97,38 @@ def test_batch_matches_single_solves_and_oracle(rp):
         mref = O.bound_mask(O.temporal_mean_abs(r.L), th)
         if mref.any():
             assert O.dice(g["mask"], mref) >= 0.999
+
+
+@pytest.mark.parametrize("lanes", [1, 2])
+def test_paired_lanes_refill_their_slots(rp, lanes):
+    # 9 windows on 1 or 2 paired lanes: each slot runs several windows one
+    # after the other, windows finish at different iterations (max_iter caps
+    # and sizes differ), so slots are refilled while the other slot's window
+    # is mid-solve; every result equals its single solve's within the FP32
+    # tolerance and the oracle's
+    shapes = [(64, 64, 20), (16, 16, 8), (40, 40, 7), (32, 48, 12), (8, 8, 3), (63, 64, 20), (16, 16, 32),
+              (20, 17, 13), (24, 24, 16)]
+    wins = windows(shapes, seed0=150)
+    params = [dict(max_iter=(5 if i % 3 == 1 else 500)) for i in range(len(wins))]
+    got, info = run_batch(rp, wins, params=params, schedule=dict(lanes=lanes, paired=True))
+    assert info["paired"] == 1 and info["lanes"] == lanes
+    for w, g, p in zip(wins, got, params):
+        s = single(rp, w, **p)
+        r = O.rpca_frames(w.frames, max_iter=p["max_iter"])
+        assert g["res"]["status"] == s["res"]["status"], (g["res"], s["res"])
+        assert abs(g["res"]["iters"] - s["res"]["iters"]) <= 1
+        assert rel(g["L"], s["L"]) <= FP32_TOL and rel(g["S"], s["S"]) <= FP32_TOL
+        assert rel(g["L"], r.L) <= FP32_TOL and rel(g["S"], r.S) <= FP32_TOL
+
+
+def test_paired_and_unpaired_schedules_agree(rp):
+    wins = windows(SHAPES[:6], seed0=170)
+    a, ia = run_batch(rp, wins, schedule=dict(lanes=3, paired=True))
+    b, ib = run_batch(rp, wins, schedule=dict(lanes=6, paired=False))
+    assert ia["paired"] == 1 and ib["paired"] == 0
+    for x, y in zip(a, b):
+        assert x["res"]["status"] == y["res"]["status"] == rp.OK
+        assert rel(x["L"], y["L"]) <= FP32_TOL and rel(x["S"], y["S"]) <= FP32_TOL
 
 
 def test_batch_is_deterministic(rp):

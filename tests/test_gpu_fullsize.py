@@ -1,0 +1,128 @@
+"""GPU parity at the sizes where the kernels' full control flow runs.
+
+The small-window tests elsewhere cover shapes, edge cases and drives; here the
+same comparison with the CPU FP64 oracle runs on windows large enough that
+
+  * the TMA-fed tensor-core pass (128-pixel tiles, one CTA per SM, a ring of
+    shared-memory stages) gives every CTA many tiles, so its stage ring wraps
+    and its TMEM accumulators are reused many times per pass;
+  * the tiled wide and complex passes stride over many tiles per CTA;
+
+and the tolerances are the stated ones: relative Frobenius error of L and S
+<= 1e-5 for FP32 and TF32x3, <= 1e-4 for BF16x3, bound-bubble mask Dice >=
+0.999 against the oracle's mask (one threshold applied to both sides).
+"""
+import functools
+
+import numpy as np
+import pytest
+
+from oracle import rpca_oracle as O
+from paper_2506_10257_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+TOL = {"FP32": 1e-5, "TF32X3": 1e-5, "BF16X3": 1e-4}
+
+
+@pytest.fixture(scope="module")
+def rp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_10257_gb300 import rpca
+    rpca.load()
+    return rpca
+
+
+def rel(a, b):
+    a = np.asarray(a, np.complex128 if np.iscomplexobj(a) else np.float64)
+    b = np.asarray(b, np.complex128 if np.iscomplexobj(b) else np.float64)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+@functools.lru_cache(maxsize=None)
+def window(ny, nx, T, seed, complex_iq=False, n_bound=400, n_free=800):
+    return synth.make_window(seed=seed, ny=ny, nx=nx, T=T, n_bound=n_bound, n_free=n_free, speed=(0.5, 5.0),
+                             complex_iq=complex_iq)
+
+
+@functools.lru_cache(maxsize=None)
+def oracle(ny, nx, T, seed, complex_iq=False, n_bound=400, n_free=800):
+    return O.rpca_frames(window(ny, nx, T, seed, complex_iq, n_bound, n_free).frames)
+
+
+def solve(rp, w, theta, **kw):
+    X = torch.from_numpy(np.ascontiguousarray(w.frames)).cuda()
+    T, m = X.shape
+    if X.dtype == torch.complex64:
+        kw.setdefault("dtype", rp.C64)
+    plan = rp.Plan(m, T, **kw)
+    mask = torch.zeros(m, dtype=torch.uint8, device="cuda")
+    L, S, res = plan.solve(X, mask=mask, theta=theta)
+    torch.cuda.synchronize()
+    plan.close()
+    return L.cpu().numpy(), S.cpu().numpy(), mask.cpu().numpy().astype(bool), res
+
+
+def check(rp, key, prec="FP32", **kw):
+    w = window(*key)
+    ref = oracle(*key)
+    img = O.temporal_mean_abs(ref.L)
+    theta = O.mask_threshold(img, w.bound_mask_gt)
+    L, S, mask, res = solve(rp, w, theta, precision=getattr(rp, "PREC_" + prec), **kw)
+    assert res["status"] == rp.OK, res
+    eL, eS = rel(L, ref.L), rel(S, ref.S)
+    assert eL <= TOL[prec] and eS <= TOL[prec], (prec, eL, eS, res["iters"], ref.iters)
+    if prec != "BF16X3":
+        # BF16x3 products carry errors near 1e-6 of the operands, so its
+        # residual approaches the 1e-7 stopping tolerance more slowly than the
+        # FP64 iteration's (measured: 39 iterations against 32 on these
+        # windows); its bar is the error of L and S and the mask, above
+        assert abs(res["iters"] - ref.iters) <= 1, (res["iters"], ref.iters)
+    assert O.dice(mask, O.bound_mask(img, theta)) >= 0.999
+    return res
+
+
+@pytest.mark.parametrize("prec", ["TF32X3", "BF16X3"])
+def test_tensor_core_512x512x20(rp, prec):
+    # the benchmark's window shape, 2048 tiles of 128 pixels on one CTA per SM
+    check(rp, (512, 512, 20, 1), prec)
+
+
+@pytest.mark.parametrize("prec", ["TF32X3", "BF16X3"])
+def test_tensor_core_768x512x20_ring_wraps(rp, prec):
+    # 393216 pixels = 3072 tiles: about 20 tiles per CTA, so each CTA's stage
+    # ring (2-4 stages) wraps several times and both warpgroups reuse their
+    # TMEM columns many times per pass
+    check(rp, (768, 512, 20, 2, False, 600, 1200), prec)
+
+
+def test_tensor_core_tf32x3_odd_pixel_count(rp):
+    # m % 4 != 0 takes the tensor-core pass without TMA (256-pixel tiles)
+    check(rp, (509, 515, 20, 3), "TF32X3")
+
+
+def test_plain_tf32_is_not_offered(rp):
+    # one TF32 product per contraction misses the 1e-4 bound (7.1e-4 measured
+    # on the 262144 x 20 window), so plans reject it
+    with pytest.raises(rp.RpcaError) as e:
+        rp.Plan(4096, 20, precision=rp.PREC_TF32)
+    assert e.value.status == rp.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("T", [50, 100])
+def test_wide_256x256_matches_oracle(rp, T):
+    check(rp, (256, 256, T, 10 + T))
+
+
+def test_complex_256x256x50_matches_oracle(rp):
+    check(rp, (256, 256, 50, 77, True))
+
+
+@pytest.mark.parametrize("T", [50, 100])
+def test_wide_512x512_matches_oracle(rp, T):
+    # the paper-scale windows of the frame sweep, in the launch shape the
+    # benchmark's plan form uses
+    check(rp, (512, 512, T, 5))

@@ -207,12 +207,12 @@ def test_stream_drive_equals_graph_drive(rp):
     assert np.array_equal(a["L"], b["L"]) and np.array_equal(a["S"], b["S"])
 
 
-# ---- tensor-core contractions (TF32x3, BF16x3, TF32) ---------------------------
+# ---- tensor-core contractions (TF32x3, BF16x3) -----------------------------------
 
-PREC_TOL = {"TF32X3": 1e-5, "BF16X3": 1e-4, "TF32": 1e-2}
+PREC_TOL = {"TF32X3": 1e-5, "BF16X3": 1e-4}
 
 
-@pytest.mark.parametrize("prec", ["TF32X3", "BF16X3", "TF32"])
+@pytest.mark.parametrize("prec", ["TF32X3", "BF16X3"])
 @pytest.mark.parametrize("ny,nx,T", [(64, 64, 20), (63, 64, 20), (20, 17, 7), (16, 16, 32), (40, 40, 13)])
 def test_tensor_core_precisions(rp, prec, ny, nx, T):
     w = synth.make_window(seed=ny * nx + 3 * T, ny=ny, nx=nx, T=T, n_bound=6, n_free=10)

@@ -53,7 +53,7 @@ def test_one_process_steps_equal_the_plan(rp):
 def test_step_api_rejects_a_plan_without_sharding(rp):
     import ctypes
     plan = rp.Plan(256, 8)
-    g, s = ctypes.POINTER(ctypes.c_float)(), ctypes.POINTER(ctypes.c_double)()
+    g, s = ctypes.POINTER(ctypes.c_double)(), ctypes.POINTER(ctypes.c_double)()
     assert plan.lib.rpca_step_sums(plan.handle, ctypes.byref(g), ctypes.byref(s)) == rp.ERR_ARG
     assert plan.lib.rpca_step_run(plan.handle, 2, None) == rp.ERR_ARG
     plan.close()

@@ -139,15 +139,3 @@ def test_wide_served(rp):
     sv.close()
     ref = O.rpca_frames(F)
     assert st == rp.OK and rel(L.cpu().numpy(), ref.L) <= FP32_TOL
-
-
-@pytest.mark.slow
-@pytest.mark.parametrize("T", [50, 100])
-def test_wide_full_size_sampled(rp, T):
-    # 262144 x T: the residual and the invariants at full size (the oracle's SVD
-    # at this size is left to the bench's bounded sample)
-    w = synth.make_preset(f"w512x512_t{T}", seed=5)
-    L, S, res = gpu_solve(rp, w.frames)
-    assert res["status"] == rp.OK and res["resid"] <= 1e-7
-    X = w.frames.astype(np.float64)
-    assert rel(X - L - S, np.zeros(1)) / np.linalg.norm(X) <= 2e-7

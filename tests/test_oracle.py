@@ -244,6 +244,24 @@ def test_rmse_and_dice_hand_values():
     np.testing.assert_array_equal(O.bound_mask(img, th), [False, True, False, True])
 
 
+def test_temporal_mean_abs_hand_values():
+    # the image that is binarised (Sec. II-F): per pixel, the mean over frames
+    # of the magnitude.  Input (T, m) frame rows, output one value per pixel.
+    # Signs cancel in a mean of values (pixel 0 would give 1), not in a mean
+    # of magnitudes; a mean over pixels instead of frames gives 3 values.
+    real = np.array([[1.0, -2.0], [-3.0, 4.0], [5.0, 0.0]])
+    img = O.temporal_mean_abs(real)
+    assert img.shape == (2,)
+    np.testing.assert_array_equal(img, [3.0, 2.0])
+    # complex IQ entries count with their modulus: |3+4i| = 5, |-6-8i| = 10
+    cplx = np.array([[3 + 4j, 1j], [-6 - 8j, 0.0]])
+    img = O.temporal_mean_abs(cplx)
+    assert img.shape == (2,) and img.dtype == np.float64
+    np.testing.assert_array_equal(img, [7.5, 0.5])
+    # one frame: the magnitudes themselves
+    np.testing.assert_array_equal(O.temporal_mean_abs(np.array([[-2.5, 0.0, 7.0]])), [2.5, 0.0, 7.0])
+
+
 def test_warm_start_from_converged_state_is_a_fixed_point():
     # The ALM iteration is at a fixed point at its own converged (S, Y, mu): one
     # more iteration from there meets the stopping test at once and returns the

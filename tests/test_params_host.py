@@ -26,7 +26,8 @@ REJECTED = [
     (dict(warm_start=2), ARG), (dict(sharded=2), ARG),
     (dict(sharded=1, dtype=C64), UNSUP), (dict(sharded=1, T=rpca.MAX_T_NARROW + 1), UNSUP),
     (dict(sharded=1, precision=TF32), UNSUP), (dict(sharded=1, mu_schedule=FIXED_L1), UNSUP),
-    (dict(sharded=1, warm_start=1), UNSUP),
+    (dict(sharded=1, warm_start=1), UNSUP), (dict(precision=TF32), UNSUP),
+    (dict(drive=rpca.DRIVE_STREAM, precision=TF32), UNSUP),
     (dict(mu_init=-1.0), ARG), (dict(mu_init=math.inf), ARG), (dict(mu_prev_scale=float("nan")), ARG),
 ]
 
@@ -34,7 +35,7 @@ REJECTED = [
 ACCEPTED = [
     dict(), dict(T=1), dict(T=rpca.MAX_T), dict(dtype=C64, T=rpca.MAX_T // 2), dict(precision=BF16X3, T=32),
     dict(mu_schedule=FIXED_L1, rho=0.5),                      # rho, mu0_scale, cap only bind the IALM schedule
-    dict(sharded=1), dict(warm_start=1, mu_prev_scale=0.1), dict(drive=rpca.DRIVE_STREAM, precision=TF32),
+    dict(sharded=1), dict(warm_start=1, mu_prev_scale=0.1), dict(drive=rpca.DRIVE_STREAM, precision=TF32X3),
 ]
 
 
