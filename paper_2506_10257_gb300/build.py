@@ -15,7 +15,8 @@ CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "librpca.so")
 GENCODE = "arch=compute_103a,code=sm_103a"
-UNITS = ["rpca_batch_wide.cu", "rpca_wide.cu", "rpca_capi.cu", "rpca_batch.cu", "rpca_server.cu", "rpca_noalloc.cu", "rpca_prefilter.cu"]
+UNITS = ["rpca_batch_wide.cu", "rpca_batch_tc.cu", "rpca_wide.cu", "rpca_capi.cu", "rpca_batch.cu", "rpca_server.cu",
+         "rpca_noalloc.cu", "rpca_prefilter.cu"]
 
 
 def _sources():

@@ -32,6 +32,8 @@ namespace rpca {
 
 // The wide / complex batch kernel (rpca_batch_wide.cu).
 void* batch_wide_kernel_fn(bool cplx);
+// The tensor-core batch kernel for windows of <= tbmax frames (rpca_batch_tc.cu).
+void batch_tc_kernel_info(int tbmax, bool bf16, void** fn, size_t* smem);
 }  // namespace rpca
 
 using namespace rpca;
@@ -70,7 +72,6 @@ struct KernelInfo {
 int wide_cw(int Tr) { return (Tr + 31) / 32 * 32 / 8; }
 
 KernelInfo batch_kernel_for(int tbmax) {
-  if (tbmax <= 16) return {(void*)batch_kernel<16>, batch_smem<16>()};
   if (tbmax <= 20) return {(void*)batch_kernel<20>, batch_smem<20>()};
   return {(void*)batch_kernel<32>, batch_smem<32>()};
 }
@@ -367,12 +368,16 @@ rpca_status rpca_batch_create(const rpca_params* params, int32_t n, rpca_batch_t
   *out = nullptr;
   if (n > kMaxBatch) return RPCA_ERR_UNSUPPORTED;
   bool wide = false;
+  const int prec = params[0].precision;
   for (int i = 0; i < n; ++i) {
-    if (params[i].precision != RPCA_PREC_FP32) return RPCA_ERR_UNSUPPORTED;
+    if (params[i].precision != prec) return RPCA_ERR_UNSUPPORTED;  // one precision per batch
     if (params[i].warm_start) return RPCA_ERR_UNSUPPORTED;        // windows of a batch start cold
     if (params[i].dtype != params[0].dtype) return RPCA_ERR_UNSUPPORTED;  // one element type per batch
     if (params[i].T > kMaxT || params[i].dtype == RPCA_C64) wide = true;
   }
+  if (prec != RPCA_PREC_FP32 && prec != RPCA_PREC_TF32X3 && prec != RPCA_PREC_BF16X3) return RPCA_ERR_UNSUPPORTED;
+  // tensor-core batches: real windows of <= 32 frames (the narrow tensor-core pass)
+  if (prec != RPCA_PREC_FP32 && wide) return RPCA_ERR_UNSUPPORTED;
   rpca_batch_s* b = new rpca_batch_s();
   b->n = n;
   b->p.assign(params, params + n);
@@ -389,7 +394,10 @@ rpca_status rpca_batch_create(const rpca_params* params, int32_t n, rpca_batch_t
   if (!wide) {
     int tbmax = 8;
     for (int i = 0; i < n; ++i) tbmax = std::max(tbmax, bucket_tb(params[i].T));
-    b->kern = batch_kernel_for(tbmax);
+    if (prec == RPCA_PREC_FP32)
+      b->kern = batch_kernel_for(tbmax);
+    else
+      batch_tc_kernel_info(tbmax, prec == RPCA_PREC_BF16X3, &b->kern.fn, &b->kern.smem);
   } else {
     // shared memory: the largest tiled pass or eigen-step of the batch, with
     // as many staged V rows (<= 16) as the SM leaves room for

@@ -39,7 +39,7 @@ struct LaneDesc {
 struct BatchDesc {
   int nwin;
   int nlanes;
-  int paired;                      // lanes of >= 2 windows and >= 3 CTAs run run_lane_paired
+  int paired;                      // lanes of >= 2 windows and >= 3 CTAs run them two at a time (run_lane)
   unsigned long long spin_limit;   // polls of a publication wait before it gives up
   unsigned int stop;               // set once any wait ran out: every later wait gives up at once
   int vrows;                       // wide eigen-steps: rows of V staged per step
@@ -127,17 +127,22 @@ __device__ __forceinline__ void window_fail(Bufs b) {
 
 // Steps of one window kind: the narrow (register-resident) pass and eigen-step
 // for T <= kMaxT frames, or the tiled ones (wide or complex windows).
+// The eigen-step runs once per iteration and is called, not inlined, which
+// keeps the batch kernels' build short; the passes stay inlined.
+template <int TB>
+__device__ __noinline__ void narrow_eig_call(Bufs b, int flags, unsigned char* dsm) {
+  if (b.eig64)
+    eig64_body<TB>(b, flags, 0, 0, dsm);
+  else
+    eig_fast_body<TB, float>(b, flags, 0, 0, dsm);
+}
+
 template <int TB>
 struct NarrowBody {
   static __device__ bool pass(Bufs b, bool init, int lc, int nc, unsigned char* dsm) {
     return init ? pass_body<TB, PM_INIT>(b, lc, nc, dsm) : pass_body<TB, PM_FUSED>(b, lc, nc, dsm);
   }
-  static __device__ void eig(Bufs b, int flags, unsigned char* dsm, int) {
-    if (b.eig64)
-      eig64_body<TB>(b, flags, 0, 0, dsm);
-    else
-      eig_fast_body<TB, float>(b, flags, 0, 0, dsm);
-  }
+  static __device__ void eig(Bufs b, int flags, unsigned char* dsm, int) { narrow_eig_call<TB>(b, flags, dsm); }
 };
 
 // The window's state reset before its solve (the lane's CTA 0, thread 0).
@@ -172,42 +177,6 @@ __device__ __forceinline__ void reset_window(WinDesc& wd) {
   for (int g = 0; g <= kMaxGroups; ++g) b.red->cnt[g] = 0u;
 }
 
-template <class Body>
-__device__ void run_window(WinDesc& wd, int lc, unsigned char* dsm, unsigned long long limit, unsigned int* stop,
-                           int vrows) {
-  const Bufs b = wd.b;
-  const int nc = b.grid;
-  if (lc >= nc) return;  // the window uses fewer CTAs than its lane has
-  unsigned int* gen = &wd.gen;
-  // ---- the window's first CTA resets its state, then everyone starts ----
-  if (lc == 0) {
-    if (threadIdx.x == 0) reset_window(wd);
-    gen_publish(gen);
-  }
-  if (!gen_wait(gen, 1u, limit, stop)) {
-    window_fail(b);
-    return;
-  }
-  // ---- init pass + first eigen-step, then the iterations ----
-  int flags = EF_INIT | EF_EIG;
-  const int max_iter = __ldcg(&b.ctrl->max_iter);
-  for (int it = 0; it <= max_iter + 1; ++it) {
-    const bool fin = Body::pass(b, it == 0, lc, nc, dsm);
-    if (fin) {
-      __syncthreads();
-      Body::eig(b, flags, dsm, vrows);
-      gen_publish(gen);
-    }
-    if (!gen_wait(gen, 2u + (unsigned)it, limit, stop)) {
-      window_fail(b);
-      return;
-    }
-    flags = EF_CHECK | EF_EIG;
-    if (solve_done_uniform(b.ctrl)) break;
-  }
-  final_body(b, lc, nc);
-}
-
 // Wait until *ctr reaches target (thread 0 polls, bounded, with back-off);
 // false if the wait ran out (or another wait of the launch did).
 __device__ __forceinline__ bool ctr_wait(const unsigned int* ctr, unsigned int target, unsigned long long limit,
@@ -232,32 +201,39 @@ __host__ __device__ inline bool lane_is_paired(int paired, const LaneDesc& ld) {
   return paired && ld.w1 - ld.w0 >= 2 && ld.ncta >= 3;
 }
 
-// A lane whose windows run two at a time, with its last CTA as the lane's
-// eigen-step CTA.  The lane's windows alternate between two slots (slot s
-// starts with window w0 + s; a slot whose window has finished takes the
-// lane's next unstarted window).  The other CTAs (the pass CTAs) run slot 0's
-// pass, then slot 1's, then slot 0's next, ...; the CTA completing a pass's
-// reduction bumps the window's pass counter and goes on at once.  The
-// eigen-step CTA takes the slots in the same order: it waits for the slot's
-// pass, runs its eigen-step and publishes it.  So one window's latency-bound
-// eigen-step (one SM) runs while the pass CTAs stream the other window's
-// pixels, and a pass waits only when an eigen-step takes longer than the other
-// slot's pass.  Both sides see the same sequence of windows and iterations
-// (the eigen-step's done flag decides it), so every wait has a matching
-// publication; all waits are bounded, and a window whose wait ran out is
-// marked failed and its slot moves on.
-// Disp::pass(wd, init, lc, nc, dsm) and Disp::eig(wd, flags, dsm, vrows) run
-// the window's steps for its frame bucket.
+// The windows of one lane.
+//
+// Sequential lane (paired = false): the lane's CTAs run its windows one after
+// the other; per iteration every CTA runs its share of the window's pass, the
+// CTA that completes the pass's reduction runs the eigen-step at once and
+// publishes it, and the others wait for the publication.
+//
+// Paired lane: its windows run two at a time and its last CTA runs every
+// eigen-step.  The windows alternate between two slots (slot s starts with
+// window w0 + s; a slot whose window has finished takes the lane's next
+// unstarted window).  The other CTAs (the pass CTAs) run slot 0's pass, then
+// slot 1's, then slot 0's next, ...; the CTA completing a pass's reduction
+// bumps the window's pass counter and goes on at once.  The eigen-step CTA
+// takes the slots in the same order: it waits for the slot's pass, runs its
+// eigen-step and publishes it.  So one window's latency-bound eigen-step (one
+// SM) runs while the pass CTAs stream the other window's pixels, and a pass
+// waits only when an eigen-step takes longer than the other slot's pass.
+//
+// Both sides see the same sequence of windows and iterations (the eigen-step's
+// done flag decides it), so every wait has a matching publication; all waits
+// are bounded, and a window whose wait ran out is marked failed and its slot
+// moves on.  Disp::pass(wd, init, lc, nc, dsm) and Disp::eig(wd, flags, dsm,
+// vrows) run the window's steps for its frame bucket.
 template <class Disp>
-__device__ void run_lane_paired(BatchDesc* bd, const LaneDesc& ld, int lc, unsigned char* dsm,
-                                unsigned long long limit, unsigned int* stop, int vrows) {
-  const int np = ld.ncta - 1;          // pass CTAs; lane CTA np runs the eigen-steps
-  const bool eigc = (lc == np);
+__device__ void run_lane(BatchDesc* bd, const LaneDesc& ld, int lc, unsigned char* dsm, unsigned long long limit,
+                         unsigned int* stop, int vrows, bool paired) {
+  const int np = paired ? ld.ncta - 1 : ld.ncta;  // pass CTAs; in a paired lane CTA np runs the eigen-steps
+  const bool eigc = paired && (lc == np);
   int w[2], it[2];
   w[0] = ld.w0;
-  w[1] = (ld.w0 + 1 < ld.w1) ? ld.w0 + 1 : -1;
+  w[1] = (paired && ld.w0 + 1 < ld.w1) ? ld.w0 + 1 : -1;
   it[0] = it[1] = 0;
-  int nxt = ld.w0 + 2;  // next window of the lane to start
+  int nxt = ld.w0 + (paired ? 2 : 1);  // next window of the lane to start
   auto advance = [&](int s) {
     w[s] = (nxt < ld.w1) ? nxt++ : -1;
     it[s] = 0;
@@ -307,9 +283,14 @@ __device__ void run_lane_paired(BatchDesc* bd, const LaneDesc& ld, int lc, unsig
         const bool fin = Disp::pass(wd, it[s] == 0, lc, b.grid, dsm);
         if (fin) {
           __syncthreads();
-          if (threadIdx.x == 0) {
-            __threadfence();
-            atomicAdd(&wd.pdone, 1u);
+          if (paired) {
+            if (threadIdx.x == 0) {
+              __threadfence();
+              atomicAdd(&wd.pdone, 1u);
+            }
+          } else {
+            Disp::eig(wd, it[s] == 0 ? (EF_INIT | EF_EIG) : (EF_CHECK | EF_EIG), dsm, vrows);
+            gen_publish(&wd.gen);
           }
         }
       }
@@ -360,21 +341,5 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchDesc* bd) 
   const int lc = (int)blockIdx.x - ld.cta0;
   if (lc < 0 || lc >= ld.ncta) return;
   const unsigned long long limit = bd->spin_limit;
-  if (lane_is_paired(bd->paired, ld)) {
-    run_lane_paired<NarrowDisp<TBMAX>>(bd, ld, lc, batch_dsm, limit, &bd->stop, 0);
-    return;
-  }
-  for (int w = ld.w0; w < ld.w1; ++w) {
-    WinDesc& wd = bd->w[w];
-    switch (wd.TB) {
-      case 8: run_window<NarrowBody<8>>(wd, lc, batch_dsm, limit, &bd->stop, 0); break;
-      case 12: if constexpr (TBMAX >= 12) run_window<NarrowBody<12>>(wd, lc, batch_dsm, limit, &bd->stop, 0); break;
-      case 16: if constexpr (TBMAX >= 16) run_window<NarrowBody<16>>(wd, lc, batch_dsm, limit, &bd->stop, 0); break;
-      case 20: if constexpr (TBMAX >= 20) run_window<NarrowBody<20>>(wd, lc, batch_dsm, limit, &bd->stop, 0); break;
-      case 24: if constexpr (TBMAX >= 24) run_window<NarrowBody<24>>(wd, lc, batch_dsm, limit, &bd->stop, 0); break;
-      case 32: if constexpr (TBMAX >= 32) run_window<NarrowBody<32>>(wd, lc, batch_dsm, limit, &bd->stop, 0); break;
-      default: break;
-    }
-    __syncthreads();
-  }
+  run_lane<NarrowDisp<TBMAX>>(bd, ld, lc, batch_dsm, limit, &bd->stop, 0, lane_is_paired(bd->paired, ld));
 }

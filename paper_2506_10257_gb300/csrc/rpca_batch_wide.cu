@@ -67,24 +67,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel_wide(BatchDesc*
   if (lc < 0 || lc >= ld.ncta) return;
   const unsigned long long limit = bd->spin_limit;
   const int vrows = bd->vrows;
-  if (lane_is_paired(bd->paired, ld)) {
-    run_lane_paired<WideDisp<CPLX>>(bd, ld, lc, batch_dsm, limit, &bd->stop, vrows);
-    return;
-  }
-  for (int w = ld.w0; w < ld.w1; ++w) {
-    WinDesc& wd = bd->w[w];
-    switch (wd.TB) {
-      case 4: run_window<WideBody<4, CPLX>>(wd, lc, batch_dsm, limit, &bd->stop, vrows); break;
-      case 8: run_window<WideBody<8, CPLX>>(wd, lc, batch_dsm, limit, &bd->stop, vrows); break;
-      case 12: run_window<WideBody<12, CPLX>>(wd, lc, batch_dsm, limit, &bd->stop, vrows); break;
-      case 16: run_window<WideBody<16, CPLX>>(wd, lc, batch_dsm, limit, &bd->stop, vrows); break;
-      case 20: run_window<WideBody<20, CPLX>>(wd, lc, batch_dsm, limit, &bd->stop, vrows); break;
-      case 24: run_window<WideBody<24, CPLX>>(wd, lc, batch_dsm, limit, &bd->stop, vrows); break;
-      case 28: run_window<WideBody<28, CPLX>>(wd, lc, batch_dsm, limit, &bd->stop, vrows); break;
-      default: break;
-    }
-    __syncthreads();
-  }
+  run_lane<WideDisp<CPLX>>(bd, ld, lc, batch_dsm, limit, &bd->stop, vrows, lane_is_paired(bd->paired, ld));
 }
 
 void* batch_wide_kernel_fn(bool cplx) {

@@ -50,14 +50,18 @@ __host__ __device__ constexpr size_t pass_tc_smem() {
 
 constexpr uint32_t kTcWaitLimit = 1u << 21;  // tries (each may suspend ~1 us) before a wait gives up
 
+// The fused pass with tensor-core contractions over the tiles of this CTA
+// (number lc of nc), on kPassThreads threads.  `tc_smem` holds
+// pass_tc_smem<TB, KP, BF16>() bytes (128-byte aligned); `tmem` is a TMEM
+// allocation of TcShape<KP, BF16>::TMEM_COLS columns owned by the CTA.
+// Returns true in the CTA that wrote the final reduced sums (b.finalize).
 template <int TB, int KP, bool BF16, bool SPLIT>
-__global__ void __launch_bounds__(kPassThreads, 1) pass_tc_kernel(Bufs b) {
+__device__ bool pass_tc_body(Bufs b, int lc, int nc, unsigned char* tc_smem, uint32_t tmem) {
   using SH = TcShape<KP, BF16>;
   using GM = GramMap<TB>;
   constexpr int ZS = TB + 4;
   static_assert(TB <= KP, "frames exceed the MMA width");
   static_assert(pass_tc_aregion<TB, KP, BF16>() >= (size_t)GM::NGRP * GM::NBLK * 16 * sizeof(float), "scratch");
-  extern __shared__ __align__(128) unsigned char tc_smem[];
   unsigned char* sWh = tc_smem;
   unsigned char* sWl = sWh + SH::B_BYTES;
   unsigned char* sVh = sWl + SH::B_BYTES;
@@ -68,10 +72,9 @@ __global__ void __launch_bounds__(kPassThreads, 1) pass_tc_kernel(Bufs b) {
   __shared__ double sScal[2 * kMaxGroups];
   __shared__ int sLast;
   __shared__ __align__(8) uint64_t sMbar;
-  __shared__ uint32_t sTmem;
 
   const Ctrl* ctrl = b.ctrl;
-  if (ctrl->done) return;
+  if (solve_done_uniform(ctrl)) return false;
   const int tid = threadIdx.x, warp = tid >> 5;
   if (tid == 0) atomicMin(&b.red->t_start, gtimer());
   const int T = b.T;
@@ -99,12 +102,10 @@ __global__ void __launch_bounds__(kPassThreads, 1) pass_tc_kernel(Bufs b) {
     tc_store4<BF16>(sWh, sWl, o, w[0], w[1], w[2], w[3], SPLIT);
     tc_store4<BF16>(sVh, sVl, o, v[0], v[1], v[2], v[3], SPLIT);
   }
-  if (warp == 0) tmem_alloc(&sTmem, SH::TMEM_COLS);
   if (tid == 0) mbar_init(&sMbar, 1);
   fence_async_smem();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = sTmem;
   const int sub = tid >> 7;            // which 128-row tile of the 256-pixel tile
   const int row = tid & 127;           // M row = TMEM lane
   unsigned char* myAh = sA + (size_t)(2 * sub) * SH::A_BYTES;
@@ -147,7 +148,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) pass_tc_kernel(Bufs b) {
   };
 
   const int64_t ntiles = (m + kTile - 1) / kTile;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (int64_t tile = lc; tile < ntiles; tile += nc) {
     const int64_t p = tile * kTile + tid;
     const bool valid = p < m;
     float x[TB], s[TB], d[TB], z[KP];
@@ -219,6 +220,21 @@ __global__ void __launch_bounds__(kPassThreads, 1) pass_tc_kernel(Bufs b) {
   if (!ok) atomicExch(&b.red->err, 1);
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, SH::TMEM_COLS);
-  pass_epilogue<TB, true>(b, acc, e2, 0.f, sZ, sRed, sScal, &sLast, gthr, ggrp, gblk, blockIdx.x, gridDim.x);
+  return pass_epilogue<TB, true>(b, acc, e2, 0.f, sZ, sRed, sScal, &sLast, gthr, ggrp, gblk, lc, nc);
+}
+
+template <int TB, int KP, bool BF16, bool SPLIT>
+__global__ void __launch_bounds__(kPassThreads, 1) pass_tc_kernel(Bufs b) {
+  using SH = TcShape<KP, BF16>;
+  extern __shared__ __align__(128) unsigned char tc_smem_k[];
+  __shared__ uint32_t sTmem;
+  if (solve_done_uniform(b.ctrl)) return;
+  if ((threadIdx.x >> 5) == 0) tmem_alloc(&sTmem, SH::TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  pass_tc_body<TB, KP, BF16, SPLIT>(b, blockIdx.x, gridDim.x, tc_smem_k, sTmem);
+  tc_fence_before();
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0) tmem_dealloc(sTmem, SH::TMEM_COLS);
 }

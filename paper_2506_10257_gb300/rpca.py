@@ -548,7 +548,7 @@ class Server:
     STATS = ["bytes", "peak_bytes", "budget", "queued", "running", "peak_running", "started", "finished",
              "evicted", "refused"]
 
-    def __init__(self, hbm_budget_bytes: int = 120 * 10**9, max_slots: int = 8, warm: bool = True,
+    def __init__(self, hbm_budget_bytes: int = 120 * 10**9, max_slots: int = 8, warm: bool = False,
                  warm_mu_scale: float = 0.1, cold_every: int = 0):
         _torch()
         self.lib = load()

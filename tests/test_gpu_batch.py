@@ -173,7 +173,9 @@ def test_batch_per_window_parameters(rp):
 
 def test_batch_rejects_unsupported(rp):
     with pytest.raises(rp.RpcaError):
-        rp.Batch([(4096, 20)], precision=rp.PREC_BF16X3)
+        rp.Batch([(4096, 20)], precision=rp.PREC_TF32)
+    with pytest.raises(rp.RpcaError):
+        rp.Batch([(4096, 20), (4096, 20)], params=[dict(), dict(precision=rp.PREC_BF16X3)])
     with pytest.raises(ValueError):
         rp.Batch([])
 
@@ -223,3 +225,40 @@ def test_batch_of_complex_windows(rp):
 def test_batch_rejects_mixed_element_types(rp):
     with pytest.raises(rp.RpcaError):
         rp.Batch([(256, 8), (256, 8)], params=[dict(), dict(dtype=rp.C64)])
+
+
+@pytest.mark.parametrize("prec", ["TF32X3", "BF16X3"])
+@pytest.mark.parametrize("paired", [True, False])
+def test_tensor_core_batch_matches_oracle(rp, prec, paired):
+    # the mixed-precision batched form: every window's two contractions on the
+    # tensor cores inside the persistent launch; each window against the FP64
+    # oracle at the precision's tolerance and against its single solve
+    tol = {"TF32X3": 1e-5, "BF16X3": 1e-4}[prec]
+    wins = windows([(64, 64, 20), (32, 48, 12), (63, 64, 20), (16, 16, 32), (40, 40, 7), (20, 17, 13)], seed0=800)
+    lanes = 3 if paired else 6
+    got, info = run_batch(rp, wins, precision=getattr(rp, "PREC_" + prec), schedule=dict(lanes=lanes, paired=paired))
+    assert info["paired"] == int(paired)
+    for w, g in zip(wins, got):
+        assert g["res"]["status"] == rp.OK, g["res"]
+        r = O.rpca_frames(w.frames)
+        eL, eS = rel(g["L"], r.L), rel(g["S"], r.S)
+        assert eL <= tol and eS <= tol, (prec, w.m, w.T, eL, eS)
+        s = single(rp, w, precision=getattr(rp, "PREC_" + prec))
+        assert rel(g["L"], s["L"]) <= tol and rel(g["S"], s["S"]) <= tol
+
+
+@pytest.mark.slow
+def test_tensor_core_batch_full_size(rp):
+    # 4 windows of 512 x 512 x 20 in TF32x3: many tiles per CTA in every pass
+    wins = [synth.make_preset("w512x512_t20", seed=900 + i) for i in range(4)]
+    got, info = run_batch(rp, wins, precision=rp.PREC_TF32X3)
+    for w, g in zip(wins[:2], got[:2]):
+        r = O.rpca_frames(w.frames)
+        assert g["res"]["status"] == rp.OK
+        assert rel(g["L"], r.L) <= 1e-5 and rel(g["S"], r.S) <= 1e-5
+
+
+def test_tensor_core_batch_rejects_wide_windows(rp):
+    with pytest.raises(rp.RpcaError) as e:
+        rp.Batch([(4096, 20), (4096, 40)], precision=rp.PREC_TF32X3)
+    assert e.value.status == rp.ERR_UNSUPPORTED

@@ -117,6 +117,7 @@ PROBES = [(41, 32, 32, 20), (42, 48, 40, 20), (43, 16, 64, 12)]   # (seed, ny, n
 
 
 def serve(rp, probes_windows, slots, warm=True, mu_scale=0.1, order="interleave"):
+    # (warm starts are opt-in on a server; these tests exercise them explicitly)
     sv = rp.Server(hbm_budget_bytes=10**9, max_slots=slots, warm=warm, warm_mu_scale=mu_scale)
     ids = {}
     n = max(len(w) for w in probes_windows.values())
@@ -192,6 +193,38 @@ def test_served_cold_policy_matches_cold_oracle(rp):
         ref = O.rpca_frames(F)
         st, res, L, S = got[(5, k)]
         assert rel(L, ref.L) <= FP32_TOL and rel(S, ref.S) <= FP32_TOL
+
+
+@pytest.mark.slow
+def test_served_default_chain_of_100_windows_matches_cold_oracle(rp):
+    # the served form's default policy (cold starts) along one probe's chain of
+    # 100 sliding 20-frame windows, two probes interleaved: every window's L
+    # and S within the FP32 tolerance of the cold FP64 oracle and its
+    # bound-bubble mask at Dice >= 0.999 (theta from the oracle's image)
+    s, ny, nx, T = PROBES[0]
+    wins, w = stream(s, ny, nx, T, 100)
+    other, _ = stream(PROBES[1][0], PROBES[1][1], PROBES[1][2], PROBES[1][3], 30)
+    sv = rp.Server(hbm_budget_bytes=10**9, max_slots=4)
+    ids = []
+    for k, F in enumerate(wins):
+        ids.append(sv.submit(cuda(F), key=0))
+        if k < len(other):
+            sv.submit(cuda(other[k]), key=1)
+    worst = (1.0, 0.0)
+    for k, F in enumerate(wins):
+        st, res = sv.wait(ids[k])
+        L, S, _ = sv.outputs(ids[k])
+        L, S = L.cpu().numpy(), S.cpu().numpy()
+        ref = O.rpca_frames(F)
+        assert st == rp.OK
+        eL, eS = rel(L, ref.L), rel(S, ref.S)
+        assert eL <= FP32_TOL and eS <= FP32_TOL, (k, eL, eS)
+        img = O.temporal_mean_abs(ref.L)
+        th = O.mask_threshold(img, w.bound_mask_gt)
+        d = O.dice(O.bound_mask(O.temporal_mean_abs(L), th), O.bound_mask(img, th))
+        worst = (min(worst[0], d), max(worst[1], eL))
+        assert d >= 0.999, (k, d)
+    sv.close()
 
 
 def test_admission_by_budget(rp):
