@@ -365,7 +365,8 @@ def run_batch(args):
     thetas = [_theta(w) for w in ws]
     masks = [torch.zeros(m, dtype=torch.uint8, device="cuda") for _ in ws]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    batch = rpca.Batch([(m, T)] * NB)
+    prec = {"fp32": rpca.PREC_FP32, "tf32x3": rpca.PREC_TF32X3, "bf16x3": rpca.PREC_BF16X3}[args.precision]
+    batch = rpca.Batch([(m, T)] * NB, precision=prec)
     tuned_ms = batch.tune(Xs, reps=2) if args.tune else None
     for _ in range(args.warmup):
         batch.solve(Xs, Ls, Ss, masks=masks, thetas=thetas)
@@ -414,9 +415,9 @@ def run_batch(args):
         "dtype": "f32", "data": "synthetic (seeded microbubble windows, in HBM)",
         "config": {"workload": WORKLOAD_DESC,
                    "form": f"batched persistent launch, {NB} windows per step (different seeds)",
-                   "precision": "fp32", "tol": 1e-7, "eigensolve": _eig_desc(),
+                   "precision": args.precision, "tol": 1e-7, "eigensolve": _eig_desc(),
                    "l2": "flushed before every step (256 MB write, outside step events); "
-                         "the step's windows (8 x 3 x 21 MB) exceed L2",
+                         f"the step's windows ({NB} x 3 x 21 MB) exceed L2",
                    "schedule": info, "tuned_ms": tuned_ms,
                    "parallelism": f"replicas x{world} (independent windows)"},
         "ms_per_solve": ms_per_step / NB,
@@ -427,10 +428,14 @@ def run_batch(args):
         "kernel_us": {"pass_per_window": [round(r["pass_us"], 2) for r in res[:2]],
                       "eig": round(res[0]["eig_us"], 2)},
         "gpu_launches": args.steps * 2,
-        "roofline": _roofline(alg, ms_per_step * 1e-3 / 1.0, "batch_kernel<20> (persistent: passes + eigen-steps)",
+        "roofline": _roofline(alg, ms_per_step * 1e-3 / 1.0,
+                              ("batch_kernel<20>" if args.precision == "fp32" else
+                               f"batch_kernel_tc<32,{'bf16' if args.precision == 'bf16x3' else 'tf32'}>") +
+                              " (persistent: passes + eigen-steps)",
                               "CUDA events around each persistent launch (its descriptor copy and "
                               "control-block gather included), algorithmic bytes of all windows' solves",
-                              traffic=ncu_batch_traffic(kernel_source_hash(), iters)),
+                              traffic=ncu_batch_traffic(kernel_source_hash(), iters)
+                              if args.precision == "fp32" else None),
         "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": NB * m * T * 4,
                 "d2h_bytes_per_step": NB * (2 * m * T * 4 + m), "steps": e2e_steps,
                 "api": "rpca_batch_solve_host (C ABI, pinned host buffers in and out)",
@@ -973,7 +978,7 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "tf32x3", "bf16x3"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--form", choices=["batch", "plan", "serve"], default="batch")
-    ap.add_argument("--windows", type=int, default=8, help="windows per step (batch, serve)")
+    ap.add_argument("--windows", type=int, default=16, help="windows per step (batch, serve)")
     ap.add_argument("--slots", type=int, default=4, help="server slots (serve)")
     ap.add_argument("--tune", action="store_true", help="autotune the batch schedule first")
     ap.add_argument("--workload", default="w512x512_t20",
