@@ -329,8 +329,8 @@ struct NarrowDisp {
 };
 
 // Windows of frame bucket <= TBMAX (the batch's largest), lane by lane.
-// One CTA per SM: the pass and eigen-step bodies together spill under a
-// 128-register cap (measured: 545 vs 675 solves/s on 8 windows of 262144 x 20).
+// One CTA per SM: under a 128-register cap (two CTAs per SM) the kernel
+// spills (measured on 16 windows of 262144 x 20: 638 against 749 solves/s).
 template <int TBMAX>
 __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchDesc* bd) {
   extern __shared__ __align__(16) unsigned char batch_dsm[];
