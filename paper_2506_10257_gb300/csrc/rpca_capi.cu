@@ -112,7 +112,8 @@ bool get_set(int T, KernelSet* out) {
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Layout {
-  size_t ctrl, eig, red, job, gw, ww, vw, evw, rlog, rk, rrnd, gram_part, group_part, scal_part, gscal_part, ybuf, total;
+  size_t ctrl, eig, red, job, gw, ww, vw, evw, rlog, rk, rrnd, wtc, gram_part, group_part, scal_part, gscal_part, ybuf,
+      total;
   int grid, ngroups;
   int ws_grid;     // CTAs of the warp-specialised pass (one per SM, 128-pixel tiles)
   int wide_grid;   // CTAs of the wide pass (T > kMaxT; one per SM, 32-pixel tiles)
@@ -126,7 +127,8 @@ int device_sms() {
 }
 
 // Grid: two 256-thread CTAs per SM (register bound), never more than the tiles.
-Layout make_layout(int64_t m, int T, int sms, bool wide) {
+// wtc_bytes: B operand images of the tiled tensor-core pass (0: none).
+Layout make_layout(int64_t m, int T, int sms, bool wide, size_t wtc_bytes = 0) {
   Layout L;
   const int64_t ntiles = (m + kTile - 1) / kTile;
   int64_t grid = std::min<int64_t>(ntiles, (int64_t)std::max(sms, 1) * 2);
@@ -159,8 +161,9 @@ Layout make_layout(int64_t m, int T, int sms, bool wide) {
   L.rlog = take(sizeof(float2) * nrounds * npairs);
   L.rk = take(sizeof(int) * nrounds * npairs);
   L.rrnd = take(sizeof(int) * 2 * nrounds);
+  L.wtc = take(wtc_bytes ? wtc_bytes : 1);
   L.gram_part = take(sizeof(float) * (size_t)maxgrid * T * T);
-  L.group_part = take(sizeof(double) * (size_t)L.ngroups * T * T);
+  L.group_part = take(sizeof(float2) * (size_t)L.ngroups * T * T);
   L.scal_part = take(sizeof(double) * 2 * (size_t)maxgrid);
   L.gscal_part = take(sizeof(double) * 2 * (size_t)L.ngroups);
   L.ybuf = take(sizeof(float) * (size_t)m * T);
@@ -192,7 +195,9 @@ rpca_status validate(const rpca_params* p) {
   // bound of the reduced precisions, so it is not offered
   if (p->precision == RPCA_PREC_TF32) return RPCA_ERR_UNSUPPORTED;
   if (p->precision != RPCA_PREC_FP32 && p->drive == RPCA_DRIVE_HOST) return RPCA_ERR_UNSUPPORTED;
-  if (p->precision != RPCA_PREC_FP32 && p->T > kMaxT) return RPCA_ERR_UNSUPPORTED;  // wide path is FP32
+  // the tiled path's tensor-core pass: real windows of at most 128 frames
+  if (p->precision != RPCA_PREC_FP32 && p->T > kMaxT && (p->T > 128 || p->dtype != RPCA_R32))
+    return RPCA_ERR_UNSUPPORTED;
   if (p->m * (int64_t)p->T > (int64_t)1 << 40) return RPCA_ERR_ARG;
   if (p->warm_start != 0 && p->warm_start != 1) return RPCA_ERR_ARG;
   if (p->sharded != 0 && p->sharded != 1) return RPCA_ERR_ARG;
@@ -309,18 +314,22 @@ static dim3 pass_block(const rpca_plan_s* pl) {
 // Fused per-iteration pass: CUDA-core FP32 or the tensor-core form of the plan's precision.
 static void* fused_fn(const rpca_plan_s* pl) {
   if (pl->p.precision == RPCA_PREC_FP32) return pass_fn(pl, PM_FUSED);
+  if (pl->wide) return pl->wk.pass_tc[pl->p.precision];
   return pl->use_ws ? pl->ks.pass_ws[pl->p.precision] : pl->ks.pass_tc[pl->p.precision];
 }
 static size_t fused_smem(const rpca_plan_s* pl) {
   if (pl->p.precision == RPCA_PREC_FP32) return pass_smem(pl);
+  if (pl->wide) return pl->wk.pass_tc_smem[pl->p.precision];
   return pl->use_ws ? pl->ks.pass_ws_smem[pl->p.precision] : pl->ks.pass_tc_smem[pl->p.precision];
 }
 static dim3 fused_grid(const rpca_plan_s* pl) {
   if (pl->p.precision == RPCA_PREC_FP32) return pass_grid(pl);
+  if (pl->wide) return dim3(pl->lay.ws_grid);  // one CTA per SM, 128-pixel tiles
   return dim3(pl->use_ws ? pl->lay.ws_grid : pl->lay.grid);
 }
 static dim3 fused_block(const rpca_plan_s* pl) {
   if (pl->p.precision == RPCA_PREC_FP32) return pass_block(pl);
+  if (pl->wide) return dim3(pl->wk.pass_tc_threads);
   return dim3(pl->use_ws ? kWsThreads : kPassThreads);
 }
 
@@ -451,7 +460,8 @@ rpca_status rpca_workspace_size(const rpca_params* p, size_t* bytes) {
   if (!bytes) return RPCA_ERR_ARG;
   const int sms = device_sms();
   if (sms <= 0) return RPCA_ERR_CUDA;
-  *bytes = make_layout(p->m, real_cols(p), sms, uses_wide(p)).total;
+  *bytes = make_layout(p->m, real_cols(p), sms, uses_wide(p),
+                       uses_wide(p) ? wide_tc_img_bytes(real_cols(p), p->precision) : 0).total;
   return RPCA_OK;
 }
 
@@ -493,7 +503,7 @@ static rpca_status plan_create_impl(const rpca_params* p, void* workspace, size_
     }
     set_tc(p->T, &pl->ks);
   }
-  pl->use_ws = (p->precision != RPCA_PREC_FP32) && (p->m % 4 == 0) && tma_encoder() != nullptr &&
+  pl->use_ws = !pl->wide && (p->precision != RPCA_PREC_FP32) && (p->m % 4 == 0) && tma_encoder() != nullptr &&
                !(getenv("RPCA_NO_WS") && atoi(getenv("RPCA_NO_WS")) != 0);
   // The TMA-fed FP32 pass is opt-in (RPCA_PASS_TMA=1): at 10..32 frames the
   // register-resident pass with two CTAs per SM measured as fast or faster.
@@ -520,7 +530,11 @@ static rpca_status plan_create_impl(const rpca_params* p, void* workspace, size_
       }
     }
   }
-  if (p->precision != RPCA_PREC_FP32) {
+  if (p->precision != RPCA_PREC_FP32 && pl->wide && !pl->wk.pass_tc[p->precision]) {
+    delete pl;
+    return RPCA_ERR_UNSUPPORTED;
+  }
+  if (p->precision != RPCA_PREC_FP32 && !pl->wide) {
     cudaError_t ea = cudaFuncSetAttribute(pl->ks.pass_tc[p->precision], cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)pl->ks.pass_tc_smem[p->precision]);
     if (ea == cudaSuccess && pl->use_ws)
@@ -531,7 +545,7 @@ static rpca_status plan_create_impl(const rpca_params* p, void* workspace, size_
       return cuda_status(ea);
     }
   }
-  pl->lay = make_layout(p->m, Tr, sms, pl->wide);
+  pl->lay = make_layout(p->m, Tr, sms, pl->wide, pl->wide ? wide_tc_img_bytes(Tr, p->precision) : 0);
   if (!pl->wide) {
     cudaError_t ea = cudaFuncSetAttribute(pl->ks.eig_fast, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)pl->ks.eig_fast_smem);
@@ -565,7 +579,7 @@ static rpca_status plan_create_impl(const rpca_params* p, void* workspace, size_
   b.red = (RedState*)(pl->ws + pl->lay.red);
   b.job = (Job*)(pl->ws + pl->lay.job);
   b.gram_part = (float*)(pl->ws + pl->lay.gram_part);
-  b.group_part = (double*)(pl->ws + pl->lay.group_part);
+  b.group_part = (float2*)(pl->ws + pl->lay.group_part);
   b.scal_part = (double*)(pl->ws + pl->lay.scal_part);
   b.gscal_part = (double*)(pl->ws + pl->lay.gscal_part);
   b.Gw = (double*)(pl->ws + pl->lay.gw);
@@ -575,6 +589,8 @@ static rpca_status plan_create_impl(const rpca_params* p, void* workspace, size_
   b.rot_log = (float2*)(pl->ws + pl->lay.rlog);
   b.rot_k = (int*)(pl->ws + pl->lay.rk);
   b.rot_rnd = (int*)(pl->ws + pl->lay.rrnd);
+  b.wtc = (pl->wide && p->precision == RPCA_PREC_TF32X3) ? 1 : (pl->wide && p->precision == RPCA_PREC_BF16X3) ? 2 : 0;
+  b.wtc_img = b.wtc ? (unsigned char*)(pl->ws + pl->lay.wtc) : nullptr;
   b.m = p->m;
   b.T = Tr;
   b.cplx = cplx ? 1 : 0;

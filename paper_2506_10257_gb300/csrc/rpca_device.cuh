@@ -91,7 +91,8 @@ struct EigState {
 
 // Cross-CTA reduction state (two levels, last-arriving CTA reduces).
 struct RedState {
-  double G[kMaxT * kMaxT];     // final Gram (row-major, FP64 sums of the CTAs' FP32 partials)
+  double G[kMaxT * kMaxT];     // final Gram (row-major): the CTAs' FP32 partials summed in two-float
+                               // arithmetic, stored in FP64
   double e2;                   // sum of E^2 (or ||X||_F^2 in the init pass)
   double l1;                   // sum |X| (init pass)
   unsigned long long t_start;  // earliest CTA start of the last pass (globaltimer)
@@ -132,7 +133,8 @@ struct Bufs {
   RedState* red;
   Job* job;
   float* gram_part;    // [grid][T*T] FP32 partial Gram of each CTA
-  double* group_part;  // [ngroups][T*T] FP64 sums of the partials of each group of CTAs
+  float2* group_part;  // [ngroups][T*T] sums of the partials of each group of CTAs as two-float
+                       // (hi, lo) values: hi + lo carries the sum to about 2^-48 of its terms
   double* scal_part;   // [grid][2]
   double* gscal_part;  // [ngroups][2]
   int64_t m;
@@ -146,10 +148,12 @@ struct Bufs {
   int eig64;           // narrow eigen-step: 1 FP64 Jacobi rotations and basis arithmetic, 0 FP32
   // T > kMaxT ("wide" windows): the reduced Gram, Wbar and V live in these
   // T x T row-major arrays of the workspace instead of red->G and EigState.
-  double* Gw;          // FP64 sums of the partial Grams (also scratch of the eigen-step)
+  double* Gw;          // summed partial Grams as FP64 (also scratch of the eigen-step)
   float* Ww;
   float* Vw;
   double* evw;
+  unsigned char* wtc_img;  // tiled tensor-core pass: B operand images of Wbar and V (NULL: unused)
+  int wtc;            // their arithmetic: 0 none, 1 TF32x3, 2 BF16x3
   float2* rot_log;    // wide eigen-step: (c, s) of every rotated pair of every executed round
   int* rot_k;         // ... its pair slot in the round
   int* rot_rnd;       // ... per round: round number and rotated pairs

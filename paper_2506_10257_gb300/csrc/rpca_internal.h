@@ -28,7 +28,13 @@ struct WideKernels {
   void* eig;            // (Bufs, flags, handle, use_cond)
   size_t eig_smem;
   int eig_threads;
+  void* pass_tc[4];     // fused pass on the tensor cores per rpca_precision (real TP <= 128; NULL: none)
+  size_t pass_tc_smem[4];
+  int pass_tc_threads;
 };
+
+// Bytes of the B operand images a tiled tensor-core plan keeps (0: none).
+size_t wide_tc_img_bytes(int T, int precision);
 
 // Fills *out for T real columns (complex windows: T = 2 x frames, cplx set);
 // false when T is not a wide column count (real T <= kMaxT unless force) or a

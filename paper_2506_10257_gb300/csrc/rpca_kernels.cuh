@@ -117,45 +117,68 @@ __device__ __forceinline__ void vec_mat(const float (&z)[TB], const float* M, fl
   }
 }
 
-// Sums rows [r0, r1) of a row-major [rows][TT] array (float partials of the
-// CTAs, or double group sums) entry by entry in FP64 in a fixed row order,
-// calling out(e, sum) for every entry; each thread takes entries tid,
-// tid + blockDim, ... and issues its loads in batches of 16 so that their L2
-// latencies overlap.  Sums of FP32 products in FP64 are exact to about 2^-53
-// of their magnitude, so the reduced Gram carries only the rounding of the
-// CTAs' own FP32 accumulations.
+// Two-float (hi, lo) accumulation: (hi, lo) += (bh, bl) with Knuth's TwoSum
+// and a renormalisation (Dekker's double-single addition), so hi + lo holds
+// the exact sum to about 2^-48 of the magnitudes added, on the FP32 pipe
+// (GB300's FP64 pipe runs at a small fraction of its FP32 rate).
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float bh, float bl) {
+  const float s = hi + bh;
+  const float bp = s - hi;
+  const float e = (hi - (s - bp)) + (bh - bp);
+  const float t = (e + lo) + bl;
+  hi = s + t;
+  lo = t - (hi - s);
+}
+__device__ __forceinline__ float2 ff_term(float v) { return make_float2(v, 0.f); }
+__device__ __forceinline__ float2 ff_term(float2 v) { return v; }
+
+// Sums rows [r0, r1) of a row-major [rows][TT] array (FP32 partials of the
+// CTAs, or two-float group sums) entry by entry in two-float arithmetic in a
+// fixed row order, calling out(e, hi, lo) for every entry; each thread takes
+// entries tid, tid + blockDim, ... and issues its loads in batches of 16 so
+// that their L2 latencies overlap.  The reduced Gram thus carries only the
+// rounding of the CTAs' own FP32 accumulations.
 template <int W = 1, typename Src, typename Out>
 __device__ __forceinline__ void sum_rows(const Src* src, int r0, int r1, int TT, Out out) {
   // W = 4: four entries per step (T x T Grams of wide windows), so that 64
   // loads are in flight per thread
   int e = threadIdx.x;
   for (; W == 4 && e + 3 * (int)blockDim.x < TT; e += 4 * blockDim.x) {
-    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
     for (int rb = r0; rb < r1; rb += 16) {
       Src v[4][16];
 #pragma unroll
       for (int q = 0; q < 4; ++q)
 #pragma unroll
         for (int u = 0; u < 16; ++u)
-          v[q][u] = (rb + u < r1) ? __ldcg(&src[(int64_t)(rb + u) * TT + e + q * blockDim.x]) : (Src)0;
+          if (rb + u < r1) v[q][u] = __ldcg(&src[(int64_t)(rb + u) * TT + e + q * blockDim.x]);
 #pragma unroll
       for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int u = 0; u < 16; ++u) s[q] += (double)v[q][u];
+        for (int u = 0; u < 16; ++u)
+          if (rb + u < r1) {
+            const float2 t = ff_term(v[q][u]);
+            ff_add(h[q], l[q], t.x, t.y);
+          }
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) out(e + q * blockDim.x, s[q]);
+    for (int q = 0; q < 4; ++q) out(e + q * blockDim.x, h[q], l[q]);
   }
   for (; e < TT; e += blockDim.x) {
-    double s = 0.0;
+    float h = 0.f, l = 0.f;
     for (int rb = r0; rb < r1; rb += 16) {
       Src v[16];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) v[u] = (rb + u < r1) ? __ldcg(&src[(int64_t)(rb + u) * TT + e]) : (Src)0;
+      for (int u = 0; u < 16; ++u)
+        if (rb + u < r1) v[u] = __ldcg(&src[(int64_t)(rb + u) * TT + e]);
 #pragma unroll
-      for (int u = 0; u < 16; ++u) s += (double)v[u];
+      for (int u = 0; u < 16; ++u)
+        if (rb + u < r1) {
+          const float2 t = ff_term(v[u]);
+          ff_add(h, l, t.x, t.y);
+        }
     }
-    out(e, s);
+    out(e, h, l);
   }
 }
 
@@ -216,8 +239,8 @@ static __device__ __noinline__ bool cross_cta_reduce(Bufs b, bool kGram, double*
   if (!sLast) return false;
   __threadfence();
   if (kGram) {
-    double* gp = b.group_part + (int64_t)grp * TT;
-    sum_rows<W>(b.gram_part, c0, c1, TT, [&](int e, double v) { gp[e] = v; });
+    float2* gp = b.group_part + (int64_t)grp * TT;
+    sum_rows<W>(b.gram_part, c0, c1, TT, [&](int e, float h, float l) { gp[e] = make_float2(h, l); });
   }
   sum_scalars(b.scal_part, c0, c1, sScal, [&](double s0, double s1) {
     b.gscal_part[2 * grp] = s0;
@@ -248,10 +271,11 @@ static __device__ __noinline__ bool cross_cta_reduce(Bufs b, bool kGram, double*
   if (kGram) {
     if (b.wide) {
       double* G = b.Gw;
-      sum_rows<W>(b.group_part, 0, ngroups, TT, [&](int e, double v) { G[e] = v; });
+      sum_rows<W>(b.group_part, 0, ngroups, TT, [&](int e, float h, float l) { G[e] = (double)h + (double)l; });
     } else {
       double* G = b.red->G;
-      sum_rows(b.group_part, 0, ngroups, TT, [&](int e, double v) { G[(e / T) * kMaxT + e % T] = v; });
+      sum_rows(b.group_part, 0, ngroups, TT,
+               [&](int e, float h, float l) { G[(e / T) * kMaxT + e % T] = (double)h + (double)l; });
     }
   }
   sum_scalars(b.gscal_part, 0, ngroups, sScal, [&](double s0, double s1) {
@@ -577,10 +601,11 @@ static __device__ void finalize_sums(Bufs b, double* sh) {
   if (b.red->gram_last) {
     if (b.wide) {
       double* G = b.Gw;
-      sum_rows<4>(b.group_part, 0, ng, TT, [&](int e, double v) { G[e] = v; });
+      sum_rows<4>(b.group_part, 0, ng, TT, [&](int e, float h, float l) { G[e] = (double)h + (double)l; });
     } else {
       double* G = b.red->G;
-      sum_rows(b.group_part, 0, ng, TT, [&](int e, double v) { G[(e / T) * kMaxT + e % T] = v; });
+      sum_rows(b.group_part, 0, ng, TT,
+               [&](int e, float h, float l) { G[(e / T) * kMaxT + e % T] = (double)h + (double)l; });
     }
   }
   sum_scalars(b.gscal_part, 0, ng, sh, [&](double s0, double s1) {

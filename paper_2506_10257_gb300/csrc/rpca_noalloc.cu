@@ -39,7 +39,7 @@ constexpr size_t kNaJob = na_align(kNaRed + sizeof(RedState));
 constexpr size_t kNaHeader = na_align(kNaJob + sizeof(Job));      // zeroed by every call
 constexpr size_t kNaGram = kNaHeader;
 constexpr size_t kNaGroup = na_align(kNaGram + sizeof(float) * kNaMaxGrid * kMaxT * kMaxT);
-constexpr size_t kNaScal = na_align(kNaGroup + sizeof(double) * kNaMaxGroups * kMaxT * kMaxT);
+constexpr size_t kNaScal = na_align(kNaGroup + sizeof(float2) * kNaMaxGroups * kMaxT * kMaxT);
 constexpr size_t kNaGscal = na_align(kNaScal + sizeof(double) * 2 * kNaMaxGrid);
 constexpr size_t kNaBytes = na_align(kNaGscal + sizeof(double) * 2 * kNaMaxGroups);  // about 2.4 MB
 
@@ -164,7 +164,7 @@ extern "C" rpca_status rpca_gram_noalloc(const float* X, int64_t m, int32_t T, c
   b.red = (RedState*)(s0 + kNaRed);
   b.job = (Job*)(s0 + kNaJob);
   b.gram_part = (float*)(s0 + kNaGram);
-  b.group_part = (double*)(s0 + kNaGroup);
+  b.group_part = (float2*)(s0 + kNaGroup);
   b.scal_part = (double*)(s0 + kNaScal);
   b.gscal_part = (double*)(s0 + kNaGscal);
   b.m = m;

@@ -32,7 +32,26 @@ WideKernels make_wide() {
   k.pass_threads = kWideThreads;
   k.eig = (void*)eig_wide_kernel;
   k.eig_threads = kEigWThreads;
+  for (int i = 0; i < 4; ++i) {
+    k.pass_tc[i] = nullptr;
+    k.pass_tc_smem[i] = 0;
+  }
+  k.pass_tc_threads = kWtcThreads;
+  if constexpr (!CPLX && TP >= 64 && TP <= 128) {
+    k.pass_tc[RPCA_PREC_TF32X3] = (void*)pass_wtc_kernel<TP, false>;
+    k.pass_tc_smem[RPCA_PREC_TF32X3] = WtcShape<TP, false>::SMEM;
+    k.pass_tc[RPCA_PREC_BF16X3] = (void*)pass_wtc_kernel<TP, true>;
+    k.pass_tc_smem[RPCA_PREC_BF16X3] = WtcShape<TP, true>::SMEM;
+  }
   return k;
+}
+
+size_t wide_tc_img_bytes(int T, int precision) {
+  const int TP = (T + 31) / 32 * 32;
+  if (TP < 64 || TP > 128) return 0;
+  if (precision == RPCA_PREC_TF32X3) return wtc_img_bytes(TP, false);
+  if (precision == RPCA_PREC_BF16X3) return wtc_img_bytes(TP, true);
+  return 0;
 }
 
 void wide_launch_shape(int T, int* tile, int* per_sm) {
@@ -66,6 +85,10 @@ bool wide_kernels(int T, bool cplx, bool force, WideKernels* out) {
   for (int i = 0; i < 4; ++i)
     if (cudaFuncSetAttribute(out->pass[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->pass_smem) !=
         cudaSuccess)
+      return false;
+  for (int i = 0; i < 4; ++i)
+    if (out->pass_tc[i] && cudaFuncSetAttribute(out->pass_tc[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)out->pass_tc_smem[i]) != cudaSuccess)
       return false;
   return true;
 }

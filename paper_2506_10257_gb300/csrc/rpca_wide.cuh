@@ -710,6 +710,23 @@ __global__ void __launch_bounds__(kWideThreads, res_blocks_per_sm(TP)) pass_res_
   pass_res_body<TP, MODE, CPLX>(b, blockIdx.x, gridDim.x, res_smem);
 }
 
+#include "rpca_wide_tc.cuh"
+
+// The B operand images of the tiled tensor-core pass (b.wtc), written by the
+// eigen-step once Ww and Vw are final.
+__device__ __forceinline__ void wtc_images(const Bufs& b) {
+  const int TP = (b.T + 31) / 32 * 32;
+  if (b.wtc == 1) {
+    if (TP == 64) wtc_write_images<64, false>(b);
+    else if (TP == 96) wtc_write_images<96, false>(b);
+    else if (TP == 128) wtc_write_images<128, false>(b);
+  } else if (b.wtc == 2) {
+    if (TP == 64) wtc_write_images<64, true>(b);
+    else if (TP == 96) wtc_write_images<96, true>(b);
+    else if (TP == 128) wtc_write_images<128, true>(b);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Eigen-step for wide windows (one CTA; the stand-alone kernel uses kEigWThreads threads).
 // ---------------------------------------------------------------------------
@@ -1117,6 +1134,10 @@ static __device__ void eig_wide_body(Bufs b, int flags, cudaGraphConditionalHand
           b.Ww[c * T + a] = acc[i * 4 + k];
         }
       }
+  }
+  if (b.wtc) {
+    __syncthreads();  // Ww written by the whole CTA
+    wtc_images(b);
   }
   if (tid < T) b.evw[tid] = sEv[tid];
   if (tid == 0) {

@@ -183,6 +183,9 @@ PRESETS = {
     "w512x512_t20": dict(ny=512, nx=512, T=20, n_bound=400, n_free=800, speed=(0.5, 5.0)),
     "w512x512_t50": dict(ny=512, nx=512, T=50, n_bound=400, n_free=800, speed=(0.5, 5.0)),
     "w512x512_t100": dict(ny=512, nx=512, T=100, n_bound=400, n_free=800, speed=(0.5, 5.0)),
+    # a quarter of the 512x512 field (blob counts scaled with the area)
+    "w256x256_t50": dict(ny=256, nx=256, T=50, n_bound=100, n_free=200, speed=(0.5, 5.0)),
+    "w256x256_t100": dict(ny=256, nx=256, T=100, n_bound=100, n_free=200, speed=(0.5, 5.0)),
     # the paper's own execution-time shape, 338 x 260 pixels (Sec. III-D)
     "w338x260_t20": dict(ny=338, nx=260, T=20, n_bound=200, n_free=400, speed=(0.5, 5.0)),
     "w338x260_t60": dict(ny=338, nx=260, T=60, n_bound=200, n_free=400, speed=(0.5, 5.0)),

@@ -126,3 +126,16 @@ def test_wide_512x512_matches_oracle(rp, T):
     # the paper-scale windows of the frame sweep, in the launch shape the
     # benchmark's plan form uses
     check(rp, (512, 512, T, 5))
+
+
+@pytest.mark.parametrize("prec", ["TF32X3", "BF16X3"])
+def test_wide_tensor_core_256x256x100(rp, prec):
+    # the tiled tensor-core pass (three contractions on tcgen05) at 65536
+    # pixels x 100 frames: 512 tiles of 128 pixels, several per CTA
+    check(rp, (256, 256, 100, 110), prec)
+
+
+@pytest.mark.parametrize("prec", ["TF32X3", "BF16X3"])
+def test_wide_tensor_core_512x512(rp, prec):
+    # the precision study's windows: 262144 x 100 (TF32x3) and 262144 x 50 (BF16x3)
+    check(rp, (512, 512, 100 if prec == "TF32X3" else 50, 5), prec)

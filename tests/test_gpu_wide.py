@@ -121,12 +121,55 @@ def test_wide_mask_and_fixed_schedule(rp):
     assert O.dice(mask.cpu().numpy().astype(bool), mref) >= 0.999
 
 
-def test_wide_rejects_tensor_core_precision(rp):
+def test_wide_rejects_unbuilt_tensor_core_shapes(rp):
+    # the tiled tensor-core pass covers real windows of up to 128 frames
     with pytest.raises(rp.RpcaError) as e:
-        rp.Plan(4096, 50, precision=rp.PREC_BF16X3)
+        rp.Plan(4096, 129, precision=rp.PREC_BF16X3)
+    assert e.value.status == rp.ERR_UNSUPPORTED
+    with pytest.raises(rp.RpcaError) as e:
+        rp.Plan(4096, 40, precision=rp.PREC_TF32X3, dtype=rp.C64)
     assert e.value.status == rp.ERR_UNSUPPORTED
     with pytest.raises(rp.RpcaError):
         rp.Plan(4096, 225)
+
+
+TC_TOL = {"TF32X3": 1e-5, "BF16X3": 1e-4}
+
+
+@pytest.mark.parametrize("prec", ["TF32X3", "BF16X3"])
+@pytest.mark.parametrize("ny,nx,T", [(32, 32, 33), (64, 64, 50), (31, 45, 64), (40, 51, 77), (64, 64, 100),
+                                     (48, 40, 128), (17, 19, 40)])
+def test_wide_tensor_core_matches_oracle(rp, prec, ny, nx, T):
+    # the tiled tensor-core pass (Q, Z~ and the rotated Gram on tcgen05) on
+    # 64-, 96- and 128-column tiles, ragged pixel counts (last 128-pixel tile
+    # partial) and frame counts that leave columns of the last chunk empty
+    w = synth.make_window(seed=ny * nx + T + 7, ny=ny, nx=nx, T=T, n_bound=6, n_free=10)
+    L, S, res = gpu_solve(rp, w.frames, precision=getattr(rp, "PREC_" + prec))
+    assert res["status"] == rp.OK, res
+    ref = O.rpca_frames(w.frames)
+    tol = TC_TOL[prec]
+    eL, eS = rel(L, ref.L), rel(S, ref.S)
+    assert eL <= tol and eS <= tol, (prec, eL, eS, res["iters"], ref.iters)
+
+
+@pytest.mark.parametrize("prec", ["TF32X3", "BF16X3"])
+def test_wide_tensor_core_warm_start_and_stream_drive(rp, prec):
+    w = synth.make_window(seed=31, ny=32, nx=40, T=61, n_bound=5, n_free=8)
+    F = np.ascontiguousarray(w.frames, dtype=np.float32)
+    tol = TC_TOL[prec]
+    L, S, res = gpu_solve(rp, F, precision=getattr(rp, "PREC_" + prec), drive=rp.DRIVE_STREAM)
+    ref = O.rpca_frames(F)
+    assert rel(L, ref.L) <= tol and rel(S, ref.S) <= tol
+    prev = ref
+    S0 = np.zeros_like(prev.S); S0[:-1] = prev.S[1:]
+    Y0 = np.zeros_like(prev.Y); Y0[:-1] = prev.Y[1:]
+    S0, Y0 = S0.astype(np.float32), Y0.astype(np.float32)
+    ref2 = O.rpca_frames(F, S0=S0.astype(np.float64), Y0=Y0.astype(np.float64))
+    plan = rp.Plan(w.m, 61, warm_start=1, precision=getattr(rp, "PREC_" + prec))
+    L2, S2, res2 = plan.solve(cuda(F), L=cuda(Y0), S=cuda(S0))
+    torch.cuda.synchronize()
+    plan.close()
+    assert rel(L2.cpu().numpy(), ref2.L) <= 2 * tol and rel(S2.cpu().numpy(), ref2.S) <= 2 * tol
 
 
 def test_wide_served(rp):
