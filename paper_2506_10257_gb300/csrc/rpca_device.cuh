@@ -155,7 +155,7 @@ struct Bufs {
   unsigned char* wtc_img;  // tiled tensor-core pass: B operand images of Wbar and V (NULL: unused)
   int wtc;            // their arithmetic: 0 none, 1 TF32x3, 2 BF16x3
   float2* rot_log;    // wide eigen-step: (c, s) of every rotated pair of every executed round
-  int* rot_k;         // ... its pair slot in the round
+  int* rot_k;         // ... its columns p | q << 8, bit 16 set on the first rotation of a round
   int* rot_rnd;       // ... per round: round number and rotated pairs
 };
 

@@ -742,12 +742,9 @@ static __device__ void eig_wide_body(Bufs b, int flags, cudaGraphConditionalHand
   __shared__ float sDp[kMaxTW / 2], sDq[kMaxTW / 2];
   __shared__ double sEv[kMaxTW];
   __shared__ float sG[kMaxTW];
-  __shared__ float4 sCS[2][kMaxTW / 2];   // replay: (c, s, c - 1) per rotation
-  __shared__ int2 sPQ[2][kMaxTW / 2];
   __shared__ int sAct[kMaxTW / 2], sPos[kMaxTW / 2];
   __shared__ int4 sPair[kMaxTW / 2];    // (p, q, c, s) of every pair slot of the round
   __shared__ int sWarpCnt[(kMaxTW / 2 + 31) / 32];
-  __shared__ int sNa[2];
   __shared__ int sFlag;
   __shared__ double sTau;
 
@@ -780,7 +777,7 @@ static __device__ void eig_wide_body(Bufs b, int flags, cudaGraphConditionalHand
   // (c, s)) to the workspace and applied to V after the sweeps, with V staged
   // in shared memory.
   float2* log_cs = b.rot_log;   // (c, s) of every rotated pair, round after round
-  int* log_k = b.rot_k;          // its pair slot in the round
+  int* log_k = b.rot_k;          // its columns p | q << 8, bit 16 on the first rotation of a round
   int* log_rnd = b.rot_rnd;      // per logged round: round number, rotated pairs
   const int KW = (K + 31) / 32;  // warps covering the pair slots
   int logged = 0;                // entries logged so far
@@ -842,7 +839,9 @@ static __device__ void eig_wide_body(Bufs b, int flags, cudaGraphConditionalHand
         off += __popc(bal & ((1u << (tid & 31)) - 1u));
         sAct[off] = tid;
         sPos[tid] = off;
-        log_k[logged + off] = tid;
+        // the replay needs the pair's columns and where each round starts
+        const int4 pr = sPair[tid];
+        log_k[logged + off] = pr.x | (pr.y << 8) | (off == 0 ? (1 << 16) : 0);
         log_cs[logged + off] = make_float2(sC[tid], sSn[tid]);
       }
       if (tid == 0) {
@@ -905,70 +904,62 @@ static __device__ void eig_wide_body(Bufs b, int flags, cudaGraphConditionalHand
   //      are relative to small entries; then V <- V + V D ----
   float* D = G;  // [T][LD]
   for (int i = tid; i < T * LD; i += nthr) D[i] = 0.f;
-  // rounds are fetched one ahead: loaded into registers at the start of a
-  // round, stored to the other shared buffer at its end
-  int lbase = 0;
-  auto fetch = [&](int lr, int base, float4& cs, int2& pq, int& n) {
-    n = __ldcg(&log_rnd[2 * lr + 1]);
-    if (tid < n) {
-      const float2 v = __ldcg(&log_cs[base + tid]);
-      cs = make_float4(v.x, v.y, -v.y * v.y / (1.f + v.x), 0.f);   // c - 1 = -s^2 / (1 + c)
-      int pa, pb;
-      rr_pair(__ldcg(&log_rnd[2 * lr]), __ldcg(&log_k[base + tid]), Te, pa, pb);
-      pq = make_int2(min(pa, pb), max(pa, pb));
+  // The rows of D are independent (D' = D J + (J - I) mixes columns p and q
+  // of each row) and warp w owns rows w, w + nwarps, ..., so between rounds
+  // only a warp has to wait for itself.  The CTA stages the log a chunk at a
+  // time into shared memory (over the V staging rows, free until the update
+  // below; one barrier per chunk); each warp walks the chunk 32 entries at a
+  // time, lane = rotation, and applies the rotations of one round (a run of
+  // entries starting at a flagged one) before those of the next.
+  {
+    const int nwarps = nthr >> 5, warp = tid >> 5, lane = tid & 31;
+    float2* stc = reinterpret_cast<float2*>(eigw_smem + (size_t)Te * LD);
+    const int E = max(1, (vrows * T * (int)sizeof(float)) / (int)(sizeof(float2) + sizeof(int)));
+    int* stp = reinterpret_cast<int*>(stc + E);
+    for (int c0 = 0; c0 < logged; c0 += E) {
+      const int ne = min(E, logged - c0);
+      __syncthreads();  // (D zeroed; the previous chunk consumed)
+      for (int i = tid; i < ne; i += nthr) {
+        stc[i] = __ldcg(&log_cs[c0 + i]);
+        stp[i] = __ldcg(&log_k[c0 + i]);
+      }
+      __syncthreads();
+      for (int w0 = 0; w0 < ne; w0 += 32) {
+        const int i = w0 + lane;
+        const bool have = i < ne;
+        const int pk = have ? stp[i] : 0;
+        const float2 cs = have ? stc[i] : make_float2(1.f, 0.f);
+        const unsigned starts = __ballot_sync(0xffffffffu, have && (pk >> 16) != 0);
+        const int p = pk & 255, q = (pk >> 8) & 255;
+        // Q' = Q J  <=>  D' = D J + (J - I); c - 1 = -s^2 / (1 + c)
+        const float c = cs.x, sn = cs.y, cm1 = -sn * sn / (1.f + c);
+        const int nlive = min(32, ne - w0);
+        for (int lo = 0; lo < nlive;) {
+          const unsigned later = lo < 31 ? (starts & ~((2u << lo) - 1u)) : 0u;
+          const int hi = later ? __ffs(later) - 1 : 32;
+          if (lane >= lo && lane < hi && have && q < T) {
+            for (int r = warp; r < T; r += nwarps) {
+              float* dr = &D[r * LD];
+              const float dp = dr[p], dq = dr[q];
+              float np = fmaf(c, dp, -sn * dq), nq = fmaf(sn, dp, c * dq);
+              if (r == p) {
+                np += cm1;
+                nq += sn;
+              } else if (r == q) {
+                np -= sn;
+                nq += cm1;
+              }
+              dr[p] = np;
+              dr[q] = nq;
+            }
+          }
+          __syncwarp();
+          lo = hi;
+        }
+      }
     }
-  };
-  if (rounds_run > 0) {
-    float4 cs;
-    int2 pq;
-    int n;
-    fetch(0, 0, cs, pq, n);
-    if (tid < n) {
-      sCS[0][tid] = cs;
-      sPQ[0][tid] = pq;
-    }
-    if (tid == 0) sNa[0] = n;
   }
   __syncthreads();
-  for (int lr = 0; lr < rounds_run; ++lr) {
-    const int cb = lr & 1;
-    const int na = sNa[cb];
-    float4 ncs = make_float4(1.f, 0.f, 0.f, 0.f);
-    int2 npq = make_int2(0, 0);
-    int nn = 0;
-    if (lr + 1 < rounds_run) fetch(lr + 1, lbase + na, ncs, npq, nn);
-    // lane l takes rotations l, l + 32, ... (read once), warp w rows w, w + 32, ...
-    for (int k = tid & 31; k < na; k += 32) {
-      const float4 cs = sCS[cb][k];
-      const int2 pq = sPQ[cb][k];
-      if (pq.y >= T) continue;
-      // Q' = Q J  <=>  D' = D J + (J - I)
-      const float c = cs.x, sn = cs.y, cm1 = cs.z;
-      for (int r = tid >> 5; r < T; r += nthr / 32) {
-        float* dr = &D[r * LD];
-        const float dp = dr[pq.x], dq = dr[pq.y];
-        float np = fmaf(c, dp, -sn * dq), nq = fmaf(sn, dp, c * dq);
-        if (r == pq.x) {
-          np += cm1;
-          nq += sn;
-        } else if (r == pq.y) {
-          np -= sn;
-          nq += cm1;
-        }
-        dr[pq.x] = np;
-        dr[pq.y] = nq;
-      }
-    }
-    if (lr + 1 < rounds_run) {
-      if (tid < nn) {
-        sCS[cb ^ 1][tid] = ncs;
-        sPQ[cb ^ 1][tid] = npq;
-      }
-      if (tid == 0) sNa[cb ^ 1] = nn;
-    }
-    lbase += na;
-    __syncthreads();
-  }
   // V <- V + V D, vrows rows of V at a time staged after D
   float* sVo = eigw_smem + (size_t)Te * LD;  // [vrows][T]
   for (int r0 = 0; r0 < T; r0 += vrows) {
