@@ -151,15 +151,14 @@ __device__ __forceinline__ void sum_rows(const Src* src, int r0, int r1, int TT,
       for (int q = 0; q < 4; ++q)
 #pragma unroll
         for (int u = 0; u < 16; ++u)
-          if (rb + u < r1) v[q][u] = __ldcg(&src[(int64_t)(rb + u) * TT + e + q * blockDim.x]);
+          v[q][u] = (rb + u < r1) ? __ldcg(&src[(int64_t)(rb + u) * TT + e + q * blockDim.x]) : Src{};
 #pragma unroll
       for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int u = 0; u < 16; ++u)
-          if (rb + u < r1) {
-            const float2 t = ff_term(v[q][u]);
-            ff_add(h[q], l[q], t.x, t.y);
-          }
+        for (int u = 0; u < 16; ++u) {
+          const float2 t = ff_term(v[q][u]);  // (zero past the last row)
+          ff_add(h[q], l[q], t.x, t.y);
+        }
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) out(e + q * blockDim.x, h[q], l[q]);
@@ -169,14 +168,12 @@ __device__ __forceinline__ void sum_rows(const Src* src, int r0, int r1, int TT,
     for (int rb = r0; rb < r1; rb += 16) {
       Src v[16];
 #pragma unroll
-      for (int u = 0; u < 16; ++u)
-        if (rb + u < r1) v[u] = __ldcg(&src[(int64_t)(rb + u) * TT + e]);
+      for (int u = 0; u < 16; ++u) v[u] = (rb + u < r1) ? __ldcg(&src[(int64_t)(rb + u) * TT + e]) : Src{};
 #pragma unroll
-      for (int u = 0; u < 16; ++u)
-        if (rb + u < r1) {
-          const float2 t = ff_term(v[u]);
-          ff_add(h, l, t.x, t.y);
-        }
+      for (int u = 0; u < 16; ++u) {
+        const float2 t = ff_term(v[u]);  // (zero past the last row)
+        ff_add(h, l, t.x, t.y);
+      }
     }
     out(e, h, l);
   }
