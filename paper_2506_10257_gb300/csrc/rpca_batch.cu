@@ -341,9 +341,13 @@ rpca_status apply_config(rpca_batch_s* b, const BatchConfig& cfg) {
 
 std::string make_signature(const rpca_batch_s* b) {
   std::vector<std::string> parts;
-  for (const rpca_params& p : b->p) parts.push_back(std::to_string(p.m) + "x" + std::to_string(p.T));
+  for (const rpca_params& p : b->p)
+    parts.push_back(std::to_string(p.m) + "x" + std::to_string(p.T) + "d" + std::to_string((int)p.dtype));
   std::sort(parts.begin(), parts.end());
-  std::string s = "sms" + std::to_string(b->sms);
+  // the kernel (its precision, tiled or not) and its residency enter too: a
+  // schedule tuned for one kernel is not valid for another
+  std::string s = "sms" + std::to_string(b->sms) + "p" + std::to_string((int)b->p[0].precision) + "w" +
+                  std::to_string((int)b->wide) + "o" + std::to_string(b->occ_max);
   for (auto& x : parts) s += "," + x;
   return s;
 }
