@@ -126,12 +126,12 @@ int device_sms() {
   return sms;
 }
 
-// Grid: two 256-thread CTAs per SM (register bound), never more than the tiles.
+// Grid: one 256-thread CTA per SM (register bound), never more than the tiles.
 // wtc_bytes: B operand images of the tiled tensor-core pass (0: none).
 Layout make_layout(int64_t m, int T, int sms, bool wide, size_t wtc_bytes = 0) {
   Layout L;
   const int64_t ntiles = (m + kTile - 1) / kTile;
-  int64_t grid = std::min<int64_t>(ntiles, (int64_t)std::max(sms, 1) * 2);
+  int64_t grid = std::min<int64_t>(ntiles, (int64_t)std::max(sms, 1) * kPassCtasPerSm);
   grid = std::min<int64_t>(grid, (int64_t)kGroup * kMaxGroups);
   L.grid = (int)std::max<int64_t>(grid, 1);
   L.ws_grid = (int)std::max<int64_t>(std::min<int64_t>((m + 127) / 128, std::max(sms, 1)), 1);

@@ -29,6 +29,7 @@ constexpr int kMaxTW = 224;          // largest frame count of the wide (shared-
 constexpr int kWideLogSweeps = 30;   // Jacobi sweeps one wide eigen-step may take (and log)
 constexpr int kPassThreads = 256;    // one pixel per thread per tile
 constexpr int kTile = kPassThreads;  // pixels per CTA tile
+constexpr int kPassCtasPerSm = 1;    // resident CTAs of the narrow passes per SM
 constexpr int kGroup = 16;           // CTAs per first-level reduction group
 constexpr int kMaxGroups = 64;
 

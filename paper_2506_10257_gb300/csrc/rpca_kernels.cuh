@@ -21,7 +21,7 @@ struct BoolC {
 // Z = X - S + Y/mu, formed identically wherever it is needed, so that the Gram
 // accumulated in one pass belongs to exactly the Z the next pass uses.
 __device__ __forceinline__ float form_z(float x, float s, float y, float inv_mu) {
-  return (x - s) + y * inv_mu;
+  return fmaf(y, inv_mu, x - s);
 }
 
 // Whether the solve has ended, as one value for the whole CTA (thread 0
@@ -95,6 +95,21 @@ __device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
   asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
   return d;
 }
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
 
 // out[j] = sum_t z[t] M[t][j] for a TB x TB row-major shared-memory matrix M
 // (16-byte aligned rows), summed over t in increasing order.  Each step t is
@@ -121,6 +136,25 @@ __device__ __forceinline__ void vec_mat(const float (&z)[TB], const float* M, fl
     const float2 h = f2_unpack(acc[i]);
     out[2 * i] = h.x;
     out[2 * i + 1] = h.y;
+  }
+}
+
+// vec_mat with the result left as (out[2i], out[2i+1]) pairs, for callers that
+// continue in paired arithmetic.
+template <int TB>
+__device__ __forceinline__ void vec_mat2(const float (&z)[TB], const float* M, uint64_t (&acc)[TB / 2]) {
+#pragma unroll
+  for (int i = 0; i < TB / 2; ++i) acc[i] = 0;  // (+0.f, +0.f)
+#pragma unroll
+  for (int t = 0; t < TB; ++t) {
+    const uint64_t zz = f2_pack(z[t], z[t]);
+    const float4* row = reinterpret_cast<const float4*>(M + t * TB);
+#pragma unroll
+    for (int k = 0; k < TB / 4; ++k) {
+      const float4 w = row[k];
+      acc[2 * k] = f2_fma(zz, f2_pack(w.x, w.y), acc[2 * k]);
+      acc[2 * k + 1] = f2_fma(zz, f2_pack(w.z, w.w), acc[2 * k + 1]);
+    }
   }
 }
 
@@ -459,6 +493,9 @@ __device__ bool pass_body(Bufs b, int lc, int nc, unsigned char* dsm) {
 #pragma unroll
   for (int i = 0; i < 16; ++i) acc[i] = 0.f;
   float e2 = 0.f, l1 = 0.f;
+  uint64_t e2p = 0;  // residual sums of the paired (exact) tiles, per lane
+  const uint64_t inv_mu2 = f2_pack(inv_mu, inv_mu), f_mu2 = f2_pack(f_mu, f_mu);
+  const uint64_t inv_nxt2 = f2_pack(inv_mu_nxt, inv_mu_nxt);
 
   const int64_t ntiles = (m + kTile - 1) / kTile;
   // One tile.  EXACT: the window has exactly TB frames, the tile lies inside
@@ -481,6 +518,60 @@ __device__ bool pass_body(Bufs b, int lc, int nc, unsigned char* dsm) {
         l1 += fabsf(x);
       }
       if (tile + nc < ntiles) prefetch_tile_l2(job, Yin, m, T, (tile + nc) * kTile, true);
+    } else if constexpr (EXACT) {
+      // the same arithmetic as below on (frame 2i, frame 2i+1) pairs, two
+      // lanes per instruction (add/sub/mul/fma.rn.f32x2 round each lane as
+      // the scalar operation does)
+      uint64_t s2[TB / 2], d2[TB / 2], z2[TB / 2];
+#pragma unroll
+      for (int i = 0; i < TB / 2; ++i) {
+        const int64_t o0 = (int64_t)(2 * i) * m + p, o1 = o0 + m;
+        const uint64_t x2 = f2_pack(job.X[o0], job.X[o1]);
+        s2[i] = f2_pack(job.S[o0], job.S[o1]);
+        const uint64_t y2 = f2_pack(Yin[o0], Yin[o1]);
+        d2[i] = f2_mul(y2, inv_mu2);
+        z2[i] = f2_fma(y2, inv_mu2, f2_sub(x2, s2[i]));   // form_z per lane
+      }
+      float z[TB];
+#pragma unroll
+      for (int i = 0; i < TB / 2; ++i) {
+        const float2 h = f2_unpack(z2[i]);
+        z[2 * i] = h.x;
+        z[2 * i + 1] = h.y;
+      }
+      if (MODE == PM_GRAM) {
+        if (tile + nc < ntiles) prefetch_tile_l2(job, Yin, m, T, (tile + nc) * kTile, false);
+        vec_mat<TB>(z, sV, zt);
+      } else {
+        uint64_t q2[TB / 2];
+        vec_mat2<TB>(z, sW, q2);   // (Z Wbar)_j
+#pragma unroll
+        for (int i = 0; i < TB / 2; ++i) {
+          const uint64_t r2 = f2_add(s2[i], q2[i]);                      // X - L + Y/mu
+          const float2 r = f2_unpack(r2);
+          const uint64_t c2 = f2_pack(fminf(fmaxf(r.x, -gamma), gamma),  // clip to +-lambda/mu
+                                      fminf(fmaxf(r.y, -gamma), gamma));
+          const float2 sn = f2_unpack(f2_sub(r2, c2));                   // Eq. 5
+          const uint64_t yn2 = f2_mul(f_mu2, c2);                        // Eq. 6
+          const float2 yn = f2_unpack(yn2);
+          const uint64_t e = f2_sub(c2, d2[i]);                          // X - L - S'
+          e2p = f2_fma(e, e, e2p);
+          const int64_t o0 = (int64_t)(2 * i) * m + p, o1 = o0 + m;
+          job.S[o0] = sn.x;
+          job.S[o1] = sn.y;
+          Yout[o0] = yn.x;
+          Yout[o1] = yn.y;
+          // Z' = X - S' + Y'/mu' with X = Z + S - Y/mu and S' = S + Q - clip
+          const float2 zn = f2_unpack(f2_fma(yn2, inv_nxt2, f2_add(f2_sub(f2_sub(z2[i], d2[i]), q2[i]), c2)));
+          z[2 * i] = zn.x;
+          z[2 * i + 1] = zn.y;
+        }
+        // S and Y of this tile are written; the next tile's rows can come
+        if (tile + nc < ntiles) prefetch_tile_l2(job, Yin, m, T, (tile + nc) * kTile, false);
+        if (MODE == PM_FUSED) {
+          vec_mat<TB>(z, sV, zt);
+        }
+      }
     } else {
       // z = X - S + Y/mu for this pixel row (the argument of Eq. 4); X itself
       // is not kept (Z' below needs only Z, Y/mu, Q and the clip)
@@ -547,15 +638,21 @@ __device__ bool pass_body(Bufs b, int lc, int nc, unsigned char* dsm) {
       tile_body(BoolC<false>{}, tile, parity);
   }
   if (kGram) __syncthreads();  // the last tile's Gram reads are done before the scratch reuse
+  {
+    const float2 h = f2_unpack(e2p);
+    e2 += h.x + h.y;
+  }
 
   return pass_epilogue<TB, kGram>(b, acc, e2, l1, sZ, sRed, sScal, &sLast, gthr, ggrp, gblk, lc, nc);
 }
 
-// Two CTAs per SM (128 registers a thread) hide more HBM latency than one CTA
-// with all 255; at 32 frames the cap would spill, so that bucket keeps one.
+// One CTA of 256 threads per SM with up to 255 registers a thread: the exact
+// form of the tile body keeps all of a pixel row's loads in flight at once,
+// which a 128-register cap (two CTAs per SM) turns into spills; the L2
+// prefetch of the next tile covers the latency a second CTA would hide.
 template <int TB>
 __host__ __device__ constexpr int pass_min_blocks() {
-  return TB <= 24 ? 2 : 1;
+  return 1;
 }
 
 template <int TB, int MODE>

@@ -152,7 +152,8 @@ extern "C" rpca_status rpca_gram_noalloc(const float* X, int64_t m, int32_t T, c
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return na_status(e);
   const int64_t ntiles = (m + kTile - 1) / kTile;
-  int64_t grid = ntiles < (int64_t)2 * sms ? ntiles : (int64_t)2 * sms;
+  const int64_t cap = (int64_t)kPassCtasPerSm * sms;
+  int64_t grid = ntiles < cap ? ntiles : cap;
   if (grid > kNaMaxGrid) grid = kNaMaxGrid;
   if (grid < 1) grid = 1;
 
