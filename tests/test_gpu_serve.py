@@ -217,8 +217,14 @@ def test_served_default_chain_of_100_windows_matches_cold_oracle(rp):
         L, S = L.cpu().numpy(), S.cpu().numpy()
         ref = O.rpca_frames(F)
         assert st == rp.OK
+        assert abs(res["iters"] - ref.iters) <= 1, (k, res["iters"], ref.iters)
+        if res["iters"] != ref.iters:
+            # the residual sits within rounding of the tolerance (the Sec. II-A
+            # stopping test decides one iteration either way): compare with the
+            # oracle run to the GPU's iteration count
+            ref = O.rpca_frames(F, max_iter=res["iters"], tol=1e-30)
         eL, eS = rel(L, ref.L), rel(S, ref.S)
-        assert eL <= FP32_TOL and eS <= FP32_TOL, (k, eL, eS)
+        assert eL <= FP32_TOL and eS <= FP32_TOL, (k, eL, eS, res["iters"], ref.iters)
         img = O.temporal_mean_abs(ref.L)
         th = O.mask_threshold(img, w.bound_mask_gt)
         d = O.dice(O.bound_mask(O.temporal_mean_abs(L), th), O.bound_mask(img, th))
