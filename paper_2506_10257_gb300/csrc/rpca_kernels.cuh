@@ -62,6 +62,16 @@ struct GramMap {
   static_assert(NBLK * NGRP <= kPassThreads, "gram blocks exceed the CTA");
 };
 
+// The same blocks when every warp accumulates the Gram of its own 32-pixel
+// slices: G lanes (pixel groups) per block, NGRP groups in a CTA.
+template <int TB>
+struct WarpGramMap {
+  static constexpr int NBLK = GramMap<TB>::NBLK;
+  static constexpr int G = NBLK >= 32 ? 1 : 32 / NBLK;
+  static constexpr int NGRP = (kPassThreads / 32) * G;
+  static_assert(NBLK <= 32, "gram blocks exceed a warp");
+};
+
 __device__ __forceinline__ void blk_coords(int blk, int nb, int& bi, int& bj) {
   bi = 0;
   bj = 0;
@@ -361,7 +371,7 @@ __device__ __forceinline__ void gram_tile(const float* sZ, float (&acc)[16], int
 // End of a pass (all threads of the CTA): write this CTA's partial Gram and
 // scalar sums, then the two-level last-arriving-CTA reduction (fixed order)
 // that leaves the final Gram in red->G and the sums in red->e2, red->l1.
-template <int TB, bool kGram>
+template <int TB, bool kGram, int NGRP = GramMap<TB>::NGRP>
 __device__ __forceinline__ bool pass_epilogue(Bufs b, const float (&acc)[16], float e2, float l1, float* sZ,
                                               double (*sRed)[kPassThreads / 32], double* sScal, int* sLastp,
                                               bool gthr, int ggrp, int gblk, int lc, int nc) {
@@ -379,7 +389,7 @@ __device__ __forceinline__ bool pass_epilogue(Bufs b, const float (&acc)[16], fl
     __syncthreads();
     for (int e = tid; e < GM::NBLK * 16; e += kPassThreads) {
       float sum = 0.f;
-      for (int g = 0; g < GM::NGRP; ++g) sum += red[g * GM::NBLK * 16 + e];
+      for (int g = 0; g < NGRP; ++g) sum += red[g * GM::NBLK * 16 + e];
       int ebi, ebj;
       blk_coords(e / 16, GM::NB, ebi, ebj);
       const int a = 4 * ebi + (e % 16) / 4, c = 4 * ebj + (e % 4);
@@ -485,8 +495,21 @@ __device__ bool pass_body(Bufs b, int lc, int nc, unsigned char* dsm) {
   }
   __syncthreads();
 
-  const bool gthr = kGram && (tid < GM::NBLK * GM::NGRP);
-  const int gblk = tid % GM::NBLK, ggrp = tid / GM::NBLK;
+  // Warp tiles (up to 24 frames): warp w owns the 32-pixel slice [32w, 32w+32)
+  // of every tile, stages its Z~ rows in a buffer of its own and adds them to
+  // Gram blocks held by its own lanes, so the warps need no barrier between
+  // tiles and drift apart (one warp's loads are in flight while another
+  // computes).  At 32 frames the blocks outnumber a warp's lanes, and the CTA
+  // shares its tiles' rows through one barrier per tile.
+  constexpr bool kWarpTiles = GM::NBLK <= 32 && TB <= 24;
+  using WG = WarpGramMap<(TB <= 24 ? TB : 8)>;
+  constexpr int kNgrp = kWarpTiles ? WG::NGRP : GM::NGRP;
+  static_assert((size_t)kNgrp * GM::NBLK * 16 <= 2 * (size_t)kTile * ZS, "Gram scratch exceeds the staging region");
+  const int lane = tid & 31, warp = tid >> 5;
+  const bool gthr = kGram && (kWarpTiles ? lane < GM::NBLK * WG::G : tid < GM::NBLK * GM::NGRP);
+  const int gblk = kWarpTiles ? lane % GM::NBLK : tid % GM::NBLK;
+  const int glocal = kWarpTiles ? lane / GM::NBLK : tid / GM::NBLK;   // pixel group within the warp / CTA
+  const int ggrp = kWarpTiles ? warp * WG::G + glocal : glocal;
   int bi, bj;
   blk_coords(gblk, GM::NB, bi, bj);
   float acc[16];
@@ -498,6 +521,26 @@ __device__ bool pass_body(Bufs b, int lc, int nc, unsigned char* dsm) {
   const uint64_t inv_nxt2 = f2_pack(inv_mu_nxt, inv_mu_nxt);
 
   const int64_t ntiles = (m + kTile - 1) / kTile;
+  // L2 prefetch of this thread's part of the CTA's next tile (this warp's
+  // slice of it in the warp-tile form)
+  auto prefetch_next = [&](int64_t tile, bool xonly) {
+    const int64_t nt = tile + nc;
+    if (nt >= ntiles) return;
+    if constexpr (kWarpTiles) {
+      const int64_t s0 = nt * kTile + 32 * warp;
+      if (s0 >= m) return;
+      for (int t = lane; t < T; t += 32) {
+        const int64_t off = (int64_t)t * m + s0;
+        prefetch_l2(job.X + off);
+        if (!xonly) {
+          prefetch_l2(job.S + off);
+          prefetch_l2(Yin + off);
+        }
+      }
+    } else {
+      prefetch_tile_l2(job, Yin, m, T, nt * kTile, xonly);
+    }
+  };
   // One tile.  EXACT: the window has exactly TB frames, the tile lies inside
   // the window and S, Y are read (not the first iteration), so the frame and
   // pixel guards are compile-time true: the guarded form spends about 500
@@ -517,7 +560,7 @@ __device__ bool pass_body(Bufs b, int lc, int nc, unsigned char* dsm) {
         e2 = fmaf(x, x, e2);
         l1 += fabsf(x);
       }
-      if (tile + nc < ntiles) prefetch_tile_l2(job, Yin, m, T, (tile + nc) * kTile, true);
+      prefetch_next(tile, true);
     } else if constexpr (EXACT) {
       // the same arithmetic as below on (frame 2i, frame 2i+1) pairs, two
       // lanes per instruction (add/sub/mul/fma.rn.f32x2 round each lane as
@@ -540,7 +583,7 @@ __device__ bool pass_body(Bufs b, int lc, int nc, unsigned char* dsm) {
         z[2 * i + 1] = h.y;
       }
       if (MODE == PM_GRAM) {
-        if (tile + nc < ntiles) prefetch_tile_l2(job, Yin, m, T, (tile + nc) * kTile, false);
+        prefetch_next(tile, false);
         vec_mat<TB>(z, sV, zt);
       } else {
         uint64_t q2[TB / 2];
@@ -567,7 +610,7 @@ __device__ bool pass_body(Bufs b, int lc, int nc, unsigned char* dsm) {
           z[2 * i + 1] = zn.y;
         }
         // S and Y of this tile are written; the next tile's rows can come
-        if (tile + nc < ntiles) prefetch_tile_l2(job, Yin, m, T, (tile + nc) * kTile, false);
+        prefetch_next(tile, false);
         if (MODE == PM_FUSED) {
           vec_mat<TB>(z, sV, zt);
         }
@@ -586,7 +629,7 @@ __device__ bool pass_body(Bufs b, int lc, int nc, unsigned char* dsm) {
         z[t] = form_z(x, s[t], y, inv_mu);
       }
       if (MODE == PM_GRAM) {
-        if (tile + nc < ntiles) prefetch_tile_l2(job, Yin, m, T, (tile + nc) * kTile, frst);
+        prefetch_next(tile, frst);
         vec_mat<TB>(z, sV, zt);
       } else {
         float q[TB];
@@ -609,22 +652,34 @@ __device__ bool pass_body(Bufs b, int lc, int nc, unsigned char* dsm) {
           }
         }
         // S and Y of this tile are written; the next tile's rows can come
-        if (tile + nc < ntiles) prefetch_tile_l2(job, Yin, m, T, (tile + nc) * kTile, frst);
+        prefetch_next(tile, frst);
         if (MODE == PM_FUSED) {
           vec_mat<TB>(z, sV, zt);
         }
       }
     }
     if (kGram) {
-      // one barrier per tile: the next tile stages into the other buffer, and
-      // this tile's barrier orders the buffer's reuse two tiles later
-      float* zb = sZ + parity * kTile * ZS;
-      float4* dst = reinterpret_cast<float4*>(&zb[tid * ZS]);
+      if constexpr (kWarpTiles) {
+        // this warp's rows only: warp-level ordering around its own buffer
+        float* zb = sZ + warp * 32 * ZS;
+        float4* dst = reinterpret_cast<float4*>(&zb[lane * ZS]);
 #pragma unroll
-      for (int j4 = 0; j4 < TB / 4; ++j4)
-        dst[j4] = make_float4(zt[4 * j4], zt[4 * j4 + 1], zt[4 * j4 + 2], zt[4 * j4 + 3]);
-      __syncthreads();
-      if (gthr) gram_tile<TB>(zb, acc, ggrp, bi, bj);
+        for (int j4 = 0; j4 < TB / 4; ++j4)
+          dst[j4] = make_float4(zt[4 * j4], zt[4 * j4 + 1], zt[4 * j4 + 2], zt[4 * j4 + 3]);
+        __syncwarp();
+        if (gthr) gram_rows<TB, 32, WG::G>(zb, acc, glocal, bi, bj);
+        __syncwarp();
+      } else {
+        // one barrier per tile: the next tile stages into the other buffer, and
+        // this tile's barrier orders the buffer's reuse two tiles later
+        float* zb = sZ + parity * kTile * ZS;
+        float4* dst = reinterpret_cast<float4*>(&zb[tid * ZS]);
+#pragma unroll
+        for (int j4 = 0; j4 < TB / 4; ++j4)
+          dst[j4] = make_float4(zt[4 * j4], zt[4 * j4 + 1], zt[4 * j4 + 2], zt[4 * j4 + 3]);
+        __syncthreads();
+        if (gthr) gram_tile<TB>(zb, acc, glocal, bi, bj);
+      }
     }
   };
   // the exact form serves the iterations of windows whose frame count is the
@@ -632,7 +687,9 @@ __device__ bool pass_body(Bufs b, int lc, int nc, unsigned char* dsm) {
   const bool exact_ok = MODE != PM_INIT && T == TB && !first;
   int parity = 0;  // staging buffer of this tile
   for (int64_t tile = lc; tile < ntiles; tile += nc, parity ^= 1) {
-    if (exact_ok && (tile + 1) * kTile <= m)
+    // (uniform over the warp in the warp-tile form, over the CTA otherwise)
+    const int64_t end = kWarpTiles ? tile * kTile + 32 * (warp + 1) : (tile + 1) * kTile;
+    if (exact_ok && end <= m)
       tile_body(BoolC<true>{}, tile, parity);
     else
       tile_body(BoolC<false>{}, tile, parity);
@@ -643,7 +700,7 @@ __device__ bool pass_body(Bufs b, int lc, int nc, unsigned char* dsm) {
     e2 += h.x + h.y;
   }
 
-  return pass_epilogue<TB, kGram>(b, acc, e2, l1, sZ, sRed, sScal, &sLast, gthr, ggrp, gblk, lc, nc);
+  return pass_epilogue<TB, kGram, kNgrp>(b, acc, e2, l1, sZ, sRed, sScal, &sLast, gthr, ggrp, gblk, lc, nc);
 }
 
 // One CTA of 256 threads per SM with up to 255 registers a thread: the exact
