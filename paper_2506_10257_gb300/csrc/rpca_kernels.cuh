@@ -448,11 +448,33 @@ __device__ __forceinline__ void prefetch_tile_l2(const Job& job, const float* Yi
   }
 }
 
-// dynamic shared memory of pass_body: Wbar, V and two staging buffers for the
-// tiles' Z~ rows
+// Frame counts up to this bucket copy the fused pass's next tile into shared
+// memory while the current one is computed (two stages of every thread's X,
+// S, Y values: 123 KB at 20 frames).
+constexpr int kRowsMaxTB = 20;
+template <int TB>
+__host__ __device__ constexpr size_t pass_rows_bytes() {
+  return TB <= kRowsMaxTB ? sizeof(float) * 2 * 3 * (size_t)TB * kTile : 0;
+}
+
+// dynamic shared memory of pass_body: Wbar, V, two staging buffers for the
+// tiles' Z~ rows and the row stages
 template <int TB>
 __host__ __device__ constexpr size_t pass_simt_smem() {
-  return sizeof(float) * (2 * (size_t)TB * TB + 2 * (size_t)kTile * (TB + 4));
+  return sizeof(float) * (2 * (size_t)TB * TB + 2 * (size_t)kTile * (TB + 4)) + pass_rows_bytes<TB>();
+}
+
+// One 4-byte asynchronous copy global -> shared memory (cp.async), and the
+// per-thread group bookkeeping that orders it before this thread's reads.
+__device__ __forceinline__ void cp_async4(float* sdst, const float* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)),
+               "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 // One pass over the pixels of this CTA (number lc of nc); `dsm` holds
@@ -467,6 +489,7 @@ __device__ bool pass_body(Bufs b, int lc, int nc, unsigned char* dsm) {
   float* sW = reinterpret_cast<float*>(dsm);    // Wbar, row-major TB x TB (zero outside T)
   float* sV = sW + TB * TB;                     // V
   float* sZ = sV + TB * TB;                     // [2][kTile][ZS]: tiles alternate buffers
+  float* sRows = sZ + 2 * kTile * ZS;           // [2][X|S|Y][TB][kTile]: row stages (async form)
   __shared__ double sRed[2][kPassThreads / 32];
   __shared__ double sScal[2 * kMaxGroups];
   __shared__ int sLast;
@@ -545,8 +568,14 @@ __device__ bool pass_body(Bufs b, int lc, int nc, unsigned char* dsm) {
   // the window and S, Y are read (not the first iteration), so the frame and
   // pixel guards are compile-time true: the guarded form spends about 500
   // more instructions per pixel row on predicates and branches (measured).
-  auto tile_body = [&](auto exact_c, int64_t tile, int parity) {
+  // Async form (warp tiles, fused pass, exact tiles): every thread copies its
+  // pixel row of the CTA's next tile (X, S, Y) into its own column of a
+  // shared-memory stage with cp.async while it computes the current tile, so
+  // a tile's loads are on chip when it starts, at no register cost.
+  constexpr bool kAsyncRows = kWarpTiles && MODE == PM_FUSED && pass_rows_bytes<TB>() > 0;
+  auto tile_body = [&](auto exact_c, int64_t tile, int parity, int st) {
     constexpr bool EXACT = decltype(exact_c)::value;
+    constexpr bool ROWS = EXACT && kAsyncRows;  // this tile's rows are in stage st
     const int TT = EXACT ? TB : T;
     const bool frst = EXACT ? false : first;
     const int64_t p = tile * kTile + tid;
@@ -566,12 +595,20 @@ __device__ bool pass_body(Bufs b, int lc, int nc, unsigned char* dsm) {
       // lanes per instruction (add/sub/mul/fma.rn.f32x2 round each lane as
       // the scalar operation does)
       uint64_t s2[TB / 2], d2[TB / 2], z2[TB / 2];
+      const float* rx = sRows + (size_t)st * 3 * TB * kTile + tid;
 #pragma unroll
       for (int i = 0; i < TB / 2; ++i) {
         const int64_t o0 = (int64_t)(2 * i) * m + p, o1 = o0 + m;
-        const uint64_t x2 = f2_pack(job.X[o0], job.X[o1]);
-        s2[i] = f2_pack(job.S[o0], job.S[o1]);
-        const uint64_t y2 = f2_pack(Yin[o0], Yin[o1]);
+        uint64_t x2, y2;
+        if constexpr (ROWS) {
+          x2 = f2_pack(rx[(2 * i) * kTile], rx[(2 * i + 1) * kTile]);
+          s2[i] = f2_pack(rx[(TB + 2 * i) * kTile], rx[(TB + 2 * i + 1) * kTile]);
+          y2 = f2_pack(rx[(2 * TB + 2 * i) * kTile], rx[(2 * TB + 2 * i + 1) * kTile]);
+        } else {
+          x2 = f2_pack(job.X[o0], job.X[o1]);
+          s2[i] = f2_pack(job.S[o0], job.S[o1]);
+          y2 = f2_pack(Yin[o0], Yin[o1]);
+        }
         d2[i] = f2_mul(y2, inv_mu2);
         z2[i] = f2_fma(y2, inv_mu2, f2_sub(x2, s2[i]));   // form_z per lane
       }
@@ -610,7 +647,7 @@ __device__ bool pass_body(Bufs b, int lc, int nc, unsigned char* dsm) {
           z[2 * i + 1] = zn.y;
         }
         // S and Y of this tile are written; the next tile's rows can come
-        prefetch_next(tile, false);
+        if (!ROWS) prefetch_next(tile, false);
         if (MODE == PM_FUSED) {
           vec_mat<TB>(z, sV, zt);
         }
@@ -685,15 +722,41 @@ __device__ bool pass_body(Bufs b, int lc, int nc, unsigned char* dsm) {
   // the exact form serves the iterations of windows whose frame count is the
   // bucket's (the initial pass runs once and keeps the guarded form)
   const bool exact_ok = MODE != PM_INIT && T == TB && !first;
-  int parity = 0;  // staging buffer of this tile
-  for (int64_t tile = lc; tile < ntiles; tile += nc, parity ^= 1) {
-    // (uniform over the warp in the warp-tile form, over the CTA otherwise)
+  // (uniform over the warp in the warp-tile form, over the CTA otherwise)
+  auto exact_tile = [&](int64_t tile) {
     const int64_t end = kWarpTiles ? tile * kTile + 32 * (warp + 1) : (tile + 1) * kTile;
-    if (exact_ok && end <= m)
-      tile_body(BoolC<true>{}, tile, parity);
-    else
-      tile_body(BoolC<false>{}, tile, parity);
+    return exact_ok && tile < ntiles && end <= m;
+  };
+  // this thread's X, S, Y values of tile nt into row stage st
+  auto rows_issue = [&](int64_t nt, int st) {
+    const int64_t p = nt * kTile + tid;
+    float* dst = sRows + (size_t)st * 3 * TB * kTile + tid;
+#pragma unroll
+    for (int t = 0; t < TB; ++t) {
+      const int64_t o = (int64_t)t * m + p;
+      cp_async4(dst + (size_t)t * kTile, job.X + o);
+      cp_async4(dst + (size_t)(TB + t) * kTile, job.S + o);
+      cp_async4(dst + (size_t)(2 * TB + t) * kTile, Yin + o);
+    }
+  };
+  if constexpr (kAsyncRows) {
+    if (exact_tile(lc)) rows_issue(lc, 0);
+    cp_async_commit();
   }
+  int parity = 0;  // staging buffer of this tile
+  int st = 0;      // row stage of this tile (async form)
+  for (int64_t tile = lc; tile < ntiles; tile += nc, parity ^= 1, st ^= 1) {
+    if constexpr (kAsyncRows) {
+      if (exact_tile(tile + nc)) rows_issue(tile + nc, st ^ 1);
+      cp_async_commit();
+      cp_async_wait<1>();  // this tile's copies (all groups but the newest) have landed
+    }
+    if (exact_tile(tile))
+      tile_body(BoolC<true>{}, tile, parity, st);
+    else
+      tile_body(BoolC<false>{}, tile, parity, st);
+  }
+  if constexpr (kAsyncRows) cp_async_wait<0>();
   if (kGram) __syncthreads();  // the last tile's Gram reads are done before the scratch reuse
   {
     const float2 h = f2_unpack(e2p);
