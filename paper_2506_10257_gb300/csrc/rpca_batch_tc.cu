@@ -14,7 +14,7 @@ namespace rpca {
 #include "rpca_batch.cuh"
 
 // TMEM columns each CTA of a tensor-core batch holds for the whole launch
-// (Q and Z~ of the two 128-row halves of a 256-pixel tile at up to 32 frames).
+// (Q and Z~ of the two warpgroups at up to 32 frames).
 constexpr uint32_t kBatchTmemCols = 128;
 
 // The CTA's TMEM allocation (written by warp 0 at the start of the launch).

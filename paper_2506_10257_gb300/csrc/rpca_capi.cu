@@ -503,10 +503,12 @@ static rpca_status plan_create_impl(const rpca_params* p, void* workspace, size_
     }
     set_tc(p->T, &pl->ks);
   }
+  // The TMA-fed warp-specialised tensor-core pass is opt-in (RPCA_PASS_WS=1):
+  // pass_tc_kernel's independent warpgroups measured faster (262144 x 20,
+  // TF32x3: 41 against 54 us).  The TMA-fed FP32 pass is opt-in too
+  // (RPCA_PASS_TMA=1): the register-resident pass measured as fast or faster.
   pl->use_ws = !pl->wide && (p->precision != RPCA_PREC_FP32) && (p->m % 4 == 0) && tma_encoder() != nullptr &&
-               !(getenv("RPCA_NO_WS") && atoi(getenv("RPCA_NO_WS")) != 0);
-  // The TMA-fed FP32 pass is opt-in (RPCA_PASS_TMA=1): at 10..32 frames the
-  // register-resident pass with two CTAs per SM measured as fast or faster.
+               getenv("RPCA_PASS_WS") && atoi(getenv("RPCA_PASS_WS")) != 0;
   pl->use_fs = !pl->wide && (p->precision == RPCA_PREC_FP32) && (p->m % 4 == 0) && (p->m < ((int64_t)1 << 31)) &&
                tma_encoder() != nullptr && getenv("RPCA_PASS_TMA") && atoi(getenv("RPCA_PASS_TMA")) != 0;
   if (!pl->wide) {

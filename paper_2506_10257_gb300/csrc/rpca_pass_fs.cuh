@@ -48,10 +48,6 @@ struct FsShape {
   static_assert(NBLK * NGRP <= 128, "Gram blocks exceed a warpgroup");
 };
 
-__device__ __forceinline__ void mbar_inval(uint64_t* mbar) {
-  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(mbar)) : "memory");
-}
-
 // Waits (bounded) until the stage's last issued load is local tile j.
 __device__ __forceinline__ bool wait_issued(const int* issued, int j, uint32_t limit) {
   const volatile int* v = issued;

@@ -65,9 +65,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint32_t limit) {
   uint32_t done = 0;
   for (uint32_t it = 0; it < limit; ++it) {
-    // the thread may be suspended up to ~1 us inside try_wait instead of spinning
+    // the thread may be suspended inside try_wait (a system-dependent time)
+    // instead of spinning; it resumes when the phase completes
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 1000;\n selp.u32 %0, 1, 0, p;\n}"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
         : "=r"(done)
         : "r"(smem_u32(mbar)), "r"(parity));
     if (done) return true;
@@ -172,6 +173,12 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t b
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
+
+// Ends the life of an mbarrier whose phases are all complete, so that its
+// word can be initialised again.
+__device__ __forceinline__ void mbar_inval(uint64_t* mbar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(mbar)) : "memory");
 }
 
 // Barrier among `n` threads (a multiple of 32) with id 1..15.
