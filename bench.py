@@ -75,20 +75,20 @@ def _ncu_entry(name: str, kernel_src_hash: str):
     return e
 
 
-def ncu_traffic(kernel_src_hash: str):
+def ncu_traffic(kernel_src_hash: str, entry: str = "fused_pass"):
     """DRAM bytes per launch of the fused pass (committed ncu capture)."""
-    e = _ncu_entry("fused_pass", kernel_src_hash)
+    e = _ncu_entry(entry, kernel_src_hash)
     return float(e["dram_bytes_per_launch"]) if e else None
 
 
-def ncu_batch_traffic(kernel_src_hash: str, iters):
+def ncu_batch_traffic(kernel_src_hash: str, iters, entry: str = "batch_kernel"):
     """DRAM bytes of one persistent batch launch, from the committed ncu
     capture of the same kernel on windows of this workload: its bytes per
     window solve scaled to these windows by their iteration counts (a solve's
     traffic grows with its iterations: the initial and final steps read and
     write about 1 + 5 window arrays, each iteration 5).  None for another
     kernel source."""
-    e = _ncu_entry("batch_kernel", kernel_src_hash)
+    e = _ncu_entry(entry, kernel_src_hash)
     if not e:
         return None
     per_window, it0 = float(e["dram_bytes_per_window_solve"]), int(e["iters_per_window"])
@@ -435,7 +435,9 @@ def run_batch(args):
                               "CUDA events around each persistent launch (its descriptor copy and "
                               "control-block gather included), algorithmic bytes of all windows' solves",
                               traffic=ncu_batch_traffic(kernel_source_hash(), iters)
-                              if args.precision == "fp32" else None),
+                              if args.precision == "fp32" else
+                              ncu_batch_traffic(kernel_source_hash(), iters, "batch_kernel_tc_tf32x3")
+                              if args.precision == "tf32x3" else None),
         "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": NB * m * T * 4,
                 "d2h_bytes_per_step": NB * (2 * m * T * 4 + m), "steps": e2e_steps,
                 "api": "rpca_batch_solve_host (C ABI, pinned host buffers in and out)",
@@ -951,8 +953,10 @@ def run_ours(args):
         "gpu_launches": args.steps * launches_per_solve(args.drive, res["iters"]),
         "roofline": _roofline(alg_bytes, pass_us * 1e-6, _plan_pass_name(T, m, args),
                               "device global timer per launch over the timed solves",
-                              traffic=(ncu_traffic(src_hash) if (wl == "w512x512_t20" and not args.complex
-                                                                  and args.precision == "fp32") else None)),
+                              traffic=(ncu_traffic(src_hash, "fused_pass" if args.precision == "fp32" else
+                                                   "pass_tc_kernel_" + args.precision)
+                                       if (wl == "w512x512_t20" and not args.complex
+                                           and args.precision in ("fp32", "tf32x3")) else None)),
         "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": m * T * esz,
                 "d2h_bytes_per_step": 2 * m * T * esz + m + 48, "steps": e2e_steps},
         "clocks": clocks,

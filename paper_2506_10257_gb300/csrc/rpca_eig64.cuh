@@ -112,10 +112,13 @@ __device__ void eig64_body(Bufs b, int flags, cudaGraphConditionalHandle h, int 
   const int rj = rl % LPP;                                          // its part: 0 (p,p) [and (p,q) if LPP = 2],
                                                                     // 1 (q,q), 2 (p,q)
   const bool rlead = rwarp && rj == 0 && rk < K;
+  // The entries beyond the first NW (and the V items beyond the first NW) go
+  // to workers whose warps run on other sub-partitions than warp 0's, so
+  // the FP64 pipes of sub-partitions 0-2 carry about equal shares of a round.
   int ea[SH::EPT], ec[SH::EPT];
 #pragma unroll
   for (int u = 0; u < SH::EPT; ++u) {
-    int e = wi + u * NW, a = 0;
+    int e = (u == 0 ? wi : (wi + NW - 128) % NW) + u * NW, a = 0;
     ea[u] = -1;
     ec[u] = -1;
     if (worker && e < NE) {
@@ -213,7 +216,7 @@ __device__ void eig64_body(Bufs b, int flags, cudaGraphConditionalHandle h, int 
         // V <- V J on the round's pairs (each (row, pair) item touches only its two entries)
 #pragma unroll
         for (int u = 0; u < SH::VPT; ++u) {
-          const int item = wi + u * NW;
+          const int item = (u == 0 ? wi : (wi + NW - 64) % NW) + u * NW;
           if (item >= T * K) continue;
           const int r = item / K, k = item % K;
           const double2 r2 = S.cs[cb][k];
