@@ -730,16 +730,26 @@ __device__ __forceinline__ void wtc_images(const Bufs& b) {
 // ---------------------------------------------------------------------------
 // Eigen-step for wide windows (one CTA; the stand-alone kernel uses kEigWThreads threads).
 // ---------------------------------------------------------------------------
+// Windows up to this many frames keep D = Q - I (the product of the step's
+// rotations, minus I) in shared memory beside G and update it in every round
+// (each round's items are independent, so the CTA shares them); larger ones
+// log the rotations and replay them onto D after the sweeps, when G is
+// consumed.
+constexpr int kWideInlineDMaxT = 144;
+__host__ __device__ constexpr bool eig_wide_inline_d(int T) { return T <= kWideInlineDMaxT; }
+
 // The eigen-step on one CTA of any multiple of 32 threads; `eigw_smem` holds
 // eig_wide_smem(T, vrows) bytes.
 __host__ __device__ constexpr size_t eig_wide_smem(int T, int vrows) {
-  return sizeof(float) * ((size_t)(T + (T & 1)) * (T + (T & 1) + 1) + (size_t)vrows * T);
+  return sizeof(float) * ((size_t)(eig_wide_inline_d(T) ? 2 : 1) * (T + (T & 1)) * (T + (T & 1) + 1) +
+                          (size_t)vrows * T);
 }
 
 static __device__ void eig_wide_body(Bufs b, int flags, cudaGraphConditionalHandle h, int use_cond, float* eigw_smem,
                               int vrows) {
   __shared__ float sC[kMaxTW / 2], sSn[kMaxTW / 2];
   __shared__ float sDp[kMaxTW / 2], sDq[kMaxTW / 2];
+  __shared__ float sCm1[kMaxTW / 2];  // c - 1 = -s^2 / (1 + c) of every pair slot of the round
   __shared__ double sEv[kMaxTW];
   __shared__ float sG[kMaxTW];
   __shared__ int sAct[kMaxTW / 2], sPos[kMaxTW / 2];
@@ -755,6 +765,9 @@ static __device__ void eig_wide_body(Bufs b, int flags, cudaGraphConditionalHand
   const int K = Te / 2;
   const int LD = Te + 1;
   float* G = eigw_smem;          // [Te][LD]
+  const bool inline_d = eig_wide_inline_d(T);
+  float* Dn = eigw_smem + (size_t)Te * LD;  // [Te][LD]: D = Q - I, updated per round (inline_d)
+  float* after = eigw_smem + (size_t)(inline_d ? 2 : 1) * Te * LD;  // staging beyond G (and D)
   const unsigned long long t0 = gtimer();
   if (!eig_control(b, flags, h, use_cond, &sFlag)) return;
   const bool cold = (flags & EF_INIT) != 0;
@@ -765,6 +778,8 @@ static __device__ void eig_wide_body(Bufs b, int flags, cudaGraphConditionalHand
   }
   if (cold)
     for (int i = tid; i < T * T; i += nthr) b.Vw[i] = (i / T == i % T) ? 1.f : 0.f;
+  if (inline_d)
+    for (int i = tid; i < Te * LD; i += nthr) Dn[i] = 0.f;
   __syncthreads();  // (global writes of the block are visible to its later reads)
   const unsigned long long t1 = gtimer();
 
@@ -813,6 +828,7 @@ static __device__ void eig_wide_body(Bufs b, int flags, cudaGraphConditionalHand
         }
         sC[tid] = c;
         sSn[tid] = s;
+        sCm1[tid] = -s * s / (1.f + c);
         sDp[tid] = dp;
         sDq[tid] = dq;
         sPair[tid] = make_int4(p, q, __float_as_int(c), __float_as_int(s));
@@ -839,12 +855,14 @@ static __device__ void eig_wide_body(Bufs b, int flags, cudaGraphConditionalHand
         off += __popc(bal & ((1u << (tid & 31)) - 1u));
         sAct[off] = tid;
         sPos[tid] = off;
-        // the replay needs the pair's columns and where each round starts
-        const int4 pr = sPair[tid];
-        log_k[logged + off] = pr.x | (pr.y << 8) | (off == 0 ? (1 << 16) : 0);
-        log_cs[logged + off] = make_float2(sC[tid], sSn[tid]);
+        if (!inline_d) {
+          // the replay needs the pair's columns and where each round starts
+          const int4 pr = sPair[tid];
+          log_k[logged + off] = pr.x | (pr.y << 8) | (off == 0 ? (1 << 16) : 0);
+          log_cs[logged + off] = make_float2(sC[tid], sSn[tid]);
+        }
       }
-      if (tid == 0) {
+      if (tid == 0 && !inline_d) {
         log_rnd[2 * rounds_run] = rnd;
         log_rnd[2 * rounds_run + 1] = na;
       }
@@ -891,6 +909,32 @@ static __device__ void eig_wide_body(Bufs b, int flags, cudaGraphConditionalHand
         G[qC * LD + qA] = n11;
         }
       }
+      if (inline_d) {
+        // D' = D J + (J - I) on the round's rotated pairs: (row r, rotated
+        // pair) touches D[r][p] and D[r][q] only; lane = rotated pair, warp =
+        // rows
+        const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
+        for (int ai = lane; ai < na; ai += 32) {
+          const int A = sAct[ai];
+          const int4 pr = sPair[A];
+          const int p = pr.x, q = pr.y;
+          const float c = __int_as_float(pr.z), sn = __int_as_float(pr.w), cm1 = sCm1[A];
+          for (int r = warp; r < T; r += nwarps) {
+            float* dr = &Dn[r * LD];
+            const float dp = dr[p], dq = dr[q];
+            float np = fmaf(c, dp, -sn * dq), nq = fmaf(sn, dp, c * dq);
+            if (r == p) {
+              np += cm1;
+              nq += sn;
+            } else if (r == q) {
+              np -= sn;
+              nq += cm1;
+            }
+            dr[p] = np;
+            dr[q] = nq;
+          }
+        }
+      }
       __syncthreads();
     }
     ++sweeps;
@@ -899,11 +943,13 @@ static __device__ void eig_wide_body(Bufs b, int flags, cudaGraphConditionalHand
   if (tid < T) sEv[tid] = (double)G[tid * LD + tid];
   __syncthreads();
 
-  // ---- Q = J_1 J_2 ... from the logged rounds, kept as D = Q - I (over the
-  //      consumed G): near the identity D is small, so its rounding errors
-  //      are relative to small entries; then V <- V + V D ----
-  float* D = G;  // [T][LD]
-  for (int i = tid; i < T * LD; i += nthr) D[i] = 0.f;
+  // ---- Q = J_1 J_2 ... kept as D = Q - I: near the identity D is small, so
+  //      its rounding errors are relative to small entries; then V <- V + V D.
+  //      Inline: D is already complete; else replay the logged rounds onto D
+  //      over the consumed G ----
+  float* D = inline_d ? Dn : G;  // [T][LD]
+  if (!inline_d)
+    for (int i = tid; i < T * LD; i += nthr) D[i] = 0.f;
   // The rows of D are independent (D' = D J + (J - I) mixes columns p and q
   // of each row) and warp w owns rows w, w + nwarps, ..., so between rounds
   // only a warp has to wait for itself.  The CTA stages the log a chunk at a
@@ -911,9 +957,9 @@ static __device__ void eig_wide_body(Bufs b, int flags, cudaGraphConditionalHand
   // below; one barrier per chunk); each warp walks the chunk 32 entries at a
   // time, lane = rotation, and applies the rotations of one round (a run of
   // entries starting at a flagged one) before those of the next.
-  {
+  if (!inline_d) {
     const int nwarps = nthr >> 5, warp = tid >> 5, lane = tid & 31;
-    float2* stc = reinterpret_cast<float2*>(eigw_smem + (size_t)Te * LD);
+    float2* stc = reinterpret_cast<float2*>(after);
     const int E = max(1, (vrows * T * (int)sizeof(float)) / (int)(sizeof(float2) + sizeof(int)));
     int* stp = reinterpret_cast<int*>(stc + E);
     for (int c0 = 0; c0 < logged; c0 += E) {
@@ -961,7 +1007,7 @@ static __device__ void eig_wide_body(Bufs b, int flags, cudaGraphConditionalHand
   }
   __syncthreads();
   // V <- V + V D, vrows rows of V at a time staged after D
-  float* sVo = eigw_smem + (size_t)Te * LD;  // [vrows][T]
+  float* sVo = after;  // [vrows][T]
   for (int r0 = 0; r0 < T; r0 += vrows) {
     const int nr = min(vrows, T - r0);
     for (int i = tid; i < nr * T; i += nthr) sVo[i] = __ldcg(&b.Vw[(size_t)r0 * T + i]);
