@@ -104,6 +104,13 @@ def test_tensor_core_tf32x3_odd_pixel_count(rp):
     check(rp, (509, 515, 20, 3), "TF32X3")
 
 
+def test_fp32_odd_pixel_count(rp):
+    # 262135 pixels: every tile but the last takes the exact form (row stages,
+    # paired arithmetic), the last one the guarded form, and a warp's slice of
+    # it ends inside the window, all in one pass
+    check(rp, (509, 515, 20, 3), "FP32")
+
+
 def test_plain_tf32_is_not_offered(rp):
     # one TF32 product per contraction misses the 1e-4 bound (7.1e-4 measured
     # on the 262144 x 20 window), so plans reject it
