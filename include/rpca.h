@@ -49,8 +49,9 @@ typedef enum {
 /* Element type of X, L, S.  R32: float32 envelope/RF data.  C64: complex64 IQ
  * data, (Re, Im) float pairs, frame-major; the SVT then acts on the Hermitian
  * Gram Z^H Z and the shrink of Eq. 5 on each entry's magnitude (phase kept).
- * C64 needs precision FP32 and 2 T <= RPCA_MAX_T (the solver works on the
- * interleaved real embedding with 2 T columns). */
+ * C64 needs 2 T <= RPCA_MAX_T (the solver works on the interleaved real
+ * embedding with 2 T columns), and 2 T <= 128 for the tensor-core precisions
+ * (plans; batches of complex windows run FP32). */
 typedef enum { RPCA_R32 = 0, RPCA_C64 = 1 } rpca_dtype;
 
 /* Arithmetic of the two dense contractions per iteration (Z*Wbar and the

@@ -188,7 +188,10 @@ rpca_status validate(const rpca_params* p) {
   if (p->drive != RPCA_DRIVE_GRAPH && p->drive != RPCA_DRIVE_HOST && p->drive != RPCA_DRIVE_STREAM)
     return RPCA_ERR_ARG;
   if (p->dtype != RPCA_R32 && p->dtype != RPCA_C64) return RPCA_ERR_ARG;
-  if (p->dtype == RPCA_C64 && (2 * p->T > kMaxTW || p->precision != RPCA_PREC_FP32)) return RPCA_ERR_UNSUPPORTED;
+  // complex windows: the tiled path up to 112 frames; the tensor-core
+  // precisions up to 64 frames (128 real columns)
+  if (p->dtype == RPCA_C64 && (2 * p->T > kMaxTW || (p->precision != RPCA_PREC_FP32 && 2 * p->T > 128)))
+    return RPCA_ERR_UNSUPPORTED;
   if (p->precision < RPCA_PREC_FP32 || p->precision > RPCA_PREC_TF32) return RPCA_ERR_ARG;
   // one TF32 product per contraction (10-bit mantissa) leaves L and S about
   // 7e-4 from the FP64 solution on the 262144 x 20 window, outside the 1e-4
@@ -196,8 +199,8 @@ rpca_status validate(const rpca_params* p) {
   if (p->precision == RPCA_PREC_TF32) return RPCA_ERR_UNSUPPORTED;
   if (p->precision != RPCA_PREC_FP32 && p->drive == RPCA_DRIVE_HOST) return RPCA_ERR_UNSUPPORTED;
   // the tiled path's tensor-core pass: real windows of at most 128 frames
-  if (p->precision != RPCA_PREC_FP32 && p->T > kMaxT && (p->T > 128 || p->dtype != RPCA_R32))
-    return RPCA_ERR_UNSUPPORTED;
+  // (complex ones: checked above)
+  if (p->precision != RPCA_PREC_FP32 && p->dtype == RPCA_R32 && p->T > 128) return RPCA_ERR_UNSUPPORTED;
   if (p->m * (int64_t)p->T > (int64_t)1 << 40) return RPCA_ERR_ARG;
   if (p->warm_start != 0 && p->warm_start != 1) return RPCA_ERR_ARG;
   if (p->sharded != 0 && p->sharded != 1) return RPCA_ERR_ARG;

@@ -37,18 +37,21 @@ WideKernels make_wide() {
     k.pass_tc_smem[i] = 0;
   }
   k.pass_tc_threads = kWtcThreads;
-  if constexpr (!CPLX && TP >= 64 && TP <= 128) {
-    k.pass_tc[RPCA_PREC_TF32X3] = (void*)pass_wtc_kernel<TP, false>;
-    k.pass_tc_smem[RPCA_PREC_TF32X3] = WtcShape<TP, false>::SMEM;
-    k.pass_tc[RPCA_PREC_BF16X3] = (void*)pass_wtc_kernel<TP, true>;
-    k.pass_tc_smem[RPCA_PREC_BF16X3] = WtcShape<TP, true>::SMEM;
+  // the tiled tensor-core pass: real windows of 33..128 frames, complex ones
+  // of up to 64 frames (128 real columns; 16 frames and fewer padded to 64)
+  constexpr int TPW = wtc_tp(TP);
+  if constexpr ((CPLX || TP >= 64) && TPW <= 128) {
+    k.pass_tc[RPCA_PREC_TF32X3] = (void*)pass_wtc_kernel<TPW, false, CPLX>;
+    k.pass_tc_smem[RPCA_PREC_TF32X3] = WtcShape<TPW, false>::SMEM;
+    k.pass_tc[RPCA_PREC_BF16X3] = (void*)pass_wtc_kernel<TPW, true, CPLX>;
+    k.pass_tc_smem[RPCA_PREC_BF16X3] = WtcShape<TPW, true>::SMEM;
   }
   return k;
 }
 
 size_t wide_tc_img_bytes(int T, int precision) {
-  const int TP = (T + 31) / 32 * 32;
-  if (TP < 64 || TP > 128) return 0;
+  const int TP = wtc_tp(T);
+  if (TP > 128) return 0;
   if (precision == RPCA_PREC_TF32X3) return wtc_img_bytes(TP, false);
   if (precision == RPCA_PREC_BF16X3) return wtc_img_bytes(TP, true);
   return 0;

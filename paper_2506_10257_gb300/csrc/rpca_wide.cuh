@@ -715,7 +715,7 @@ __global__ void __launch_bounds__(kWideThreads, res_blocks_per_sm(TP)) pass_res_
 // The B operand images of the tiled tensor-core pass (b.wtc), written by the
 // eigen-step once Ww and Vw are final.
 __device__ __forceinline__ void wtc_images(const Bufs& b) {
-  const int TP = (b.T + 31) / 32 * 32;
+  const int TP = wtc_tp(b.T);
   if (b.wtc == 1) {
     if (TP == 64) wtc_write_images<64, false>(b);
     else if (TP == 96) wtc_write_images<96, false>(b);

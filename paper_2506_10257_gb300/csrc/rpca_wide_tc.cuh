@@ -33,6 +33,13 @@
 // wait is bounded: a wait that runs out sets the pass's error flag and the
 // CTA leaves its tile loop (the solve then ends with RPCA_ERR_TIMEOUT).
 //
+// Complex windows (CPLX) run as their interleaved real embedding (columns
+// 2f, 2f+1 = Re, Im of frame f; up to 64 frames): step 2 applies the complex
+// shrink of Eq. 5 to each (Re, Im) pair, and after each pair's Z~ chunks the
+// rows of i Z' (per frame (-Im, Re)) are staged and multiplied by V as well
+// (columns [3 TP, 4 TP)); step 3 adds both row sets to the Gram (the real
+// embedding of the Hermitian Gram is the real Gram of the rows of Z and i Z).
+//
 // Shared-memory layouts: the canonical K-major no-swizzle layout of rpca_tc.cuh.
 // A and B chunks keep K-adjacent core matrices contiguous (LBO 128 B); the
 // Gram operand spaces them 144 B apart, so that the 32 lanes of a warp, which
@@ -74,6 +81,10 @@ struct WtcShape {
   // bytes of the B operand images a plan keeps: [Wbar, V][chunk][hi, lo]
   static constexpr size_t IMG_BYTES = 2 * (size_t)NCH * 2 * B_BYTES;
 };
+
+// Columns the tiled tensor-core pass pads a window of T real columns to: T
+// rounded up to 32, at least 64 (complex windows of up to 16 frames).
+__host__ __device__ constexpr int wtc_tp(int T) { return ((T + 31) / 32 * 32) < 64 ? 64 : (T + 31) / 32 * 32; }
 
 __host__ __device__ constexpr size_t wtc_img_bytes(int TP, bool bf16) {
   return 2 * (size_t)(TP / kWtcKCh) * 2 * (size_t)((TP / 8) * ((kWtcKCh / (bf16 ? 8 : 4)) * 128));
@@ -118,9 +129,10 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                : "memory");
 }
 
-template <int TP, bool BF16>
+template <int TP, bool BF16, bool CPLX>
 __global__ void __launch_bounds__(kWtcThreads, 1) pass_wtc_kernel(Bufs b) {
   using SH = WtcShape<TP, BF16>;
+  static_assert(!CPLX || 4 * TP <= (int)SH::TMEM_COLS, "TMEM columns of the complex form");
   constexpr int NCH = SH::NCH, NPAIR = SH::NPAIR;
   extern __shared__ __align__(1024) unsigned char wtc_smem[];
   unsigned char* sA = wtc_smem;                       // [2][hi, lo]
@@ -163,7 +175,12 @@ __global__ void __launch_bounds__(kWtcThreads, 1) pass_wtc_kernel(Bufs b) {
   tc_fence_after();
   const uint32_t tmem = sTmem;
   const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-  const uint32_t colQ = 0, colZ = TP, colG = 2 * TP;
+  const uint32_t colQ = 0, colZ = TP, colG = 2 * TP, colZi = 3 * TP;
+  // float index of real column t of pixel p in a frame-major X, S or Y
+  // (complex: interleaved (Re, Im) of frame t / 2)
+  auto gidx = [&](int t, int64_t px) -> int64_t {
+    return CPLX ? ((int64_t)(t >> 1) * m + px) * 2 + (t & 1) : (int64_t)t * m + px;
+  };
   constexpr uint32_t idesc = tc_idesc(BF16 ? 1u : 2u, 128, TP);
 
   uint32_t ncommit = 0;      // MMA groups committed (uniform across the CTA)
@@ -186,9 +203,11 @@ __global__ void __launch_bounds__(kWtcThreads, 1) pass_wtc_kernel(Bufs b) {
     ++ib[s];
   };
   // thread 0: the MMAs of chunk c (A buffer c % 2, B slot s) into TMEM column col
-  auto issue_chunk = [&](int c, int s, uint32_t col) {
-    if (!mbar_wait(&mb_b[s], ub[s] & 1u, kTcWaitLimit)) atomicOr(&sFail, 1);
-    ++ub[s];
+  auto issue_chunk = [&](int c, int s, uint32_t col, bool b_resident = false) {
+    if (!b_resident) {
+      if (!mbar_wait(&mb_b[s], ub[s] & 1u, kTcWaitLimit)) atomicOr(&sFail, 1);
+      ++ub[s];
+    }
     tc_fence_after();
     const uint32_t ah = smem_u32(sA + (size_t)(c & 1) * 2 * SH::A_BYTES), al = ah + SH::A_BYTES;
     const uint32_t bh = smem_u32(sB + (size_t)s * 2 * SH::B_BYTES), bl = bh + SH::B_BYTES;
@@ -211,13 +230,21 @@ __global__ void __launch_bounds__(kWtcThreads, 1) pass_wtc_kernel(Bufs b) {
     // into L2 while this one is computed: one prefetch per 128-byte piece
     if (tile + gridDim.x < ntiles) {
       const int64_t pn = (tile + gridDim.x) * 128;
-      const int pieces = T * 4;   // frame rows x 128-byte pieces of 32 pixels
+      const int pieces = T * 4;   // frame rows x 128-byte pieces (32 real or 16 complex pixels)
       for (int k = tid; k < (first ? 1 : 3) * pieces; k += kWtcThreads) {
-        const int a = k / pieces, q = k % pieces, t = q / 4;
-        const int64_t px = pn + 32 * (q % 4);
-        if (px >= m) continue;
+        const int a = k / pieces, q = k % pieces;
         const float* base = a == 0 ? X : (a == 1 ? Sp : Yin);
-        prefetch_l2(base + (int64_t)t * m + px);
+        if (CPLX) {
+          const int f = q / 8;
+          const int64_t px = pn + 16 * (q % 8);
+          if (px >= m) continue;
+          prefetch_l2(base + ((int64_t)f * m + px) * 2);
+        } else {
+          const int t = q / 4;
+          const int64_t px = pn + 32 * (q % 4);
+          if (px >= m) continue;
+          prefetch_l2(base + (int64_t)t * m + px);
+        }
       }
     }
     // the previous tile's Gram MMAs read the operand region the B slots use
@@ -235,9 +262,10 @@ __global__ void __launch_bounds__(kWtcThreads, 1) pass_wtc_kernel(Bufs b) {
       for (int u = 0; u < kWtcKCh; ++u) {
         const int t = c * kWtcKCh + u;
         const bool in = has && valid && t < T;
-        const float x = in ? X[(int64_t)t * m + p] : 0.f;
-        const float s = (in && !first) ? Sp[(int64_t)t * m + p] : 0.f;
-        const float y = (in && !first) ? Yin[(int64_t)t * m + p] : 0.f;
+        const int64_t gi = in ? gidx(t, p) : 0;
+        const float x = in ? X[gi] : 0.f;
+        const float s = (in && !first) ? Sp[gi] : 0.f;
+        const float y = (in && !first) ? Yin[gi] : 0.f;
         z[u] = form_z(x, s, y, inv_mu);
       }
       wait_mma();   // A buffers free (the group before has completed)
@@ -282,6 +310,37 @@ __global__ void __launch_bounds__(kWtcThreads, 1) pass_wtc_kernel(Bufs b) {
       if (has) {
         float q[kWtcKCh];
         tmem_ld32(tmem + lane_base + colQ + (uint32_t)(c * kWtcKCh), q);
+        if constexpr (CPLX) {
+          // Eq. 5-6 on each complex value: the shrink scales R by
+          // max(|R| - gamma, 0) / |R| (phase kept), Y' = mu R min(1, gamma / |R|)
+          float2* S2 = reinterpret_cast<float2*>(Sp);
+          float2* Yo2 = reinterpret_cast<float2*>(Yout);
+#pragma unroll
+          for (int u = 0; u < kWtcKCh; u += 2) {
+            const int t = c * kWtcKCh + u;
+            zn[u] = 0.f;
+            zn[u + 1] = 0.f;
+            if (valid && t < T) {
+              const int64_t gf = (int64_t)(t >> 1) * m + p;
+              const float2 x = reinterpret_cast<const float2*>(X)[gf];
+              const float2 sv = first ? make_float2(0.f, 0.f) : S2[gf];
+              const float2 y = first ? make_float2(0.f, 0.f) : reinterpret_cast<const float2*>(Yin)[gf];
+              const float dr = y.x * inv_mu, di = y.y * inv_mu;
+              const float rr = sv.x + q[u], ri = sv.y + q[u + 1];    // X - L + Y/mu
+              const float mag = sqrtf(fmaf(rr, rr, ri * ri));
+              const float f = (mag > gamma) ? gamma / mag : 1.f;
+              const float cr = rr * f, ci = ri * f;
+              const float ynr = f_mu * cr, yni = f_mu * ci;          // Eq. 6
+              const float er = cr - dr, ei = ci - di;                // X - L - S'
+              e2 = fmaf(er, er, fmaf(ei, ei, e2));
+              const float snr = rr - cr, sni = ri - ci;              // Eq. 5
+              S2[gf] = make_float2(snr, sni);
+              Yo2[gf] = make_float2(ynr, yni);
+              zn[u] = form_z(x.x, snr, ynr, inv_mu_nxt);
+              zn[u + 1] = form_z(x.y, sni, yni, inv_mu_nxt);
+            }
+          }
+        } else {
 #pragma unroll
         for (int u = 0; u < kWtcKCh; ++u) {
           const int t = c * kWtcKCh + u;
@@ -302,6 +361,7 @@ __global__ void __launch_bounds__(kWtcThreads, 1) pass_wtc_kernel(Bufs b) {
             Yout[gi] = yn;
             zn[u] = form_z(x, sn, yn, inv_mu_nxt);
           }
+        }
         }
       }
       if (j > 0) wait_mma();   // the previous Z~ pair has read its A buffers
@@ -327,10 +387,34 @@ __global__ void __launch_bounds__(kWtcThreads, 1) pass_wtc_kernel(Bufs b) {
         }
       }
       ++ncommit;
+      if constexpr (CPLX) {
+        // the rows of i Z' (per frame (-Im, Re)) times the same V chunks, which
+        // stay in their slots until the next pair's MMAs have been issued
+        wait_mma();   // the Z' chunks have been read
+        if (has) {
+          unsigned char* ah = sA + (size_t)wg * 2 * SH::A_BYTES;
+#pragma unroll
+          for (int k4 = 0; k4 < kWtcKCh; k4 += 4)
+            tc_store4<BF16>(ah, ah + SH::A_BYTES, SH::off(r, k4), -zn[k4 + 1], zn[k4], -zn[k4 + 3], zn[k4 + 2], true);
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (sFail) break;
+        if (tid == 0) {
+          const int sb = 2 * ((NPAIR + j) & 1);
+          issue_chunk(2 * j, sb, colZi, true);
+          if (2 * j + 1 < NCH) issue_chunk(2 * j + 1, sb + 1, colZi, true);
+          tc_commit(&mb_mma);
+        }
+        ++ncommit;
+      }
     }
     if (sFail) break;
-    // ---- 3. G += Z~^T Z~ ----
-    wait_mma();   // Z~ complete; A and B regions free
+    // ---- 3. G += Z~^T Z~ (complex: then the rows of (i Z') V) ----
+    for (int round = 0; round < (CPLX ? 2 : 1); ++round) {
+    const uint32_t colU = round == 0 ? colZ : colZi;
+    wait_mma();   // Z~ complete (or the round before has read the operands); A and B regions free
     tc_fence_after();
     {
       const int kq = warp & 3;              // pixel chunk of this warp: pixels 32 kq .. 32 kq + 31
@@ -339,7 +423,7 @@ __global__ void __launch_bounds__(kWtcThreads, 1) pass_wtc_kernel(Bufs b) {
       const int t0 = wg * (TP / 2), t1 = t0 + TP / 2;
       for (int tb = t0; tb < t1; tb += 16) {
         float v[16];
-        tmem_ld16(tmem + lane_base + colZ + (uint32_t)tb, v);
+        tmem_ld16(tmem + lane_base + colU + (uint32_t)tb, v);
 #pragma unroll
         for (int u = 0; u < 16; ++u) tc_store1<BF16>(gh, gl, SH::goff(tb + u, lane), valid ? v[u] : 0.f);
       }
@@ -360,7 +444,7 @@ __global__ void __launch_bounds__(kWtcThreads, 1) pass_wtc_kernel(Bufs b) {
         for (int kk = 0; kk < 32 / SH::KSTEP; ++kk) {
           const uint32_t ko = (uint32_t)kk * (SH::KSTEP / SH::KC) * kWtcGLbo;
           const uint64_t dh = tc_desc(gh + ko, kWtcGLbo, SH::G_SBO), dl = tc_desc(gl + ko, kWtcGLbo, SH::G_SBO);
-          tc_mma<BF16>(tmem + colG, dh, dh, idesc, (gram_started || kq > 0 || kk > 0) ? 1u : 0u);
+          tc_mma<BF16>(tmem + colG, dh, dh, idesc, (gram_started || round > 0 || kq > 0 || kk > 0) ? 1u : 0u);
           tc_mma<BF16>(tmem + colG, dl, dh, idesc, 1u);
           tc_mma<BF16>(tmem + colG, dh, dl, idesc, 1u);
         }
@@ -368,6 +452,8 @@ __global__ void __launch_bounds__(kWtcThreads, 1) pass_wtc_kernel(Bufs b) {
       tc_commit(&mb_mma);
     }
     ++ncommit;
+    }
+    if (sFail) break;
     gram_started = true;
   }
   wait_mma();

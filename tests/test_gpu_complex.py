@@ -51,13 +51,14 @@ def solve(rp, frames, theta=None, **kw):
     return out
 
 
-def check(frames, got, **kw):
+def check(frames, got, tol=FP32_TOL, iters_within=1, **kw):
     ref = O.rpca_frames(frames, **kw)
-    assert abs(got["res"]["iters"] - ref.iters) <= 1, (got["res"]["iters"], ref.iters)
-    if got["res"]["iters"] != ref.iters:
-        ref = O.rpca_frames(frames, **dict(kw, max_iter=got["res"]["iters"], tol=1e-30))
+    if iters_within is not None:
+        assert abs(got["res"]["iters"] - ref.iters) <= iters_within, (got["res"]["iters"], ref.iters)
+        if got["res"]["iters"] != ref.iters:
+            ref = O.rpca_frames(frames, **dict(kw, max_iter=got["res"]["iters"], tol=1e-30))
     eL, eS = rel(got["L"], ref.L), rel(got["S"], ref.S)
-    assert eL <= FP32_TOL and eS <= FP32_TOL, (eL, eS, got["res"]["iters"], ref.iters)
+    assert eL <= tol and eS <= tol, (eL, eS, got["res"]["iters"], ref.iters)
     return ref
 
 
@@ -68,6 +69,22 @@ def test_complex_solve_matches_oracle(rp, ny, nx, T):
     assert got["res"]["status"] == rp.OK
     ref = check(w.frames, got)
     assert got["res"]["rank"] == ref.rank
+
+
+@pytest.mark.parametrize("prec", ["TF32X3", "BF16X3"])
+@pytest.mark.parametrize("ny,nx,T", [(16, 16, 8), (64, 64, 20), (31, 45, 13), (40, 40, 50), (48, 48, 64)])
+def test_complex_tensor_core_matches_oracle(rp, prec, ny, nx, T):
+    # the tiled tensor-core pass on the real embedding (Q, Z~ = Z' V and
+    # (i Z') V, and the Gram of both row sets on tcgen05): TF32x3 at the FP32
+    # tolerance and within one iteration of the oracle; BF16x3 at 1e-4 (its
+    # rounding floor near the stopping tolerance can cost iterations)
+    w = synth.make_window(seed=3 * ny * nx + T, ny=ny, nx=nx, T=T, n_bound=6, n_free=10, complex_iq=True)
+    got = solve(rp, w.frames, precision=getattr(rp, "PREC_" + prec))
+    assert got["res"]["status"] == rp.OK
+    if prec == "TF32X3":
+        check(w.frames, got)
+    else:
+        check(w.frames, got, tol=1e-4, iters_within=None)
 
 
 def test_complex_mask(rp):
@@ -142,4 +159,5 @@ def test_complex_limits(rp):
     with pytest.raises(rp.RpcaError):
         rp.Plan(1000, 113, dtype=rp.C64)          # 2T > 224
     with pytest.raises(rp.RpcaError):
-        rp.Plan(1000, 20, dtype=rp.C64, precision=rp.PREC_BF16X3)
+        rp.Plan(1000, 65, dtype=rp.C64, precision=rp.PREC_BF16X3)   # 2T > 128: no tensor-core pass
+    rp.Plan(1000, 64, dtype=rp.C64, precision=rp.PREC_BF16X3).close()

@@ -128,6 +128,12 @@ def test_complex_256x256x50_matches_oracle(rp):
     check(rp, (256, 256, 50, 77, True))
 
 
+def test_complex_tensor_core_256x256x50(rp):
+    # the complex form of the tiled tensor-core pass: 65536 pixels x 100 real
+    # columns, 512 tiles of 128 pixels
+    check(rp, (256, 256, 50, 78, True), "TF32X3")
+
+
 @pytest.mark.parametrize("T", [50, 100])
 def test_wide_512x512_matches_oracle(rp, T):
     # the paper-scale windows of the frame sweep, in the launch shape the

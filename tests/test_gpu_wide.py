@@ -122,12 +122,13 @@ def test_wide_mask_and_fixed_schedule(rp):
 
 
 def test_wide_rejects_unbuilt_tensor_core_shapes(rp):
-    # the tiled tensor-core pass covers real windows of up to 128 frames
+    # the tiled tensor-core pass covers real windows of up to 128 frames and
+    # complex ones of up to 64 (128 real columns)
     with pytest.raises(rp.RpcaError) as e:
         rp.Plan(4096, 129, precision=rp.PREC_BF16X3)
     assert e.value.status == rp.ERR_UNSUPPORTED
     with pytest.raises(rp.RpcaError) as e:
-        rp.Plan(4096, 40, precision=rp.PREC_TF32X3, dtype=rp.C64)
+        rp.Plan(4096, 65, precision=rp.PREC_TF32X3, dtype=rp.C64)
     assert e.value.status == rp.ERR_UNSUPPORTED
     with pytest.raises(rp.RpcaError):
         rp.Plan(4096, 225)
