@@ -22,7 +22,7 @@ REJECTED = [
     (dict(drive=3), ARG), (dict(dtype=2), ARG), (dict(precision=4), ARG), (dict(precision=-1), ARG),
     (dict(dtype=C64, T=rpca.MAX_T // 2 + 1), UNSUP), (dict(dtype=C64, precision=TF32), UNSUP),
     (dict(precision=TF32X3, drive=rpca.DRIVE_HOST), UNSUP), (dict(precision=BF16X3, T=129), UNSUP),
-    (dict(precision=TF32X3, T=40, dtype=C64), UNSUP),
+    (dict(precision=TF32X3, T=65, dtype=C64), UNSUP),             # complex: 2T > 128 has no tensor-core pass
     (dict(m=2 ** 36), ARG),                                   # m * T above 2^40 elements
     (dict(warm_start=2), ARG), (dict(sharded=2), ARG),
     (dict(sharded=1, dtype=C64), UNSUP), (dict(sharded=1, T=rpca.MAX_T_NARROW + 1), UNSUP),
@@ -35,7 +35,7 @@ REJECTED = [
 # accepted by validation (on a machine without a GPU the size query then fails with RPCA_ERR_CUDA)
 ACCEPTED = [
     dict(), dict(T=1), dict(T=rpca.MAX_T), dict(dtype=C64, T=rpca.MAX_T // 2), dict(precision=BF16X3, T=32),
-    dict(precision=BF16X3, T=128), dict(precision=TF32X3, T=33),
+    dict(precision=BF16X3, T=128), dict(precision=TF32X3, T=33), dict(precision=TF32X3, T=64, dtype=C64),
     dict(mu_schedule=FIXED_L1, rho=0.5),                      # rho, mu0_scale, cap only bind the IALM schedule
     dict(sharded=1), dict(warm_start=1, mu_prev_scale=0.1), dict(drive=rpca.DRIVE_STREAM, precision=TF32X3),
 ]
