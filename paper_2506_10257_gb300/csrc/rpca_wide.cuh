@@ -849,18 +849,21 @@ static __device__ void eig_wide_body(Bufs b, int flags, cudaGraphConditionalHand
         __syncthreads();  // the counts are read before the next round rewrites them
         continue;
       }
-      if (tid < K) sPos[tid] = -1;
-      __syncthreads();
-      if (act) {
-        off += __popc(bal & ((1u << (tid & 31)) - 1u));
-        sAct[off] = tid;
-        sPos[tid] = off;
-        if (!inline_d) {
-          // the replay needs the pair's columns and where each round starts
-          const int4 pr = sPair[tid];
-          log_k[logged + off] = pr.x | (pr.y << 8) | (off == 0 ? (1 << 16) : 0);
-          log_cs[logged + off] = make_float2(sC[tid], sSn[tid]);
+      if (tid < K) {
+        // (each slot has one writer, and the previous round's readers passed
+        // its closing barrier)
+        int pos = -1;
+        if (act) {
+          pos = off + __popc(bal & ((1u << (tid & 31)) - 1u));
+          sAct[pos] = tid;
+          if (!inline_d) {
+            // the replay needs the pair's columns and where each round starts
+            const int4 pr = sPair[tid];
+            log_k[logged + pos] = pr.x | (pr.y << 8) | (pos == 0 ? (1 << 16) : 0);
+            log_cs[logged + pos] = make_float2(sC[tid], sSn[tid]);
+          }
         }
+        sPos[tid] = pos;
       }
       if (tid == 0 && !inline_d) {
         log_rnd[2 * rounds_run] = rnd;
