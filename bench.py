@@ -320,7 +320,7 @@ def _plan_pass_name(T, m, args):
         return "pass_res_kernel / pass_wide_kernel (tiled, FUSED)"
     tb = next(b for b in (8, 12, 16, 20, 24, 32) if T <= b)
     if args.precision != "fp32":
-        return f"pass_ws_kernel / pass_tc_kernel ({args.precision}, tcgen05)"
+        return f"pass_tc_kernel ({args.precision}, tcgen05)"
     if m % 4 == 0 and os.environ.get("RPCA_PASS_TMA", "0") not in ("", "0"):
         return f"pass_fs_kernel<{tb},FUSED> (TMA-fed)"
     return f"pass_kernel<{tb},FUSED>"

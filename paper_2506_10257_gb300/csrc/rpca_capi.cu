@@ -23,8 +23,6 @@ struct KernelSet {
   size_t pass_smem;        // dynamic shared memory of the CUDA-core passes
   void* pass_tc[4];        // fused pass with tensor-core contractions, per rpca_precision (0 unused)
   size_t pass_tc_smem[4];
-  void* pass_ws[4];        // the same, warp-specialised and fed by TMA (needs m % 4 == 0)
-  size_t pass_ws_smem[4];
   void* pass_fs[4];        // CUDA-core FP32 passes fed by TMA, by mode (needs m % 4 == 0)
   size_t pass_fs_smem;
   void* eig64;       // plain smem Jacobi, FP64 rotations (rpca_eig on an external matrix)
@@ -80,14 +78,6 @@ void add_tc(KernelSet& k) {
   k.pass_tc_smem[RPCA_PREC_BF16X3] = pass_tc_smem<TB, KP, true>();
   k.pass_tc[RPCA_PREC_TF32] = nullptr;  // plain TF32 is not offered (validate)
   k.pass_tc_smem[RPCA_PREC_TF32] = 0;
-  k.pass_ws[RPCA_PREC_FP32] = nullptr;
-  k.pass_ws_smem[RPCA_PREC_FP32] = 0;
-  k.pass_ws[RPCA_PREC_TF32X3] = (void*)pass_ws_kernel<TB, KP, false, true>;
-  k.pass_ws_smem[RPCA_PREC_TF32X3] = pass_ws_smem<TB, KP, false>();
-  k.pass_ws[RPCA_PREC_BF16X3] = (void*)pass_ws_kernel<TB, KP, true, true>;
-  k.pass_ws_smem[RPCA_PREC_BF16X3] = pass_ws_smem<TB, KP, true>();
-  k.pass_ws[RPCA_PREC_TF32] = nullptr;
-  k.pass_ws_smem[RPCA_PREC_TF32] = 0;
 }
 
 // Tensor-core pass buckets: T <= 16, 20, 32.
@@ -115,7 +105,7 @@ struct Layout {
   size_t ctrl, eig, red, job, gw, ww, vw, evw, rlog, rk, rrnd, wtc, gram_part, group_part, scal_part, gscal_part, ybuf,
       total;
   int grid, ngroups;
-  int ws_grid;     // CTAs of the warp-specialised pass (one per SM, 128-pixel tiles)
+  int ws_grid;     // CTAs of the passes with 128-pixel tiles (TMA-fed FP32, tiled tensor-core): one per SM
   int wide_grid;   // CTAs of the wide pass (T > kMaxT; one per SM, 32-pixel tiles)
 };
 
@@ -228,7 +218,6 @@ struct rpca_plan_s {
   cudaGraph_t graph;
   cudaGraphExec_t exec;
   Ctrl* ctrl_host;  // pinned
-  bool use_ws;      // fused pass = warp-specialised TMA kernel
   bool use_fs;      // FP32 passes = TMA-fed CUDA-core kernels (narrow windows, m % 4 == 0)
   // device staging of rpca_solve_host (allocated on first use)
   float* stage_x;
@@ -318,22 +307,22 @@ static dim3 pass_block(const rpca_plan_s* pl) {
 static void* fused_fn(const rpca_plan_s* pl) {
   if (pl->p.precision == RPCA_PREC_FP32) return pass_fn(pl, PM_FUSED);
   if (pl->wide) return pl->wk.pass_tc[pl->p.precision];
-  return pl->use_ws ? pl->ks.pass_ws[pl->p.precision] : pl->ks.pass_tc[pl->p.precision];
+  return pl->ks.pass_tc[pl->p.precision];
 }
 static size_t fused_smem(const rpca_plan_s* pl) {
   if (pl->p.precision == RPCA_PREC_FP32) return pass_smem(pl);
   if (pl->wide) return pl->wk.pass_tc_smem[pl->p.precision];
-  return pl->use_ws ? pl->ks.pass_ws_smem[pl->p.precision] : pl->ks.pass_tc_smem[pl->p.precision];
+  return pl->ks.pass_tc_smem[pl->p.precision];
 }
 static dim3 fused_grid(const rpca_plan_s* pl) {
   if (pl->p.precision == RPCA_PREC_FP32) return pass_grid(pl);
   if (pl->wide) return dim3(pl->lay.ws_grid);  // one CTA per SM, 128-pixel tiles
-  return dim3(pl->use_ws ? pl->lay.ws_grid : pl->lay.grid);
+  return dim3(pl->lay.grid);
 }
 static dim3 fused_block(const rpca_plan_s* pl) {
   if (pl->p.precision == RPCA_PREC_FP32) return pass_block(pl);
   if (pl->wide) return dim3(pl->wk.pass_tc_threads);
-  return dim3(pl->use_ws ? kWsThreads : kPassThreads);
+  return dim3(kPassThreads);
 }
 
 static cudaError_t add_kernel(cudaGraph_t g, cudaGraphNode_t* node, const cudaGraphNode_t* deps, size_t ndeps,
@@ -506,12 +495,8 @@ static rpca_status plan_create_impl(const rpca_params* p, void* workspace, size_
     }
     set_tc(p->T, &pl->ks);
   }
-  // The TMA-fed warp-specialised tensor-core pass is opt-in (RPCA_PASS_WS=1):
-  // pass_tc_kernel's independent warpgroups measured faster (262144 x 20,
-  // TF32x3: 41 against 54 us).  The TMA-fed FP32 pass is opt-in too
-  // (RPCA_PASS_TMA=1): the register-resident pass measured as fast or faster.
-  pl->use_ws = !pl->wide && (p->precision != RPCA_PREC_FP32) && (p->m % 4 == 0) && tma_encoder() != nullptr &&
-               getenv("RPCA_PASS_WS") && atoi(getenv("RPCA_PASS_WS")) != 0;
+  // The TMA-fed FP32 pass is opt-in (RPCA_PASS_TMA=1): the register-resident
+  // pass measured as fast or faster.
   pl->use_fs = !pl->wide && (p->precision == RPCA_PREC_FP32) && (p->m % 4 == 0) && (p->m < ((int64_t)1 << 31)) &&
                tma_encoder() != nullptr && getenv("RPCA_PASS_TMA") && atoi(getenv("RPCA_PASS_TMA")) != 0;
   if (!pl->wide) {
@@ -542,9 +527,6 @@ static rpca_status plan_create_impl(const rpca_params* p, void* workspace, size_
   if (p->precision != RPCA_PREC_FP32 && !pl->wide) {
     cudaError_t ea = cudaFuncSetAttribute(pl->ks.pass_tc[p->precision], cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)pl->ks.pass_tc_smem[p->precision]);
-    if (ea == cudaSuccess && pl->use_ws)
-      ea = cudaFuncSetAttribute(pl->ks.pass_ws[p->precision], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)pl->ks.pass_ws_smem[p->precision]);
     if (ea != cudaSuccess) {
       delete pl;
       return cuda_status(ea);
@@ -750,7 +732,7 @@ rpca_status rpca::plan_solve_ex(rpca_plan_t pl, const void* X, void* L, void* S,
   TmaMaps maps;
   memset(&maps, 0, sizeof(maps));
   int use_maps = 0;
-  if (pl->use_ws || pl->use_fs) {
+  if (pl->use_fs) {
     const float* y1 = (const float*)(pl->ws + pl->lay.ybuf);
     if (!encode_map(&maps.x, X, pl->p.m, pl->p.T) || !encode_map(&maps.s, S, pl->p.m, pl->p.T) ||
         !encode_map(&maps.y0, L, pl->p.m, pl->p.T) || !encode_map(&maps.y1, y1, pl->p.m, pl->p.T))

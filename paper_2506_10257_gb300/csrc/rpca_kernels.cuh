@@ -1252,7 +1252,6 @@ static __global__ void begin_kernel(Bufs b, const float* X, float* L, float* S, 
 
 #include "rpca_tc.cuh"
 #include "rpca_pass_tc.cuh"
-#include "rpca_pass_ws.cuh"
 #include "rpca_pass_fs.cuh"
 #include "rpca_eig_fast.cuh"
 #include "rpca_eig64.cuh"
