@@ -85,7 +85,8 @@ typedef enum {
 typedef struct {
   int64_t m;                /* pixels per frame (rows of X), >= 1 */
   int32_t T;                /* frames (columns of X), 1 <= T <= RPCA_MAX_T; precisions other
-                               than FP32 need T <= RPCA_MAX_T_NARROW */
+                               than FP32 need T <= 128 (real) or T <= 64 (complex) in plans,
+                               T <= RPCA_MAX_T_NARROW (real) in batches */
   int32_t dtype;            /* rpca_dtype */
   int32_t precision;        /* rpca_precision */
   int32_t mu_schedule;      /* rpca_mu_schedule */
