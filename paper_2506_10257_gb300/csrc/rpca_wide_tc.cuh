@@ -48,6 +48,12 @@
 
 constexpr int kWtcThreads = 256;
 constexpr int kWtcKCh = 32;            // frames per K-chunk
+// Step 2 reads X, S, Y of a chunk in groups of kWtcLd columns, every load of
+// a group issued before the group's stores of S', Y': the compiler cannot
+// tell those stores from the loads (for all it knows the arrays overlap), so
+// a load placed after a store waits until the store's operands are ready,
+// and one load per column would cost one L2 round trip per column.
+constexpr int kWtcLd = 16;
 constexpr uint32_t kWtcGLbo = 144;     // Gram operand: K-adjacent core matrices 144 B apart
 
 template <int TP, bool BF16>
@@ -316,52 +322,75 @@ __global__ void __launch_bounds__(kWtcThreads, 1) pass_wtc_kernel(Bufs b) {
           float2* S2 = reinterpret_cast<float2*>(Sp);
           float2* Yo2 = reinterpret_cast<float2*>(Yout);
 #pragma unroll
-          for (int u = 0; u < kWtcKCh; u += 2) {
-            const int t = c * kWtcKCh + u;
-            zn[u] = 0.f;
-            zn[u + 1] = 0.f;
-            if (valid && t < T) {
-              const int64_t gf = (int64_t)(t >> 1) * m + p;
-              const float2 x = reinterpret_cast<const float2*>(X)[gf];
-              const float2 sv = first ? make_float2(0.f, 0.f) : S2[gf];
-              const float2 y = first ? make_float2(0.f, 0.f) : reinterpret_cast<const float2*>(Yin)[gf];
-              const float dr = y.x * inv_mu, di = y.y * inv_mu;
-              const float rr = sv.x + q[u], ri = sv.y + q[u + 1];    // X - L + Y/mu
-              const float mag = sqrtf(fmaf(rr, rr, ri * ri));
-              const float f = (mag > gamma) ? gamma / mag : 1.f;
-              const float cr = rr * f, ci = ri * f;
-              const float ynr = f_mu * cr, yni = f_mu * ci;          // Eq. 6
-              const float er = cr - dr, ei = ci - di;                // X - L - S'
-              e2 = fmaf(er, er, fmaf(ei, ei, e2));
-              const float snr = rr - cr, sni = ri - ci;              // Eq. 5
-              S2[gf] = make_float2(snr, sni);
-              Yo2[gf] = make_float2(ynr, yni);
-              zn[u] = form_z(x.x, snr, ynr, inv_mu_nxt);
-              zn[u + 1] = form_z(x.y, sni, yni, inv_mu_nxt);
+          for (int u0 = 0; u0 < kWtcKCh; u0 += kWtcLd) {
+            float2 xg[kWtcLd / 2], sg[kWtcLd / 2], yg[kWtcLd / 2];
+#pragma unroll
+            for (int v = 0; v < kWtcLd / 2; ++v) {
+              const int t = c * kWtcKCh + u0 + 2 * v;
+              const bool in = valid && t < T;
+              const int64_t gf = in ? (int64_t)(t >> 1) * m + p : 0;
+              xg[v] = in ? reinterpret_cast<const float2*>(X)[gf] : make_float2(0.f, 0.f);
+              sg[v] = (in && !first) ? S2[gf] : make_float2(0.f, 0.f);
+              yg[v] = (in && !first) ? reinterpret_cast<const float2*>(Yin)[gf] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int v = 0; v < kWtcLd / 2; ++v) {
+              const int u = u0 + 2 * v;
+              const int t = c * kWtcKCh + u;
+              zn[u] = 0.f;
+              zn[u + 1] = 0.f;
+              if (valid && t < T) {
+                const int64_t gf = (int64_t)(t >> 1) * m + p;
+                const float2 x = xg[v], sv = sg[v], y = yg[v];
+                const float dr = y.x * inv_mu, di = y.y * inv_mu;
+                const float rr = sv.x + q[u], ri = sv.y + q[u + 1];    // X - L + Y/mu
+                const float mag = sqrtf(fmaf(rr, rr, ri * ri));
+                const float f = (mag > gamma) ? gamma / mag : 1.f;
+                const float cr = rr * f, ci = ri * f;
+                const float ynr = f_mu * cr, yni = f_mu * ci;          // Eq. 6
+                const float er = cr - dr, ei = ci - di;                // X - L - S'
+                e2 = fmaf(er, er, fmaf(ei, ei, e2));
+                const float snr = rr - cr, sni = ri - ci;              // Eq. 5
+                S2[gf] = make_float2(snr, sni);
+                Yo2[gf] = make_float2(ynr, yni);
+                zn[u] = form_z(x.x, snr, ynr, inv_mu_nxt);
+                zn[u + 1] = form_z(x.y, sni, yni, inv_mu_nxt);
+              }
             }
           }
         } else {
 #pragma unroll
-        for (int u = 0; u < kWtcKCh; ++u) {
-          const int t = c * kWtcKCh + u;
-          zn[u] = 0.f;
-          if (valid && t < T) {
-            const int64_t gi = (int64_t)t * m + p;
-            const float x = X[gi];
-            const float s = first ? 0.f : Sp[gi];
-            const float y = first ? 0.f : Yin[gi];
-            const float d = y * inv_mu;
-            const float rr = s + q[u];                          // X - L + Y/mu
-            const float cl = fminf(fmaxf(rr, -gamma), gamma);   // clip to +-lambda/mu
-            const float sn = rr - cl;                           // Eq. 5
-            const float yn = f_mu * cl;                         // Eq. 6
-            const float e = cl - d;                             // X - L - S'
-            e2 = fmaf(e, e, e2);
-            Sp[gi] = sn;
-            Yout[gi] = yn;
-            zn[u] = form_z(x, sn, yn, inv_mu_nxt);
+          for (int u0 = 0; u0 < kWtcKCh; u0 += kWtcLd) {
+            float xg[kWtcLd], sg[kWtcLd], yg[kWtcLd];
+#pragma unroll
+            for (int v = 0; v < kWtcLd; ++v) {
+              const int t = c * kWtcKCh + u0 + v;
+              const bool in = valid && t < T;
+              const int64_t gi = in ? (int64_t)t * m + p : 0;
+              xg[v] = in ? X[gi] : 0.f;
+              sg[v] = (in && !first) ? Sp[gi] : 0.f;
+              yg[v] = (in && !first) ? Yin[gi] : 0.f;
+            }
+#pragma unroll
+            for (int v = 0; v < kWtcLd; ++v) {
+              const int u = u0 + v;
+              const int t = c * kWtcKCh + u;
+              zn[u] = 0.f;
+              if (valid && t < T) {
+                const int64_t gi = (int64_t)t * m + p;
+                const float d = yg[v] * inv_mu;
+                const float rr = sg[v] + q[u];                      // X - L + Y/mu
+                const float cl = fminf(fmaxf(rr, -gamma), gamma);   // clip to +-lambda/mu
+                const float sn = rr - cl;                           // Eq. 5
+                const float yn = f_mu * cl;                         // Eq. 6
+                const float e = cl - d;                             // X - L - S'
+                e2 = fmaf(e, e, e2);
+                Sp[gi] = sn;
+                Yout[gi] = yn;
+                zn[u] = form_z(xg[v], sn, yn, inv_mu_nxt);
+              }
+            }
           }
-        }
         }
       }
       if (j > 0) wait_mma();   // the previous Z~ pair has read its A buffers
