@@ -35,6 +35,11 @@
 namespace rpca {
 
 constexpr int kWP = 32;           // pixels per tile (one per lane)
+// Frame rows per warp whose loads the tiled passes' staging issues together:
+// the compiler cannot tell the staging's shared-memory stores from the global
+// loads that follow them, so a load placed after a store waits for the store's
+// operand, i.e. for the previous load.
+constexpr int kResLd = 4;
 constexpr int kWKC = 32;          // rows of Wbar / V staged per step
 constexpr int kWideThreads = 256;
 constexpr int kEigWThreads = 1024;
@@ -166,40 +171,69 @@ __device__ bool pass_wide_body(Bufs b, int lc, int nc, float* wide_smem) {
     const int64_t p = tile * kWP + lane;
     const bool valid = p < m;
     __syncthreads();  // the previous tile's U is consumed
-    // ---- 1. stage the tile (frame-major) ----
+    // ---- 1. stage the tile (frame-major); the loads of kResLd frame rows
+    //      per warp are issued before their shared-memory stores ----
     if constexpr (CPLX) {
       const float2* X2 = reinterpret_cast<const float2*>(job.X);
       const float2* S2 = reinterpret_cast<const float2*>(job.S);
       const float2* Y2 = reinterpret_cast<const float2*>(Yin);
-      for (int f = w; f < TP / 2; f += 8) {
-        const bool in = valid && 2 * f < T;
-        const float2 x = in ? X2[(int64_t)f * m + p] : make_float2(0.f, 0.f);
-        sX[(2 * f) * kWP + lane] = x.x;
-        sX[(2 * f + 1) * kWP + lane] = x.y;
-        if (MODE == PM_INIT) {
-          const float a2 = fmaf(x.x, x.x, x.y * x.y);
-          e2 += a2;
-          l1 += sqrtf(a2);
-        } else {
-          const float2 sv = (in && !first) ? S2[(int64_t)f * m + p] : make_float2(0.f, 0.f);
-          const float2 yv = (in && !first) ? Y2[(int64_t)f * m + p] : make_float2(0.f, 0.f);
-          sS[(2 * f) * kWP + lane] = sv.x;
-          sS[(2 * f + 1) * kWP + lane] = sv.y;
-          sY[(2 * f) * kWP + lane] = yv.x;
-          sY[(2 * f + 1) * kWP + lane] = yv.y;
+      constexpr int G = kResLd / 2;
+      static_assert((TP / 2) % (8 * G) == 0, "whole groups of frame rows");
+      for (int f0 = w; f0 < TP / 2; f0 += 8 * G) {
+        float2 xg[G], sg[G], yg[G];
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
+          const int f = f0 + 8 * i;
+          const bool in = valid && 2 * f < T;
+          const int64_t gi = in ? (int64_t)f * m + p : 0;
+          xg[i] = in ? X2[gi] : make_float2(0.f, 0.f);
+          sg[i] = (MODE != PM_INIT && in && !first) ? S2[gi] : make_float2(0.f, 0.f);
+          yg[i] = (MODE != PM_INIT && in && !first) ? Y2[gi] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
+          const int f = f0 + 8 * i;
+          const float2 x = xg[i];
+          sX[(2 * f) * kWP + lane] = x.x;
+          sX[(2 * f + 1) * kWP + lane] = x.y;
+          if (MODE == PM_INIT) {
+            const float a2 = fmaf(x.x, x.x, x.y * x.y);
+            e2 += a2;
+            l1 += sqrtf(a2);
+          } else {
+            sS[(2 * f) * kWP + lane] = sg[i].x;
+            sS[(2 * f + 1) * kWP + lane] = sg[i].y;
+            sY[(2 * f) * kWP + lane] = yg[i].x;
+            sY[(2 * f + 1) * kWP + lane] = yg[i].y;
+          }
         }
       }
     } else {
-      for (int t = w; t < TP; t += 8) {
-        const bool in = valid && t < T;
-        const float x = in ? job.X[(int64_t)t * m + p] : 0.f;
-        sX[t * kWP + lane] = x;
-        if (MODE == PM_INIT) {
-          e2 = fmaf(x, x, e2);
-          l1 += fabsf(x);
-        } else {
-          sS[t * kWP + lane] = (in && !first) ? job.S[(int64_t)t * m + p] : 0.f;
-          sY[t * kWP + lane] = (in && !first) ? Yin[(int64_t)t * m + p] : 0.f;
+      constexpr int G = kResLd;
+      static_assert(TP % (8 * G) == 0, "whole groups of frame rows");
+      for (int t0 = w; t0 < TP; t0 += 8 * G) {
+        float xg[G], sg[G], yg[G];
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
+          const int t = t0 + 8 * i;
+          const bool in = valid && t < T;
+          const int64_t gi = in ? (int64_t)t * m + p : 0;
+          xg[i] = in ? job.X[gi] : 0.f;
+          sg[i] = (MODE != PM_INIT && in && !first) ? job.S[gi] : 0.f;
+          yg[i] = (MODE != PM_INIT && in && !first) ? Yin[gi] : 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
+          const int t = t0 + 8 * i;
+          const float x = xg[i];
+          sX[t * kWP + lane] = x;
+          if (MODE == PM_INIT) {
+            e2 = fmaf(x, x, e2);
+            l1 += fabsf(x);
+          } else {
+            sS[t * kWP + lane] = sg[i];
+            sY[t * kWP + lane] = yg[i];
+          }
         }
       }
     }
@@ -490,56 +524,82 @@ __device__ bool pass_res_body(Bufs b, int lc, int nc, float* smem) {
   for (int64_t tile = lc; tile < ntiles; tile += nc) {
     const int64_t pb = tile * kRP;
     __syncthreads();  // the previous tile (and the resident matrices) are ready / consumed
-    // ---- 1. stage: warp w takes frames w, w + 8, ...; lane l pixels l, l + 32 ----
+    // ---- 1. stage: warp w takes frames w, w + 8, ...; lane l pixels l, l + 32;
+    //      the loads of kResLd frame rows per warp are issued before their
+    //      shared-memory stores ----
     if constexpr (CPLX) {
       const float2* X2 = reinterpret_cast<const float2*>(job.X);
       const float2* S2 = reinterpret_cast<const float2*>(job.S);
       const float2* Y2 = reinterpret_cast<const float2*>(Yin);
-      for (int f = w; f < TP / 2; f += 8) {
+      constexpr int G = kResLd / 2;   // TP / 2 is a multiple of 16
+      for (int f0 = w; f0 < TP / 2; f0 += 8 * G) {
+        float2 xg[G][2], sg[G][2], yg[G][2];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int pp = lane + 32 * h;
-          const bool in = (pb + pp < m) && 2 * f < T;
-          const int64_t gi = (int64_t)f * m + pb + pp;
-          const float2 x = in ? X2[gi] : make_float2(0.f, 0.f);
-          if (MODE == PM_INIT) {
-            sZ[res_at(2 * f, pp)] = x.x;
-            sZ[res_at(2 * f + 1, pp)] = x.y;
-            const float a2 = fmaf(x.x, x.x, x.y * x.y);
-            e2 += a2;
-            l1 += sqrtf(a2);
-          } else {
-            const float2 sv = (in && !first) ? S2[gi] : make_float2(0.f, 0.f);
-            const float2 yv = (in && !first) ? Y2[gi] : make_float2(0.f, 0.f);
-            sZ[res_at(2 * f, pp)] = form_z(x.x, sv.x, yv.x, inv_mu);
-            sZ[res_at(2 * f + 1, pp)] = form_z(x.y, sv.y, yv.y, inv_mu);
-            sS[res_at(2 * f, pp)] = sv.x;
-            sS[res_at(2 * f + 1, pp)] = sv.y;
-            sD[res_at(2 * f, pp)] = yv.x * inv_mu;
-            sD[res_at(2 * f + 1, pp)] = yv.y * inv_mu;
+        for (int i = 0; i < G; ++i)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int f = f0 + 8 * i, pp = lane + 32 * h;
+            const bool in = (pb + pp < m) && 2 * f < T;
+            const int64_t gi = in ? (int64_t)f * m + pb + pp : 0;
+            xg[i][h] = in ? X2[gi] : make_float2(0.f, 0.f);
+            sg[i][h] = (MODE != PM_INIT && in && !first) ? S2[gi] : make_float2(0.f, 0.f);
+            yg[i][h] = (MODE != PM_INIT && in && !first) ? Y2[gi] : make_float2(0.f, 0.f);
           }
-        }
+#pragma unroll
+        for (int i = 0; i < G; ++i)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int f = f0 + 8 * i, pp = lane + 32 * h;
+            const float2 x = xg[i][h];
+            if (MODE == PM_INIT) {
+              sZ[res_at(2 * f, pp)] = x.x;
+              sZ[res_at(2 * f + 1, pp)] = x.y;
+              const float a2 = fmaf(x.x, x.x, x.y * x.y);
+              e2 += a2;
+              l1 += sqrtf(a2);
+            } else {
+              const float2 sv = sg[i][h], yv = yg[i][h];
+              sZ[res_at(2 * f, pp)] = form_z(x.x, sv.x, yv.x, inv_mu);
+              sZ[res_at(2 * f + 1, pp)] = form_z(x.y, sv.y, yv.y, inv_mu);
+              sS[res_at(2 * f, pp)] = sv.x;
+              sS[res_at(2 * f + 1, pp)] = sv.y;
+              sD[res_at(2 * f, pp)] = yv.x * inv_mu;
+              sD[res_at(2 * f + 1, pp)] = yv.y * inv_mu;
+            }
+          }
       }
     } else {
-      for (int t = w; t < TP; t += 8) {
+      constexpr int G = kResLd;       // TP is a multiple of 32
+      for (int t0 = w; t0 < TP; t0 += 8 * G) {
+        float xg[G][2], sg[G][2], yg[G][2];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int pp = lane + 32 * h;
-          const bool in = (pb + pp < m) && t < T;
-          const int64_t gi = (int64_t)t * m + pb + pp;
-          const float x = in ? job.X[gi] : 0.f;
-          if (MODE == PM_INIT) {
-            sZ[res_at(t, pp)] = x;
-            e2 = fmaf(x, x, e2);
-            l1 += fabsf(x);
-          } else {
-            const float sv = (in && !first) ? job.S[gi] : 0.f;
-            const float yv = (in && !first) ? Yin[gi] : 0.f;
-            sZ[res_at(t, pp)] = form_z(x, sv, yv, inv_mu);
-            sS[res_at(t, pp)] = sv;
-            sD[res_at(t, pp)] = yv * inv_mu;
+        for (int i = 0; i < G; ++i)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int t = t0 + 8 * i, pp = lane + 32 * h;
+            const bool in = (pb + pp < m) && t < T;
+            const int64_t gi = in ? (int64_t)t * m + pb + pp : 0;
+            xg[i][h] = in ? job.X[gi] : 0.f;
+            sg[i][h] = (MODE != PM_INIT && in && !first) ? job.S[gi] : 0.f;
+            yg[i][h] = (MODE != PM_INIT && in && !first) ? Yin[gi] : 0.f;
           }
-        }
+#pragma unroll
+        for (int i = 0; i < G; ++i)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int t = t0 + 8 * i, pp = lane + 32 * h;
+            const float x = xg[i][h];
+            if (MODE == PM_INIT) {
+              sZ[res_at(t, pp)] = x;
+              e2 = fmaf(x, x, e2);
+              l1 += fabsf(x);
+            } else {
+              const float sv = sg[i][h], yv = yg[i][h];
+              sZ[res_at(t, pp)] = form_z(x, sv, yv, inv_mu);
+              sS[res_at(t, pp)] = sv;
+              sD[res_at(t, pp)] = yv * inv_mu;
+            }
+          }
       }
     }
     __syncthreads();
