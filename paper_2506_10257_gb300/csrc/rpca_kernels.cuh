@@ -1138,6 +1138,12 @@ __global__ void __launch_bounds__(512) eig_kernel(Bufs b, int flags, cudaGraphCo
 // Final outputs: L = X - S - E with E = (Y_k - Y_{k-1})/mu_k (Eq. 6 rearranged),
 // and the bound-bubble mask: temporal mean of |L| >= theta (Sec. II-F).
 // ---------------------------------------------------------------------------
+// The final step loads kFinLd frames of a pixel (X, S, Y_k, Y_{k-1}) before it
+// stores their L (and the copies out): the compiler cannot tell those stores
+// from the loads that follow them, so a load placed after a store waits for
+// the store's operand, i.e. for the previous frame's loads.
+constexpr int kFinLd = 8;
+
 static __device__ void final_body(Bufs b, int lc, int nc) {
   const Ctrl* ctrl = b.ctrl;
   const Job job = *b.job;
@@ -1148,8 +1154,12 @@ static __device__ void final_body(Bufs b, int lc, int nc) {
   const float inv_mu = __ldcg(&ctrl->f_inv_mu);
   const float* Yk = (kc & 1) ? job.Y1 : job.Y0;
   const float* Ykm1 = (kc & 1) ? job.Y0 : job.Y1;
+  // kc == 0: finished at the init step (X == 0 or non-finite): L = 0, S = 0.
+  // Y_{k-1}: the previous iterate, Y0 itself after one warm iteration.
+  const bool ld_xs = kc != 0, ld_yk = kc != 0 || warm, ld_ym = kc != 0 && (kc >= 2 || warm);
   if (b.cplx) {
     // complex window: (Re, Im) pairs, frame-major; the mask uses |L|
+    constexpr int G = kFinLd / 2;
     const int F = T / 2;
     const float2* X2 = reinterpret_cast<const float2*>(job.X);
     float2* S2 = reinterpret_cast<float2*>(job.S);
@@ -1158,50 +1168,71 @@ static __device__ void final_body(Bufs b, int lc, int nc) {
     const float2* Ym2 = reinterpret_cast<const float2*>(Ykm1);
     float2* So2 = reinterpret_cast<float2*>(job.Sout);
     float2* Yo2 = reinterpret_cast<float2*>(job.Yout);
+    const float2 z2 = make_float2(0.f, 0.f);
     for (int64_t p = (int64_t)lc * blockDim.x + threadIdx.x; p < m; p += (int64_t)nc * blockDim.x) {
       float acc = 0.f;
-      for (int t = 0; t < F; ++t) {
-        const int64_t i = t * m + p;
-        float2 l = make_float2(0.f, 0.f), yk = make_float2(0.f, 0.f);
-        if (kc == 0) {
-          if (warm) yk = Yk2[i];
-          S2[i] = make_float2(0.f, 0.f);
-        } else {
-          const float2 x = X2[i], s = S2[i];
-          yk = Yk2[i];
-          const float2 ym = (kc >= 2 || warm) ? Ym2[i] : make_float2(0.f, 0.f);
-          l.x = (x.x - s.x) - (yk.x * inv_mu - ym.x * inv_mu);
-          l.y = (x.y - s.y) - (yk.y * inv_mu - ym.y * inv_mu);
+      for (int t0 = 0; t0 < F; t0 += G) {
+        float2 xg[G], sg[G], yg[G], mg[G];
+#pragma unroll
+        for (int u = 0; u < G; ++u) {
+          const bool in = t0 + u < F;
+          const int64_t i = (int64_t)(in ? t0 + u : 0) * m + p;
+          xg[u] = (in && ld_xs) ? X2[i] : z2;
+          sg[u] = (in && ld_xs) ? S2[i] : z2;
+          yg[u] = (in && ld_yk) ? Yk2[i] : z2;
+          mg[u] = (in && ld_ym) ? Ym2[i] : z2;
         }
-        if (So2) So2[i] = S2[i];
-        if (Yo2) Yo2[i] = yk;
-        L2[i] = l;
-        acc += sqrtf(fmaf(l.x, l.x, l.y * l.y));
+#pragma unroll
+        for (int u = 0; u < G; ++u) {
+          if (t0 + u < F) {
+            const int64_t i = (int64_t)(t0 + u) * m + p;
+            float2 l = z2;
+            if (kc == 0) {
+              S2[i] = z2;
+            } else {
+              l.x = (xg[u].x - sg[u].x) - (yg[u].x * inv_mu - mg[u].x * inv_mu);
+              l.y = (xg[u].y - sg[u].y) - (yg[u].y * inv_mu - mg[u].y * inv_mu);
+            }
+            if (So2) So2[i] = sg[u];
+            if (Yo2) Yo2[i] = yg[u];
+            L2[i] = l;
+            acc += sqrtf(fmaf(l.x, l.x, l.y * l.y));
+          }
+        }
       }
       if (job.mask) job.mask[p] = (acc / (float)F >= job.theta) ? 1 : 0;
     }
     return;
   }
+  constexpr int G = kFinLd;
   for (int64_t p = (int64_t)lc * blockDim.x + threadIdx.x; p < m; p += (int64_t)nc * blockDim.x) {
     float acc = 0.f;
-    for (int t = 0; t < T; ++t) {
-      const int64_t i = t * m + p;
-      float l = 0.f, yk = 0.f;
-      if (kc == 0) {
-        // finished at the init step (X == 0 or non-finite): L = 0, S = 0
-        if (warm) yk = Yk[i];
-        job.S[i] = 0.f;
-      } else {
-        const float x = job.X[i], s = job.S[i];
-        yk = Yk[i];
-        // Y_{k-1}: the previous iterate, Y0 itself after one warm iteration
-        const float ym = (kc >= 2 || warm) ? Ykm1[i] : 0.f;
-        l = (x - s) - (yk * inv_mu - ym * inv_mu);
+    for (int t0 = 0; t0 < T; t0 += G) {
+      float xg[G], sg[G], yg[G], mg[G];
+#pragma unroll
+      for (int u = 0; u < G; ++u) {
+        const bool in = t0 + u < T;
+        const int64_t i = (int64_t)(in ? t0 + u : 0) * m + p;
+        xg[u] = (in && ld_xs) ? job.X[i] : 0.f;
+        sg[u] = (in && ld_xs) ? job.S[i] : 0.f;
+        yg[u] = (in && ld_yk) ? Yk[i] : 0.f;
+        mg[u] = (in && ld_ym) ? Ykm1[i] : 0.f;
       }
-      if (job.Sout) job.Sout[i] = job.S[i];
-      if (job.Yout) job.Yout[i] = yk;
-      job.L[i] = l;
-      acc += fabsf(l);
+#pragma unroll
+      for (int u = 0; u < G; ++u) {
+        if (t0 + u < T) {
+          const int64_t i = (int64_t)(t0 + u) * m + p;
+          float l = 0.f;
+          if (kc == 0)
+            job.S[i] = 0.f;
+          else
+            l = (xg[u] - sg[u]) - (yg[u] * inv_mu - mg[u] * inv_mu);
+          if (job.Sout) job.Sout[i] = sg[u];
+          if (job.Yout) job.Yout[i] = yg[u];
+          job.L[i] = l;
+          acc += fabsf(l);
+        }
+      }
     }
     if (job.mask) job.mask[p] = (acc / (float)T >= job.theta) ? 1 : 0;
   }
