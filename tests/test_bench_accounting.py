@@ -6,6 +6,7 @@ matched to the device code and scaled to a launch's windows.
 """
 import json
 import os
+import shutil
 
 import bench
 
@@ -41,9 +42,27 @@ def test_traffic_entries_count_only_for_their_kernel_source(tmp_path, monkeypatc
     assert bench.ncu_batch_traffic(h, [32], "missing") is None
 
 
-def test_kernel_source_hash_covers_the_narrow_headers():
+def test_kernel_source_hash_covers_the_narrow_headers(tmp_path, monkeypatch):
     csrc = os.path.join(os.path.dirname(bench.__file__), "paper_2506_10257_gb300", "csrc")
     heads = [f for f in os.listdir(csrc) if f.endswith(".cuh")]
     assert "rpca_kernels.cuh" in heads and "rpca_batch.cuh" in heads
     h = bench.kernel_source_hash()
     assert len(h) == 16 and int(h, 16) >= 0
+    # on a copy of the headers: editing a tiled header keeps the hash, editing
+    # a narrow one (or adding a header) changes it
+    dst = tmp_path / "paper_2506_10257_gb300" / "csrc"
+    dst.mkdir(parents=True)
+    for f in heads:
+        shutil.copy(os.path.join(csrc, f), dst / f)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.kernel_source_hash() == h
+    for f in bench.TILED_HEADERS:
+        with open(dst / f, "a") as fh:
+            fh.write("// edited\n")
+    assert bench.kernel_source_hash() == h
+    with open(dst / "rpca_kernels.cuh", "a") as fh:
+        fh.write("// edited\n")
+    h2 = bench.kernel_source_hash()
+    assert h2 != h
+    (dst / "rpca_new.cuh").write_text("// a new narrow header\n")
+    assert bench.kernel_source_hash() not in (h, h2)
