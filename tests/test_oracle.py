@@ -95,6 +95,32 @@ def test_fixed_l1_schedule_first_iteration():
     assert r.Y[0, 0] == pytest.approx(lam, rel=1e-12)
     r5 = O.rpca(X, schedule=O.SCHEDULE_FIXED_L1, max_iter=5, tol=0)
     assert all(h[0] == r.mu for h in r5.history)     # mu held constant
+    # a negative entry counts with its magnitude in ||X||_1: a e_00 - a e_11
+    # has ||X||_1 = 2a, so mu = 32 / (8 a) = 4/a
+    X[1, 1] = -a
+    assert O.rpca(X, schedule=O.SCHEDULE_FIXED_L1, max_iter=1).mu == pytest.approx(4 / a, rel=1e-15)
+
+
+def test_ialm_penalty_schedule_and_default_lambda():
+    # mu0 = 1.25 / ||X||_2 with the spectral norm: X = diag(3, 4) in a 6 x 3
+    # matrix has singular values {4, 3} (Frobenius norm 5), so mu0 = 1.25/4;
+    # lambda = 1/sqrt(max(m, T)) = 1/sqrt(6)
+    X = np.zeros((6, 3))
+    X[0, 0], X[1, 1] = 3.0, 4.0
+    r = O.rpca(X, max_iter=1)
+    assert r.mu == pytest.approx(1.25 / 4, rel=1e-15)
+    assert r.lam == pytest.approx(1 / math.sqrt(6), rel=1e-15)
+    # the larger dimension sets lambda whichever it is: 100 x 4 and 4 x 100 both give 1/10
+    rng = np.random.default_rng(5)
+    for shape in ((100, 4), (4, 100)):
+        assert O.rpca(rng.standard_normal(shape), max_iter=1).lam == pytest.approx(0.1, rel=1e-15)
+    # mu_k = min(1.5^(k-1), 1e7) mu0: the cap binds from k = 41 (1.5^40 > 1e7)
+    G = rng.standard_normal((6, 3))
+    h = O.rpca(G, max_iter=45, tol=-1.0).history
+    assert len(h) == 45
+    for k, (mu, _, _) in enumerate(h):
+        assert mu == pytest.approx(min(1.5 ** k, 1e7) * h[0][0], rel=1e-12)
+    assert h[44][0] == h[40][0] == pytest.approx(1e7 * h[0][0], rel=1e-12) and h[39][0] < h[40][0]
 
 
 # --- stopping rule and special cases ----------------------------------------
@@ -242,6 +268,8 @@ def test_rmse_and_dice_hand_values():
     th = O.mask_threshold(img, np.array([0, 1, 0, 1], bool))
     assert th == pytest.approx(1.75)
     np.testing.assert_array_equal(O.bound_mask(img, th), [False, True, False, True])
+    # "at least theta": a pixel exactly at the threshold is in the mask
+    np.testing.assert_array_equal(O.bound_mask(np.array([1.0, 0.999, 2.0]), 1.0), [True, False, True])
 
 
 def test_temporal_mean_abs_hand_values():
