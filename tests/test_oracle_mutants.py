@@ -1,12 +1,14 @@
-"""Planted mistakes in the oracle, on the CPU: every one must fail a pin.
+"""Planted mistakes in the oracles, on the CPU: every one must fail a pin.
 
-The pins of tests/test_oracle.py check the oracle against closed forms, hand
-derivations, certificates and brute force.  Here each test plants one
-plausible mistake in one oracle function (a dropped term, a wrong sign, a
-wrong threshold, a transposed operand, a misplaced step), swaps the mutated
-function into the oracle module for the duration of the test, runs the pins
-and requires at least one of them to fail.  A mistake that no pin notices
-would mean the pins leave that part of Sec. II-A unchecked.
+The pins of tests/test_oracle.py (the solver's oracle) and of
+tests/test_prefilter_oracle.py (the pre-filter's) check the oracles against
+closed forms, hand derivations, certificates and brute force.  Here each test
+plants one plausible mistake in one oracle function (a dropped term, a wrong
+sign, a wrong threshold, a transposed operand, a misplaced step), swaps the
+mutated function into the oracle module for the duration of the test, runs
+that oracle's pins and requires at least one of them to fail.  A mistake that
+no pin notices would mean the pins leave that part of Sec. II-A (or of the
+pre-filter of Sec. III-IV) unchecked.
 """
 import __future__
 import inspect
@@ -16,6 +18,8 @@ import numpy as np
 import pytest
 
 import test_oracle as pins
+import test_prefilter_oracle as pf_pins
+from oracle import prefilter_oracle as PF
 from oracle import rpca_oracle as O
 
 # (oracle function, text in its source, replacement, what the mistake is)
@@ -66,39 +70,73 @@ MUTANTS = [
 ]
 
 
-def _mutant(name, old, new):
-    src = textwrap.dedent(inspect.getsource(getattr(O, name)))
-    assert src.count(old) == 1, (name, old)
-    code = compile(src.replace(old, new), f"<mutant of {name}>", "exec",
-                   flags=__future__.annotations.compiler_flag, dont_inherit=True)
-    g = dict(O.__dict__)
+# the pre-filter's oracle (Sec. III frame exclusion and moving average, the
+# Sec. IV high-pass): (function, [(text, replacement), ...], what)
+PF_MUTANTS = [
+    ("frame_correlation", [("ac = a - a.mean()", "ac = a")], "correlation without centring"),
+    ("frame_correlation", [("na = np.sqrt(np.sum(ac * ac))", "na = np.sum(ac * ac)")], "norm without the root"),
+    ("frame_correlation", [("        return 0.0\n", "        return 1.0\n")], "flat frame correlates fully"),
+    ("neighbour_correlations", [("frames[t + 1]", "frames[min(t + 2, T - 1)]")], "next-but-one neighbour"),
+    ("kept_frames", [("if best >= corr_min:", "if best > corr_min:")], "strict correlation limit"),
+    ("kept_frames", [("best = -np.inf", "best = np.inf"), ("best = max(best, c[t - 1])", "best = min(best, c[t - 1])"),
+                     ("best = max(best, c[t])", "best = min(best, c[t])")], "every neighbour must correlate"),
+    ("kept_frames", [("return np.array([0], dtype=np.int64)", "return np.array([], dtype=np.int64)")],
+     "a one-frame window dropped"),
+    ("moving_average", [("sum(axis=0) / window", "sum(axis=0) / (window + 1)")], "mean over window + 1"),
+    ("moving_average", [("sel[j:j + window]", "sel[j:j + window - 1]")], "window one frame short"),
+    ("moving_average", [("sel = frames[kept]", "sel = frames[:]")], "excluded frames averaged"),
+    ("moving_average", [("n = K - window + 1", "n = K - window")], "last window dropped"),
+    ("highpass", [("h = (window - 1) // 2", "h = window // 2")], "centre frame one late"),
+    ("highpass", [("frames[kept[j + h]].astype(np.float64) - avg[j]", "avg[j] - frames[kept[j + h]].astype(np.float64)")],
+     "high-pass sign"),
+    ("highpass", [("frames[kept[j + h]]", "frames[j + h]")], "centre frame by raw index"),
+    ("prefilter", [("filt = highpass if high_pass else moving_average", "filt = moving_average if high_pass else highpass")],
+     "filters swapped"),
+]
+
+
+def _mutant(mod, name, edits):
+    src = textwrap.dedent(inspect.getsource(getattr(mod, name)))
+    for old, new in edits:
+        assert src.count(old) == 1, (name, old)
+        src = src.replace(old, new)
+    code = compile(src, f"<mutant of {name}>", "exec", flags=__future__.annotations.compiler_flag, dont_inherit=True)
+    g = dict(mod.__dict__)
     exec(code, g)
     return g[name]
 
 
-def _pins():
+def _pins(module):
     out = []
-    for n in dir(pins):
-        f = getattr(pins, n)
+    for n in dir(module):
+        f = getattr(module, n)
         if n.startswith("test_") and inspect.isfunction(f) and not inspect.signature(f).parameters:
             out.append(f)
     return sorted(out, key=lambda f: f.__code__.co_firstlineno)
 
 
-def test_pins_pass_on_the_oracle_as_written():
-    for pin in _pins():
-        pin()
+def _first_failing_pin(module):
+    with np.errstate(all="ignore"):
+        for pin in _pins(module):
+            try:
+                pin()
+            except Exception:  # a failed assertion, or a crash on the mutant's output
+                return pin.__name__
+    return None
+
+
+def test_pins_pass_on_the_oracles_as_written():
+    assert _first_failing_pin(pins) is None
+    assert _first_failing_pin(pf_pins) is None
 
 
 @pytest.mark.parametrize("name,old,new,what", MUTANTS, ids=[m[3] for m in MUTANTS])
 def test_planted_mistake_fails_a_pin(name, old, new, what, monkeypatch):
-    monkeypatch.setattr(O, name, _mutant(name, old, new))
-    caught = None
-    with np.errstate(all="ignore"):
-        for pin in _pins():
-            try:
-                pin()
-            except Exception:  # a failed assertion, or a crash on the mutant's output
-                caught = pin.__name__
-                break
-    assert caught is not None, f"no pin notices: {what} ({name}: {old!r} -> {new!r})"
+    monkeypatch.setattr(O, name, _mutant(O, name, [(old, new)]))
+    assert _first_failing_pin(pins) is not None, f"no pin notices: {what} ({name}: {old!r} -> {new!r})"
+
+
+@pytest.mark.parametrize("name,edits,what", PF_MUTANTS, ids=[m[2] for m in PF_MUTANTS])
+def test_planted_prefilter_mistake_fails_a_pin(name, edits, what, monkeypatch):
+    monkeypatch.setattr(PF, name, _mutant(PF, name, edits))
+    assert _first_failing_pin(pf_pins) is not None, f"no pin notices: {what} ({name}: {edits!r})"

@@ -67,6 +67,30 @@ def test_all_uncorrelated_keeps_none_and_single_frame_keeps_it():
     assert list(P.kept_frames(F[:1], 0.8)) == [0]
 
 
+def test_frame_exactly_at_the_limit_is_kept():
+    # "below 0.8 is excluded": a neighbour correlation equal to the limit keeps
+    # the frame.  Frames with exactly representable coefficients: a and a have
+    # correlation 4 / (2 * 2) = 1, a and b (orthogonal, zero mean) 0 / 4 = 0.
+    a = np.array([1.0, -1.0, 1.0, -1.0])
+    b = np.array([1.0, 1.0, -1.0, -1.0])
+    assert P.frame_correlation(a, a) == 1.0 and P.frame_correlation(a, b) == 0.0
+    assert list(P.kept_frames(np.stack([a, a]), 1.0)) == [0, 1]
+    assert list(P.kept_frames(np.stack([a, b]), 0.0)) == [0, 1]
+    assert list(P.kept_frames(np.stack([a, b]), 1e-12)) == []
+
+
+def test_prefilter_outputs_by_hand():
+    # three frames: one pixel pattern plus the offsets 0, 3, 6 (neighbours
+    # correlate exactly 1, so all are kept); window of 2 frames
+    pat = np.array([1.0, -1.0, 1.0, -1.0])
+    F = np.stack([0.0 + pat, 3.0 + pat, 6.0 + pat])
+    avg, kept, c = P.prefilter(F, 0.8, 2)
+    assert list(kept) == [0, 1, 2] and np.all(c == 1.0)
+    np.testing.assert_array_equal(avg, np.stack([1.5 + pat, 4.5 + pat]))        # moving average of 2
+    hp, _, _ = P.prefilter(F, 0.8, 2, high_pass=True)
+    np.testing.assert_array_equal(hp, np.full((2, 4), -1.5))                       # frame j minus the mean
+
+
 def test_moving_average_closed_forms():
     m, T, w = 7, 30, 20
     v = np.arange(1, m + 1, dtype=np.float64)
